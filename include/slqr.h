@@ -1,0 +1,156 @@
+/*
+ * slqr.h -- C ABI of libslqr: in-place Householder QR in Lawson-Hanson H12
+ * storage, Q^T.B application and back-substitution on one NVIDIA GB300
+ * (sm_103a), for the least-squares subproblems of SLSQP.
+ *
+ * The operations follow the paper "Efficient Task Graph Scheduling for
+ * Parallel QR Factorization in SLSQP" (Chatterjee et al.):
+ *   - Alg. 2 (Section 3): in-place transform of A to upper-triangular form by
+ *     the kernels update_pivot_row / update_trailing_non_pivot_row;
+ *   - Task 1 / Task 2 (Alg. 3, Alg. 4): the pivot scalar `up` of each
+ *     reflector is kept in a global array for later reuse, and a pivot whose
+ *     reflector is undefined (zero column) is skipped;
+ *   - Section 1 and the abstract: the stored reflectors are reused to apply
+ *     Q^T and by the back-substitution at each SLSQP iteration.
+ *
+ * Storage form (H12).  A is m x n, column-major, leading dimension lda >= m,
+ * FP64, with m >= n.  After slqr_factor:
+ *   A[k, j] (k <= j)  = R[k, j]            (R upper triangular, R[k,k] = cl_k)
+ *   A[i, k] (i >  k)  = tail of reflector k (left exactly as it was when the
+ *                       reflector was built)
+ *   up[k]             = pivot entry of reflector k, for k < min(m-1, n);
+ *                       up[k] = 0 for a skipped pivot and for k >= min(m-1, n).
+ * Reflector k is v_k = (0,..,0, up[k], A[k+1:m, k]) and
+ * H_k = I + v_k v_k^T / b_k with b_k = up[k] * R[k,k] (< 0 when defined), which
+ * is the Householder matrix I - 2 v v^T / (v^T v) of Alg. 1.  Q = H_0 H_1 ...
+ * The sign rule is cl_k = -s when x0 > 0 and +s otherwise (s = ||x||, x the
+ * column below and on the diagonal, x0 its first entry).
+ *
+ * Conventions for every entry point:
+ *   - Pointers to matrices and vectors are DEVICE pointers owned by the
+ *     caller, unless stated otherwise.  The library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; argument errors are
+ *     returned synchronously and enqueue nothing.
+ *   - Device-side conditions (a zero diagonal of R in slqr_solve_r, a bounded
+ *     device wait that gave up) are written to a status word of the context
+ *     and returned by slqr_sync().
+ *   - A context serialises its calls: calls made with one context must be
+ *     issued on one stream, or ordered by the caller, because they share the
+ *     context's workspace.  Use one context per concurrent stream.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef SLQR_H
+#define SLQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int slqr_status;
+
+#define SLQR_OK          0
+#define SLQR_PENDING     1   /* request not finished yet (slqr_poll) */
+#define SLQR_EINVAL    (-1)  /* bad argument: nothing was enqueued */
+#define SLQR_ENOMEM    (-2)  /* device allocation failed */
+#define SLQR_ECUDA     (-3)  /* a CUDA runtime call failed */
+#define SLQR_ETIMEOUT  (-4)  /* a bounded device-side wait gave up */
+#define SLQR_ERANK     (-5)  /* R has an exact zero on its diagonal */
+#define SLQR_EBUSY     (-6)  /* over the HBM budget of the context */
+#define SLQR_ENOTFOUND (-7)  /* unknown ticket or handle */
+
+typedef struct slqr_ctx slqr_ctx;
+
+/*
+ * Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the device
+ * memory the context may hold for its own workspace and, in serving, for
+ * resident factorizations (0 = no cap).  On success *ctx is set and SLQR_OK
+ * returned; the caller releases it with slqr_destroy.
+ */
+slqr_status slqr_create(slqr_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Free the context and its workspace.  Waits for work the context enqueued. */
+void slqr_destroy(slqr_ctx *ctx);
+
+/* Text of the last error recorded in `ctx` (never NULL; "" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char *slqr_last_error(slqr_ctx *ctx);
+
+/*
+ * Wait for `stream`, then return and clear the context's device status word:
+ * SLQR_OK, SLQR_ERANK (a zero diagonal met by slqr_solve_r since the last
+ * sync) or SLQR_ETIMEOUT (a bounded device wait gave up).  Also returns
+ * SLQR_ECUDA if the stream reports a CUDA error.
+ */
+slqr_status slqr_sync(slqr_ctx *ctx, void *stream);
+
+/*
+ * Panel width the factorization uses for an m x n problem (columns per
+ * compact-WY block).  It depends only on (m, n).
+ */
+int slqr_panel_width(int m, int n);
+
+/*
+ * Size in bytes of the optional compact-WY store of an m x n factorization:
+ * for each panel of slqr_panel_width(m, n) reflectors it keeps the strict
+ * upper triangle of the Gram matrix V^T V, the scalars tau_k = -1/b_k (0 for a
+ * skipped pivot) and the top square of V.  These are intermediate results of
+ * the factorization that slqr_apply_qt can reuse instead of recomputing.
+ */
+size_t slqr_wy_size(int m, int n);
+
+/*
+ * In-place H12 QR of A (Alg. 2; Task 1 skip rule).  On return A holds R and
+ * the reflector tails and up[0:n] the pivot entries (storage form above).
+ *   m, n   sizes, m >= n >= 0, m >= 1 when n >= 1; m <= slqr_max_rows()
+ *   A      device, m x n column-major, lda >= max(1, m); overwritten
+ *   up     device, n doubles; written
+ *   wy     device, slqr_wy_size(m, n) bytes, or NULL; when given, it receives
+ *          the compact-WY store of this factorization (for slqr_apply_qt)
+ * Errors: SLQR_EINVAL (sizes, lda, NULL pointers), SLQR_ENOMEM (workspace),
+ * SLQR_ECUDA.  Device waits that give up are reported by slqr_sync.
+ */
+slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
+                        double *wy, void *stream);
+
+/* Largest m that slqr_factor accepts (the panel is held in shared memory). */
+int slqr_max_rows(void);
+
+/*
+ * B <- Q^T B for the factorization (A, up) made by slqr_factor: the
+ * reflectors H_0, H_1, ... are applied in the order they were built (the
+ * reuse of the stored reflectors named in Section 1).  Reflectors with
+ * b_k = up[k] * R[k,k] >= 0 are skipped.
+ *   A, up  device, as left by slqr_factor (read only)
+ *   nrhs   number of right-hand sides, >= 0
+ *   B      device, m x nrhs column-major, ldb >= max(1, m); overwritten
+ *   wy     device compact-WY store written by slqr_factor for this same
+ *          (A, up), or NULL to recompute it from (A, up) (costs about
+ *          panel_width/4 times the flops of one right-hand side)
+ * Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
+ */
+slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                          const double *up, const double *wy, int nrhs, double *B, int ldb,
+                          void *stream);
+
+/*
+ * Back-substitution R X = B[0:n, :] with R = triu(A[0:n, 0:n]); X overwrites
+ * B[0:n, :] (the back-substitution that reuses the factorization, Section 1).
+ * An exact zero R[i,i] sets x_i = 0 and records SLQR_ERANK in the device
+ * status word (read it with slqr_sync).
+ *   n      order of R, >= 0
+ *   A      device, lda >= max(1, n); only its upper triangle is read
+ *   nrhs   >= 0;  B device, ldb >= max(1, n)
+ * Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
+ */
+slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrhs,
+                         double *B, int ldb, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLQR_H */
