@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the FP64 H12 least-squares path on GB300.
+
+One step = one pass of the whole hot path over the two FP64 matrices of the
+plain-method workload, with inputs resident in HBM:
+  tall 16384 x 2048 and square 8192 x 8192, iid N(0,1) (seeds 2 and 3):
+  restore A from its pristine copy, in-place H12 factorization (slqr_factor,
+  keeping the compact-WY store), Q^T applied to 1 and to 64 N(0,1) right-hand
+  sides (slqr_apply_qt), back-substitution of all 65 (slqr_solve_r).
+Throughput is counted with the algorithmic Householder flop counts
+(2mn^2 - 2n^3/3 per factorization, 4mn - 2n^2 per right-hand side for Q^T,
+n^2 per right-hand side for the solve), whatever the blocking does.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one process per GPU: the path does not shard, so
+every rank runs its own replica of the workload ("replicas only"; weak
+scaling).  --impl reference times the CPU oracle (plain sequential C, FP64) on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "QR GFLOP/s & batched QR+solves/s vs plain FP64 at <=1e-10 err; p50/p99 latency"
+UNIT = "GFLOP/s"
+SHAPES = [(16384, 2048, 2), (8192, 8192, 3)]   # (m, n, seed)
+NRHS = (1, 64)
+WORKLOAD = ("plain FP64 H12 least squares: tall 16384x2048 + square 8192x8192 iid N(0,1); "
+            "factor + Q^T (1 and 64 RHS) + back-substitution (65 RHS)")
+# FP64 FMA pipe: 2 DFMA (4 flops) per clock per SM x 152 SMs x 2070 MHz
+FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12
+CPU_SAMPLE_COLS = 512   # oracle sample: leading m x 512 block of each matrix
+
+
+def step_flops(shapes=SHAPES, nrhs=NRHS):
+    total = 0.0
+    for m, n, _ in shapes:
+        total += 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+        r = sum(nrhs)
+        total += r * (4.0 * m * n - 2.0 * n * n)
+        total += r * float(n) * n
+    return total
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"slqr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the cpu_baseline leg and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(mats):
+    """Run the oracle's full LS solve on the leading m x CPU_SAMPLE_COLS block of
+    each matrix; returns (flops, seconds)."""
+    import oracle
+    oracle.build()
+    flops, secs = 0.0, 0.0
+    for (m, n, _), (A, b) in zip(SHAPES, mats):
+        p = min(n, CPU_SAMPLE_COLS)
+        As = np.asfortranarray(A[:, :p])
+        t0 = time.perf_counter()
+        oracle.lstsq(As, b)
+        secs += time.perf_counter() - t0
+        flops += 2.0 * m * p * p - 2.0 * p ** 3 / 3.0 + (4.0 * m * p - 2.0 * p * p) + p * p
+    return flops, secs
+
+
+def cpu_sample_desc():
+    return (f"oracle (gcc -O2, 1 thread) factor + Q^T b + solve of the leading m x "
+            f"{CPU_SAMPLE_COLS} column block of each matrix (16384x{CPU_SAMPLE_COLS}, "
+            f"8192x{CPU_SAMPLE_COLS})")
+
+
+def gen_inputs():
+    import workloads
+    mats = []
+    for m, n, seed in SHAPES:
+        A, b = workloads.gaussian(m, n, seed)
+        mats.append((A, b))
+    return mats
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    mats = gen_inputs()
+    for _ in range(args.warmup):
+        oracle_sample(mats)
+    tot_f, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        f, s = oracle_sample(mats)
+        tot_f += f
+        tot_s += s
+    value = tot_f / tot_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": cpu_sample_desc()},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample_desc()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def colmajor_cuda(a, device):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2506_09463_gb300 import abi, api
+
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    ctx = api.Context(local_rank)
+    stream = torch.cuda.current_stream(device)
+    mats_h = gen_inputs()
+
+    # device-resident inputs and working buffers
+    bufs = []
+    import workloads
+    for (m, n, seed), (A, b) in zip(SHAPES, mats_h):
+        A0 = colmajor_cuda(A, device)
+        Aw = A0.t().clone().t()
+        B0 = torch.empty(m, sum(NRHS), dtype=torch.float64, device=device)
+        B0[:, 0] = torch.from_numpy(b).to(device)
+        B0[:, 1:] = torch.from_numpy(workloads.gaussian_rhs(m, NRHS[1], seed)).to(device)
+        B0 = B0.t().contiguous().t()
+        Bw = B0.t().clone().t()
+        up = torch.empty(n, dtype=torch.float64, device=device)
+        wy = ctx.wy_buffer(m, n, device=device)
+        bufs.append(dict(m=m, n=n, A0=A0, A=Aw, B0=B0, B=Bw, up=up, wy=wy))
+
+    def step(timed_copy=True):
+        for d in bufs:
+            d["A"].copy_(d["A0"])
+            d["B"].copy_(d["B0"])
+            ctx.factor(d["A"], d["up"], d["wy"])
+            ctx.apply_qt(d["A"], d["up"], d["B"][:, :1], wy=d["wy"])
+            ctx.apply_qt(d["A"], d["up"], d["B"][:, 1:], wy=d["wy"])
+            ctx.solve_r(d["A"], d["B"])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    for _ in range(args.warmup):
+        step()
+    st = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up: {abi.slqr_last_error(ctx.ctx)}")
+
+    # ---- timed region (device-resident inputs) ----
+    clocks = ClockSampler(local_rank)
+    abi.slqr_profile(ctx.ctx, True)
+    launches0 = abi.slqr_launch_count(ctx.ctx)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = abi.slqr_launch_count(ctx.ctx) - launches0
+    ms = e0.elapsed_time(e1)
+    prof = {name: abi.slqr_profile_read(ctx.ctx, k) for k, name in enumerate(abi.KERNEL_NAMES)}
+    abi.slqr_profile(ctx.ctx, False)
+    st = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {abi.slqr_last_error(ctx.ctx)}")
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    flops = step_flops()
+    value = world * flops * args.steps / (t_max / 1e3) / 1e9
+
+    # ---- end-to-end through the public API with host buffers ----
+    pinned = []
+    for d, (A, b) in zip(bufs, mats_h):
+        Ah = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()       # n x m = A^T rows
+        Bh = d["B0"].t().contiguous().cpu().pin_memory()                     # nrhs x m
+        Xh = torch.empty(sum(NRHS), d["n"], dtype=torch.float64).pin_memory()
+        pinned.append((Ah, Bh, Xh))
+    h2d = sum(Ah.numel() * 8 + Bh.numel() * 8 for Ah, Bh, _ in pinned)
+    d2h = sum(Xh.numel() * 8 for _, _, Xh in pinned)
+
+    def e2e_step():
+        for d, (Ah, Bh, Xh) in zip(bufs, pinned):
+            d["A"].t().copy_(Ah, non_blocking=True)
+            d["B"].t().copy_(Bh, non_blocking=True)
+            ctx.factor(d["A"], d["up"], d["wy"])
+            ctx.apply_qt(d["A"], d["up"], d["B"][:, :1], wy=d["wy"])
+            ctx.apply_qt(d["A"], d["up"], d["B"][:, 1:], wy=d["wy"])
+            ctx.solve_r(d["A"], d["B"])
+            Xh.copy_(d["B"][: d["n"]].t(), non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * flops * args.steps / (e2e_ms / 1e3) / 1e9
+    if ctx.sync() != 0:
+        raise RuntimeError(abi.slqr_last_error(ctx.ctx))
+
+    # ---- roofline of the dominant kernel (most device time in the timed region) ----
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms, dn, dfl = prof[dom]
+    achieved = (dfl / dn) / (dms / dn / 1e3) / 1e12 if dn else 0.0
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: FP64 FMA pipe 4 flop/clk/SM x 152 SMs x 2070 MHz"}
+    kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / max(1e-9, ms)} for k, v in prof.items()}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        f, s = oracle_sample(mats_h)
+        cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": cpu_sample_desc(), "seconds": s}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1))",
+        "config": {"workload": WORKLOAD, "shapes": [[m, n] for m, n, _ in SHAPES],
+                   "nrhs": list(NRHS), "panel_width": [abi.slqr_panel_width(m, n) for m, n, _ in SHAPES],
+                   "l2": "inputs larger than L2 (268 MB and 537 MB matrices, no flush)",
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -149,6 +149,29 @@ slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *A, int lda,
 slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrhs,
                          double *B, int ldb, void *stream);
 
+/*
+ * Optional CUDA-event profiler (tracing aid; no counterpart in the paper).
+ * slqr_profile(ctx, 1) clears the totals and starts recording a pair of CUDA
+ * events on the launching stream around every kernel the context launches;
+ * slqr_profile(ctx, 0) stops.  slqr_profile_read waits for the recorded
+ * events and returns, for one kernel family, the summed device time (ms), the
+ * number of launches and the summed algorithmic flops of those launches
+ * (Householder counts; for SLQR_KERNEL_TW and the rebuild, the blocking
+ * overhead flops).  Families:
+ */
+#define SLQR_KERNEL_PANEL      0  /* cooperative panel factorization            */
+#define SLQR_KERNEL_VTX        1  /* W = V^T X partials (trailing update, Q^T B) */
+#define SLQR_KERNEL_TW         2  /* W' = T^T W                                  */
+#define SLQR_KERNEL_UPD        3  /* X -= V W'                                   */
+#define SLQR_KERNEL_WY_REBUILD 4  /* compact-WY rebuild inside slqr_apply_qt     */
+#define SLQR_KERNEL_TRSM       5  /* back-substitution steps                     */
+int slqr_profile(slqr_ctx *ctx, int enable);
+slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms, long long *launches,
+                              double *flops);
+
+/* Number of CUDA kernels this context has launched since it was created. */
+long long slqr_launch_count(slqr_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,145 @@
+"""Thin ctypes binding of libslqr (include/slqr.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libslqr.so.  There is no fallback: if the library is missing or does
+not load, importing this module raises.  Build it with
+``python -m paper_2506_09463_gb300.build`` (or ``__graft_entry__.build()``).
+
+Pointers are passed as Python ints (device addresses, e.g. ``tensor.data_ptr()``)
+and streams as ints (``torch.cuda.current_stream().cuda_stream``; 0 = legacy
+default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+SLQR_OK = 0
+SLQR_PENDING = 1
+SLQR_EINVAL = -1
+SLQR_ENOMEM = -2
+SLQR_ECUDA = -3
+SLQR_ETIMEOUT = -4
+SLQR_ERANK = -5
+SLQR_EBUSY = -6
+SLQR_ENOTFOUND = -7
+
+STATUS_NAMES = {
+    SLQR_OK: "SLQR_OK", SLQR_PENDING: "SLQR_PENDING", SLQR_EINVAL: "SLQR_EINVAL",
+    SLQR_ENOMEM: "SLQR_ENOMEM", SLQR_ECUDA: "SLQR_ECUDA", SLQR_ETIMEOUT: "SLQR_ETIMEOUT",
+    SLQR_ERANK: "SLQR_ERANK", SLQR_EBUSY: "SLQR_EBUSY", SLQR_ENOTFOUND: "SLQR_ENOTFOUND",
+}
+
+# (name, restype, argtypes) of every entry point declared in include/slqr.h
+_c_int, _c_size, _vp, _dbl = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_double
+SIGNATURES = [
+    ("slqr_create", _c_int, [ctypes.POINTER(_vp), _c_int, _c_size]),
+    ("slqr_destroy", None, [_vp]),
+    ("slqr_last_error", ctypes.c_char_p, [_vp]),
+    ("slqr_sync", _c_int, [_vp, _vp]),
+    ("slqr_panel_width", _c_int, [_c_int, _c_int]),
+    ("slqr_wy_size", _c_size, [_c_int, _c_int]),
+    ("slqr_max_rows", _c_int, []),
+    ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    ("slqr_apply_qt", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _vp, _c_int, _vp]),
+    ("slqr_solve_r", _c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int, _vp]),
+    ("slqr_profile", _c_int, [_vp, _c_int]),
+    ("slqr_profile_read", _c_int, [_vp, _c_int, ctypes.POINTER(_dbl),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_dbl)]),
+    ("slqr_launch_count", ctypes.c_longlong, [_vp]),
+]
+
+KERNEL_PANEL, KERNEL_VTX, KERNEL_TW, KERNEL_UPD, KERNEL_WY_REBUILD, KERNEL_TRSM = range(6)
+KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm"]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libslqr.so not built ({LIB_PATH} missing); run "
+            "`python -m paper_2506_09463_gb300.build` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class SlqrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def slqr_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    ctx = _vp()
+    st = _lib.slqr_create(ctypes.byref(ctx), device, hbm_budget_bytes)
+    if st != SLQR_OK:
+        raise SlqrError(st, f"slqr_create(device={device}) failed")
+    return ctx.value
+
+
+def slqr_destroy(ctx: int) -> None:
+    _lib.slqr_destroy(ctx)
+
+
+def slqr_last_error(ctx: int) -> str:
+    return _lib.slqr_last_error(ctx).decode()
+
+
+def slqr_sync(ctx: int, stream: int = 0) -> int:
+    return _lib.slqr_sync(ctx, stream)
+
+
+def slqr_panel_width(m: int, n: int) -> int:
+    return _lib.slqr_panel_width(m, n)
+
+
+def slqr_wy_size(m: int, n: int) -> int:
+    return _lib.slqr_wy_size(m, n)
+
+
+def slqr_max_rows() -> int:
+    return _lib.slqr_max_rows()
+
+
+def slqr_factor(ctx, m, n, A, lda, up, wy, stream) -> int:
+    return _lib.slqr_factor(ctx, m, n, A, lda, up, wy, stream)
+
+
+def slqr_apply_qt(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, stream) -> int:
+    return _lib.slqr_apply_qt(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, stream)
+
+
+def slqr_solve_r(ctx, n, A, lda, nrhs, B, ldb, stream) -> int:
+    return _lib.slqr_solve_r(ctx, n, A, lda, nrhs, B, ldb, stream)
+
+
+def slqr_profile(ctx: int, enable: bool) -> int:
+    return _lib.slqr_profile(ctx, 1 if enable else 0)
+
+
+def slqr_profile_read(ctx: int, kernel: int):
+    """(ms, launches, flops) recorded for one kernel family."""
+    ms, n, fl = _dbl(), ctypes.c_longlong(), _dbl()
+    st = _lib.slqr_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl))
+    check(ctx, st, "slqr_profile_read")
+    return ms.value, n.value, fl.value
+
+
+def slqr_launch_count(ctx: int) -> int:
+    return _lib.slqr_launch_count(ctx)
+
+
+def check(ctx: int, status: int, what: str) -> None:
+    """Raise SlqrError for a negative status, with the context's message."""
+    if status < 0:
+        raise SlqrError(status, f"{what}: {slqr_last_error(ctx)}")

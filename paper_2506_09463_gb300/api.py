@@ -1,0 +1,121 @@
+"""Tensor-level calls over the C ABI (torch supplies device memory and streams).
+
+Matrices are FP64 CUDA tensors of shape (m, n) in column-major layout
+(``stride() == (1, ld)``, ``ld >= m``), as the H12 storage form wants; use
+``colmajor()`` to get one.  Every call goes through libslqr (``abi``).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import abi
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """A column-major copy (or view) of a 1-D or 2-D tensor."""
+    if t.dim() == 1:
+        return t.contiguous()
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() == 1:
+        return max(1, t.shape[0])
+    if t.stride(0) != 1 and t.shape[1] > 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1)")
+    return max(1, t.stride(1) if t.shape[1] > 1 else t.shape[0])
+
+
+def _check(t: torch.Tensor, name: str):
+    if not t.is_cuda or t.dtype != torch.float64:
+        raise ValueError(f"{name} must be a float64 CUDA tensor")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """Owns one slqr context (workspace + device status word) on one device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.ctx = abi.slqr_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.ctx:
+            abi.slqr_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- entry points ---------------------------------------------------------
+    def factor(self, A: torch.Tensor, up: torch.Tensor | None = None,
+               wy: torch.Tensor | None = None, stream=None):
+        """In-place H12 QR of A (column-major m x n).  Returns (A, up, wy)."""
+        _check(A, "A")
+        m, n = A.shape
+        if up is None:
+            up = torch.empty(n, dtype=torch.float64, device=A.device)
+        st = abi.slqr_factor(self.ctx, m, n, A.data_ptr(), _ld(A), up.data_ptr(),
+                             wy.data_ptr() if wy is not None else None, _stream(stream))
+        abi.check(self.ctx, st, "slqr_factor")
+        return A, up, wy
+
+    def wy_buffer(self, m: int, n: int, device=None) -> torch.Tensor:
+        """Device buffer for the compact-WY store of an m x n factorization."""
+        nbytes = abi.slqr_wy_size(m, n)
+        return torch.empty(max(1, nbytes // 8), dtype=torch.float64,
+                           device=device if device is not None else f"cuda:{self.device}")
+
+    def apply_qt(self, A: torch.Tensor, up: torch.Tensor, B: torch.Tensor,
+                 wy: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """B <- Q^T B in place (B column-major m x nrhs, or a length-m vector)."""
+        _check(A, "A"); _check(B, "B")
+        m, n = A.shape
+        nrhs = 1 if B.dim() == 1 else B.shape[1]
+        st = abi.slqr_apply_qt(self.ctx, m, n, A.data_ptr(), _ld(A), up.data_ptr(),
+                               wy.data_ptr() if wy is not None else None, nrhs,
+                               B.data_ptr(), _ld(B), _stream(stream))
+        abi.check(self.ctx, st, "slqr_apply_qt")
+        return B
+
+    def solve_r(self, A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+        """X = R^{-1} B[0:n] in place in B[0:n] (R = triu(A[0:n, 0:n]))."""
+        _check(A, "A"); _check(B, "B")
+        n = A.shape[1]
+        nrhs = 1 if B.dim() == 1 else B.shape[1]
+        st = abi.slqr_solve_r(self.ctx, n, A.data_ptr(), _ld(A), nrhs, B.data_ptr(), _ld(B),
+                              _stream(stream))
+        abi.check(self.ctx, st, "slqr_solve_r")
+        return B
+
+    def sync(self, stream=None) -> int:
+        """Wait for the stream; return (and clear) the device status word."""
+        return abi.slqr_sync(self.ctx, _stream(stream))
+
+    def lstsq(self, A: torch.Tensor, b: torch.Tensor, stream=None):
+        """Factor A in place, apply Q^T to b in place, back-substitute.
+
+        Returns (x, up): x = b[0:n]; b[n:m] keeps the residual part of Q^T b.
+        """
+        _, up, _ = self.factor(A, stream=stream)
+        self.apply_qt(A, up, b, stream=stream)
+        self.solve_r(A, b, stream=stream)
+        return b[:A.shape[1]], up

@@ -1,0 +1,210 @@
+// ctx.cu -- context, workspace and status handling of the libslqr C ABI.
+#include "slqr_internal.cuh"
+
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+
+namespace slqr {
+
+slqr_status fail(slqr_ctx *ctx, slqr_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return st;
+}
+
+slqr_status check_launch(slqr_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return SLQR_OK;
+}
+
+slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->ws.bytes) return SLQR_OK;
+  bytes = align_up(bytes, (size_t)1 << 20);
+  if (ctx->hbm_budget && bytes > ctx->hbm_budget)
+    return fail(ctx, SLQR_EBUSY, "workspace of %zu bytes exceeds the HBM budget %zu", bytes,
+                ctx->hbm_budget);
+  if (ctx->ws.ptr) {
+    // the old workspace may still be in use by enqueued work
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws.ptr);
+    ctx->ws.ptr = nullptr;
+    ctx->ws.bytes = 0;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SLQR_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->ws.ptr = p;
+  ctx->ws.bytes = bytes;
+  return SLQR_OK;
+}
+
+static cudaEvent_t take_event(slqr_ctx *ctx) {
+  if (!ctx->prof.free_events.empty()) {
+    cudaEvent_t e = ctx->prof.free_events.back();
+    ctx->prof.free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int prof_begin(slqr_ctx *ctx, cudaStream_t stream) {
+  if (!ctx->prof.on) return -1;
+  ProfRecord r;
+  r.start = take_event(ctx);
+  r.stop = take_event(ctx);
+  r.kid = -1;
+  r.flops = 0;
+  if (!r.start || !r.stop) return -1;
+  cudaEventRecord(r.start, stream);
+  ctx->prof.pending.push_back(r);
+  return (int)ctx->prof.pending.size() - 1;
+}
+
+void prof_end(slqr_ctx *ctx, cudaStream_t stream, int slot, int kid, double flops) {
+  ++ctx->launch_count;
+  if (slot < 0) return;
+  ProfRecord &r = ctx->prof.pending[slot];
+  cudaEventRecord(r.stop, stream);
+  r.kid = kid;
+  r.flops = flops;
+}
+
+// Fold finished records into the totals (waits for their stop events).
+static void prof_collect(slqr_ctx *ctx) {
+  for (ProfRecord &r : ctx->prof.pending) {
+    float ms = 0.f;
+    if (r.kid >= 0 && cudaEventSynchronize(r.stop) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      ctx->prof.ms[r.kid] += ms;
+      ctx->prof.launches[r.kid] += 1;
+      ctx->prof.flops[r.kid] += r.flops;
+    }
+    cudaGetLastError();
+    ctx->prof.free_events.push_back(r.start);
+    ctx->prof.free_events.push_back(r.stop);
+  }
+  ctx->prof.pending.clear();
+}
+
+}  // namespace slqr
+
+using namespace slqr;
+
+extern "C" int slqr_profile(slqr_ctx *ctx, int enable) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  prof_collect(ctx);
+  if (enable) {
+    for (int k = 0; k < kNumKernelIds; ++k) {
+      ctx->prof.ms[k] = 0;
+      ctx->prof.launches[k] = 0;
+      ctx->prof.flops[k] = 0;
+    }
+  }
+  ctx->prof.on = enable != 0;
+  return SLQR_OK;
+}
+
+extern "C" slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms,
+                                         long long *launches, double *flops) {
+  if (!ctx || kernel < 0 || kernel >= kNumKernelIds) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  prof_collect(ctx);
+  if (ms) *ms = ctx->prof.ms[kernel];
+  if (launches) *launches = ctx->prof.launches[kernel];
+  if (flops) *flops = ctx->prof.flops[kernel];
+  return SLQR_OK;
+}
+
+extern "C" long long slqr_launch_count(slqr_ctx *ctx) {
+  if (!ctx) return -1;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return ctx->launch_count;
+}
+
+extern "C" slqr_status slqr_create(slqr_ctx **out, int device, size_t hbm_budget_bytes) {
+  if (!out) return SLQR_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return SLQR_EINVAL;
+  }
+  slqr_ctx *ctx = new (std::nothrow) slqr_ctx();
+  if (!ctx) return SLQR_ENOMEM;
+  ctx->device = device;
+  ctx->hbm_budget = hbm_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  int sms = 0, optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return SLQR_ECUDA;
+  }
+  ctx->num_sms = sms;
+  ctx->smem_optin = (size_t)optin;
+  if (init_kernel_attrs(ctx) != SLQR_OK) {
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return SLQR_ECUDA;
+  }
+  *out = ctx;
+  return SLQR_OK;
+}
+
+extern "C" void slqr_destroy(slqr_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->prof.free_events) cudaEventDestroy(e);
+  if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+extern "C" const char *slqr_last_error(slqr_ctx *ctx) {
+  if (!ctx) return "NULL context";
+  return ctx->last_error.c_str();
+}
+
+extern "C" slqr_status slqr_sync(slqr_ctx *ctx, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "stream: %s", cudaGetErrorString(e));
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "status word: %s", cudaGetErrorString(e));
+  if (st != 0) {
+    if (st == SLQR_ERANK) fail(ctx, st, "R has an exact zero on its diagonal");
+    else if (st == SLQR_ETIMEOUT) fail(ctx, st, "a bounded device wait gave up");
+  }
+  return st;
+}

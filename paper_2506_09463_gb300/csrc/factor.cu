@@ -1,0 +1,649 @@
+// factor.cu -- in-place H12 Householder QR on the GPU (FP64), blocked in
+// panels of NB reflectors with a compact-WY trailing update.
+//
+// What it computes is Alg. 2 of the paper (Section 3): for each pivot k the
+// kernel update_pivot_row builds reflector k from column k (its pivot entry
+// `up` kept apart, Task 1 / Alg. 3), then update_trailing_non_pivot_row
+// applies it to every later column.  The paper runs those two kernels as a
+// DAG of CPU tasks; here the same arithmetic is regrouped for the GPU:
+//
+//  * panel kernel (cooperative, one CTA per slice of rows): for each of the NB
+//    columns of the panel it does update_pivot_row (scaled norm, sign rule,
+//    up) and update_trailing_non_pivot_row on the remaining panel columns.
+//    One grid-wide reduction per column carries the partial column norm, the
+//    dot products of the column tail with every other panel column, and the
+//    pivot row.  The same dot products give the strict upper triangle of the
+//    Gram matrix G = V^T V of the panel, so the compact-WY factor needs no
+//    extra pass.
+//  * trailing update of the columns right of the panel by all NB reflectors
+//    at once: X <- (H_0 ... H_{NB-1})^T X = X - V T^T (V^T X), with
+//    T^{-1} = striu(G) + diag(-b) (the identity T^{-1} + T^{-T} = V^T V of
+//    the compact-WY form, with H_j = I - tau_j v_j v_j^T, tau_j = -1/b_j):
+//      gemm_vtx   W_s = V_s^T X_s on row slices s (partials),
+//      tw         W' = T^T W by forward substitution with striu(G), tau,
+//      gemm_upd   X -= V W'.
+//    All three run on the FP64 pipe (DFMA); on GB300 FP64 DMMA issues slower
+//    than DFMA, so these are register-tiled DFMA kernels.
+//
+// Rounding differs from the sequential order (blocked sums, power-of-two
+// scaled norms), so results agree with the sequential H12 to a tolerance,
+// not bitwise.
+#include "slqr_internal.cuh"
+
+#include <cstdio>
+#include <cstdarg>
+#include <algorithm>
+
+namespace slqr {
+
+// --------------------------------------------------------------------------
+// small device helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Scaled sum of squares: value = 2^(2E) * S.  Entries are scaled by exact
+// powers of two, so neither overflow nor underflow occurs for finite input.
+constexpr int kNoExp = -4000;
+
+__device__ __forceinline__ void ssq_add(int &E, double &S, double x) {
+  if (x != 0.0) {
+    int ex = ilogb(x);
+    if (ex > E) {
+      S = ldexp(S, 2 * (E - ex));
+      E = ex;
+    }
+    double y = ldexp(x, -E);
+    S = fma(y, y, S);
+  }
+}
+
+__device__ __forceinline__ void ssq_merge(int &E, double &S, int E2, double S2) {
+  if (S2 == 0.0) return;
+  if (S == 0.0) { E = E2; S = S2; return; }
+  if (E2 > E) {
+    S = ldexp(S, 2 * (E - E2)) + S2;
+    E = E2;
+  } else {
+    S = S + ldexp(S2, 2 * (E2 - E));
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void record_status(int *status, int code) {
+  atomicCAS(status, kStatusOk, code);
+}
+
+// --------------------------------------------------------------------------
+// panel kernel
+// --------------------------------------------------------------------------
+struct PanelParams {
+  double *A;
+  double *up;          // global up array (n doubles)
+  double *wy;          // this panel's compact-WY block (Vtop | G | tau)
+  double *rec;         // 2 * (NB+2) * P doubles, layout [buf][entry][cta]
+  double *prow;        // 2 * NB doubles
+  unsigned *bar;       // monotonic arrival counter
+  int *status;
+  int m, lda, k0, nbw;
+  int P, R;            // CTAs, rows per CTA
+  unsigned bar_base;   // counter value when this panel starts
+};
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads)
+panel_kernel(PanelParams p) {
+  extern __shared__ double smem[];
+  constexpr int NW = kThreads / 32;
+  constexpr int CPW = (NB + NW - 1) / NW;     // columns per warp
+  constexpr int RECLEN = NB + 2;
+  double *Ps = smem;                          // [NB][R] column-major panel slice
+  __shared__ double s_D[NB];                  // reduced dot products
+  __shared__ double s_sig[NB];                // sigma per column
+  __shared__ double s_up[NB];
+  __shared__ double s_norm;
+  __shared__ int s_ok;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cta = blockIdx.x;
+  const int R = p.R;
+  const int row0 = p.k0 + cta * R;                 // first global row of this slice
+  const int RO = min(R, p.m - row0);               // rows owned
+  const int nbw = p.nbw;
+  double *A = p.A;
+  const int lda = p.lda;
+
+  // load the slice of the panel
+  for (int idx = tid; idx < nbw * R; idx += kThreads) {
+    int c = idx / R, r = idx - c * R;
+    Ps[c * R + r] = (r < RO) ? A[SLQR_IDX(row0 + r, p.k0 + c, lda)] : 0.0;
+  }
+  double *G = p.wy + (size_t)NB * NB;
+  double *tau = p.wy + 2 * (size_t)NB * NB;
+  __syncthreads();
+
+  for (int j = 0; j < nbw; ++j) {
+    const int buf = j & 1;
+    double *rec = p.rec + (size_t)buf * RECLEN * p.P;
+    double *prow = p.prow + buf * NB;
+    // rows strictly below the pivot (tail) and from the pivot on (norm)
+    const int r_tail = (cta == 0) ? j + 1 : 0;
+    const double *x = Ps + j * R;
+
+    // ---- phase 1: local partials ---------------------------------------
+    {
+      double acc[CPW];
+#pragma unroll
+      for (int t = 0; t < CPW; ++t) acc[t] = 0.0;
+      int E = kNoExp;
+      double S = 0.0;
+      const bool norm_warp = (warp == (j % NW));
+      for (int r = r_tail + lane; r < RO; r += 32) {
+        double xv = x[r];
+#pragma unroll
+        for (int t = 0; t < CPW; ++t) {
+          int c = warp + t * NW;
+          if (c < nbw && c != j) acc[t] = fma(xv, Ps[c * R + r], acc[t]);
+        }
+        if (norm_warp) ssq_add(E, S, xv);
+      }
+      if (norm_warp && cta == 0 && lane == 0) ssq_add(E, S, x[j]);  // pivot entry
+#pragma unroll
+      for (int t = 0; t < CPW; ++t) {
+        int c = warp + t * NW;
+        double v = warp_sum(acc[t]);
+        if (lane == 0 && c < nbw && c != j) rec[(size_t)(2 + c) * p.P + cta] = v;
+      }
+      if (norm_warp) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          int E2 = __shfl_xor_sync(0xffffffffu, E, o);
+          double S2 = __shfl_xor_sync(0xffffffffu, S, o);
+          ssq_merge(E, S, E2, S2);
+        }
+        if (lane == 0) {
+          rec[0 * (size_t)p.P + cta] = (double)E;
+          rec[1 * (size_t)p.P + cta] = S;
+        }
+      }
+      if (cta == 0 && tid < nbw) prow[tid] = Ps[tid * R + j];
+    }
+
+    // ---- grid barrier -----------------------------------------------------
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(p.bar, 1u);
+      const unsigned target = p.bar_base + (unsigned)(j + 1) * (unsigned)p.P;
+      unsigned it = 0;
+      int ok = 1;
+      while (ld_acquire_u32(p.bar) < target) {
+        if (++it > kSpinLimit) { ok = 0; break; }
+        if (it > 256) __nanosleep(64);
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) {
+      if (tid == 0) record_status(p.status, SLQR_ETIMEOUT);
+      return;
+    }
+
+    // ---- phase 2: every CTA reduces the partials in the same fixed order ---
+    for (int e = warp; e < nbw + 1; e += NW) {
+      // e == 0: the norm pair; e >= 1: dot with panel column c = e - 1
+      if (e == 0) {
+        int E = kNoExp;
+        double S = 0.0;
+        for (int q = lane; q < p.P; q += 32) {
+          double Eq = __ldcg(rec + q), Sq = __ldcg(rec + p.P + q);
+          ssq_merge(E, S, (int)Eq, Sq);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          int E2 = __shfl_xor_sync(0xffffffffu, E, o);
+          double S2 = __shfl_xor_sync(0xffffffffu, S, o);
+          ssq_merge(E, S, E2, S2);
+        }
+        if (lane == 0) s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
+      } else {
+        int c = e - 1;
+        if (c == j) continue;
+        double v = 0.0;
+        for (int q = lane; q < p.P; q += 32) v += __ldcg(rec + (size_t)(2 + c) * p.P + q);
+        v = warp_sum(v);
+        if (lane == 0) s_D[c] = v;
+      }
+    }
+    __syncthreads();
+
+    // pivot quantities (every thread computes the same values)
+    const double s = s_norm;
+    const double x0 = __ldcg(prow + j);
+    double cl = 0.0, upk = 0.0, bk = 0.0, tk = 0.0;
+    const bool defined = (s != 0.0);
+    if (defined) {
+      cl = (x0 > 0.0) ? -s : s;
+      upk = x0 - cl;
+      bk = upk * cl;
+      tk = -1.0 / bk;
+    }
+    if (tid < nbw) {
+      int c = tid;
+      double pr = __ldcg(prow + c);
+      if (c > j) {
+        s_sig[c] = defined ? (upk * pr + s_D[c]) / bk : 0.0;
+      } else if (c < j && cta == 0) {
+        // G[c, j] = v_c^T v_j = v_c[k] * up_j + sum_{r > k} v_c[r] x_r
+        G[c + j * NB] = pr * upk + s_D[c];
+      }
+    }
+    if (cta == 0 && tid == 0) {
+      s_up[j] = upk;
+      p.up[p.k0 + j] = upk;
+      tau[j] = tk;
+    }
+    __syncthreads();
+
+    // ---- phase 3: apply the reflector to the remaining panel columns -------
+    if (defined) {
+      for (int t = 0; t < CPW; ++t) {
+        int c = warp + t * NW;
+        if (c > j && c < nbw) {
+          const double sg = s_sig[c];
+          double *col = Ps + c * R;
+          for (int r = r_tail + lane; r < RO; r += 32) col[r] = fma(sg, x[r], col[r]);
+        }
+      }
+      if (cta == 0) {
+        int c = tid;
+        if (c > j && c < nbw) Ps[c * R + j] = fma(s_sig[c], upk, Ps[c * R + j]);
+        if (tid == 0) Ps[j * R + j] = cl;
+      }
+    }
+    __syncthreads();
+  }
+
+  // write the slice back
+  for (int idx = tid; idx < nbw * R; idx += kThreads) {
+    int c = idx / R, r = idx - c * R;
+    if (r < RO) A[SLQR_IDX(row0 + r, p.k0 + c, lda)] = Ps[c * R + r];
+  }
+  if (cta == 0) {
+    // Vtop (ld NB): zero above the diagonal, up on it, tails below
+    double *Vtop = p.wy;
+    for (int idx = tid; idx < NB * NB; idx += kThreads) {
+      int c = idx / NB, r = idx - c * NB;
+      double v = 0.0;
+      if (c < nbw && r < nbw) {
+        if (r == c) v = s_up[c];
+        else if (r > c) v = Ps[c * R + r];
+      }
+      Vtop[idx] = v;
+      if (r >= c) G[idx] = 0.0;                 // keep only the strict upper part
+      if (c >= nbw && r < c) G[idx] = 0.0;
+    }
+    for (int c = nbw + tid; c < NB; c += kThreads) tau[c] = 0.0;
+  }
+}
+
+// --------------------------------------------------------------------------
+// tiled FP64 kernels of the trailing update
+// --------------------------------------------------------------------------
+// V(i, a) for the panel at row offset k0: rows i < nbw from Vtop, the rest
+// straight from the reflector tails in A.  Columns a >= nbw read as 0.
+__device__ __forceinline__ double v_at(const double *A, int lda, const double *Vtop, int NB,
+                                       int k0, int nbw, int i, int a) {
+  if (a >= nbw) return 0.0;
+  if (i < nbw) return Vtop[i + a * NB];
+  return A[SLQR_IDX(k0 + i, k0 + a, lda)];
+}
+
+constexpr int kBK = 32;   // rows per chunk of the V^T X reduction
+constexpr int kBN = 64;   // columns per tile
+constexpr int kBM = 64;   // rows per tile of the update
+
+// W_part[s][c][a] = sum_{i in slice s} V(i, a) X(i, c)
+// grid: (ceil(N / kBN), S); rows of slice s: [s*RS, min((s+1)*RS, M))
+template <int NB, bool X_IS_V>
+__global__ void __launch_bounds__(kThreads)
+gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
+                int nbw, int M, const double *__restrict__ X, int ldx, int N, int RS,
+                double *__restrict__ Wp) {
+  __shared__ double Vs[NB][kBK + 1];
+  __shared__ double Xs[kBN][kBK + 1];
+  constexpr int TP = NB / 16;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int c0 = blockIdx.x * kBN;
+  const int s = blockIdx.y;
+  const int i_begin = s * RS, i_end = min(M, i_begin + RS);
+  double acc[TP][4];
+#pragma unroll
+  for (int a = 0; a < TP; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+
+  for (int i0 = i_begin; i0 < i_end; i0 += kBK) {
+    for (int idx = tid; idx < NB * kBK; idx += kThreads) {
+      int a = idx / kBK, ii = idx - a * kBK;
+      int i = i0 + ii;
+      Vs[a][ii] = (i < i_end) ? v_at(A, lda, Vtop, NB, k0, nbw, i, a) : 0.0;
+    }
+    for (int idx = tid; idx < kBN * kBK; idx += kThreads) {
+      int c = idx / kBK, ii = idx - c * kBK;
+      int i = i0 + ii, cc = c0 + c;
+      double v = 0.0;
+      if (i < i_end && cc < N) {
+        if (X_IS_V) v = v_at(A, lda, Vtop, NB, k0, nbw, i, cc);
+        else v = X[SLQR_IDX(k0 + i, cc, ldx)];
+      }
+      Xs[c][ii] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kBK; ++kk) {
+      double va[TP], xc[4];
+#pragma unroll
+      for (int a = 0; a < TP; ++a) va[a] = Vs[tx + 16 * a][kk];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xc[q] = Xs[ty + 16 * q][kk];
+#pragma unroll
+      for (int a = 0; a < TP; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = fma(va[a], xc[q], acc[a][q]);
+    }
+    __syncthreads();
+  }
+  double *out = Wp + (size_t)s * N * NB;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int cc = c0 + ty + 16 * q;
+    if (cc < N) {
+#pragma unroll
+      for (int a = 0; a < TP; ++a) out[(size_t)cc * NB + tx + 16 * a] = acc[a][q];
+    }
+  }
+}
+
+// W'[a][c] = (T^T W)[a][c]: reduce the S partials of column c, then forward
+// substitution  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q).
+template <int NB>
+__global__ void __launch_bounds__(64)
+tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
+          double *__restrict__ Wt) {
+  __shared__ double w[NB][65];
+  const int tid = threadIdx.x;
+  const double *G = wy + (size_t)NB * NB;
+  const double *tau = wy + 2 * (size_t)NB * NB;
+  const int c = blockIdx.x * 64 + tid;
+  if (c >= N) return;
+  for (int a = 0; a < nbw; ++a) {
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += Wp[((size_t)s * N + c) * NB + a];
+    w[a][tid] = v;
+  }
+  for (int j = 0; j < nbw; ++j) {
+    double t = w[j][tid];
+    for (int q = 0; q < j; ++q) t = fma(-__ldg(G + q + j * NB), w[q][tid], t);
+    w[j][tid] = __ldg(tau + j) * t;
+  }
+  for (int a = 0; a < NB; ++a) Wt[(size_t)a * N + c] = (a < nbw) ? w[a][tid] : 0.0;
+}
+
+// X(i, c) -= sum_a V(i, a) W'[a][c] on a kBM x kBN tile; grid (ceil(M/kBM), ceil(N/kBN))
+template <int NB>
+__global__ void __launch_bounds__(kThreads)
+gemm_upd_kernel(const double *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
+                int nbw, int M, double *__restrict__ X, int ldx, int N,
+                const double *__restrict__ Wt) {
+  extern __shared__ double smem[];
+  double *Vs = smem;                 // [NB][kBM]
+  double *Ws = smem + NB * kBM;      // [NB][kBN]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
+  for (int idx = tid; idx < NB * kBM; idx += kThreads) {
+    int a = idx / kBM, ii = idx - a * kBM;
+    int i = i0 + ii;
+    Vs[idx] = (i < M) ? v_at(A, lda, Vtop, NB, k0, nbw, i, a) : 0.0;
+  }
+  for (int idx = tid; idx < NB * kBN; idx += kThreads) {
+    int a = idx / kBN, cc = idx - a * kBN;
+    Ws[idx] = (c0 + cc < N) ? Wt[(size_t)a * N + c0 + cc] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[pp][q] = 0.0;
+#pragma unroll 4
+  for (int a = 0; a < nbw; ++a) {
+    double v[4], ww[4];
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp) v[pp] = Vs[a * kBM + tx + 16 * pp];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ww[q] = Ws[a * kBN + ty + 16 * q];
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[pp][q] = fma(v[pp], ww[q], acc[pp][q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int cc = c0 + ty + 16 * q;
+    if (cc >= N) continue;
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp) {
+      int i = i0 + tx + 16 * pp;
+      if (i < M) {
+        double *dst = X + SLQR_IDX(k0 + i, cc, ldx);
+        *dst -= acc[pp][q];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+int panel_width(int m, int n) {
+  (void)m;
+  return n <= 256 ? 32 : 64;
+}
+
+static int split_count(int M, int ntiles, int num_sms) {
+  const int slots = 3 * num_sms;
+  int S = (4 * slots + ntiles - 1) / ntiles;
+  int maxS = std::max(1, M / 64);
+  return std::max(1, std::min(S, maxS));
+}
+
+// Upper bound of the partial-sum workspace over every trailing width N' <= N:
+// S * N' <= (4 * slots / ntiles' + 1) * ntiles' * kBN <= (4 * slots + ntiles) * kBN.
+size_t panel_update_work_doubles(int m, int N, int nb, int num_sms) {
+  (void)m;
+  size_t ntiles = (size_t)(N + kBN - 1) / kBN;
+  size_t slots = 3 * (size_t)num_sms;
+  return (4 * slots + ntiles + 1) * kBN * nb + (size_t)nb * N;
+}
+
+template <int NB>
+static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const double *A,
+                                     int lda, const double *wy_panel, double *X, int ldx, int N,
+                                     double *work, size_t work_doubles, cudaStream_t stream) {
+  if (N <= 0) return SLQR_OK;
+  const int M = m - k0;
+  const int ntiles = (N + kBN - 1) / kBN;
+  const int S = split_count(M, ntiles, ctx->num_sms);
+  int RS = (M + S - 1) / S;
+  RS = (RS + kBK - 1) / kBK * kBK;
+  const int Seff = (M + RS - 1) / RS;
+  if ((size_t)Seff * N * NB + (size_t)NB * N > work_doubles)
+    return fail(ctx, SLQR_ENOMEM, "internal: trailing-update workspace too small");
+  double *Wp = work;
+  double *Wt = work + (size_t)Seff * N * NB;
+  const double *Vtop = wy_panel;
+  const double gemm_flops = 2.0 * M * nbw * (double)N;
+  int slot = prof_begin(ctx, stream);
+  gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
+      A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
+  prof_end(ctx, stream, slot, kVtx, gemm_flops);
+  slot = prof_begin(ctx, stream);
+  tw_kernel<NB><<<(N + 63) / 64, 64, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
+  size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
+  slot = prof_begin(ctx, stream);
+  gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+      A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+  prof_end(ctx, stream, slot, kUpd, gemm_flops);
+  return check_launch(ctx, "trailing update");
+}
+
+slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const double *A,
+                               int lda, const double *wy_panel, double *X, int ldx, int N,
+                               double *work, size_t work_doubles, cudaStream_t stream) {
+  if (nb == 32)
+    return panel_update_impl<32>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
+                                 work_doubles, stream);
+  return panel_update_impl<64>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
+                               work_doubles, stream);
+}
+
+// Opt the kernels that use more than 48 KB of dynamic shared memory in; run
+// once per device (slqr_create) with that device current.
+slqr_status init_kernel_attrs(slqr_ctx *ctx) {
+  const int max_smem = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(panel_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             64 * (kBM + kBN) * 8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             32 * (kBM + kBN) * 8);
+  if (e != cudaSuccess)
+    return fail(ctx, SLQR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  return SLQR_OK;
+}
+
+// rows per CTA of the panel kernel
+static int panel_rows_per_cta(int M, int nbw, int num_sms) {
+  int R = (M + num_sms - 1) / num_sms;
+  R = std::max(R, nbw);
+  R = std::max(R, 32);
+  return R;
+}
+
+static int max_rows_per_cta(int nb) { return (200 * 1024) / (nb * (int)sizeof(double)); }
+
+template <int NB>
+static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
+                               double *wy, cudaStream_t stream) {
+  const int K = num_reflectors(m, n);
+  const int np = num_panels(K, NB);
+  // workspace: [bar (256 B)] [records] [prow] [wy if none given] [trailing work]
+  const int Pmax = ctx->num_sms;
+  const size_t rec_doubles = 2 * (size_t)(NB + 2) * Pmax;
+  const size_t prow_doubles = 2 * (size_t)NB;
+  const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
+  const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms);
+  const size_t bytes = 256 + (rec_doubles + prow_doubles + wy_doubles + work_doubles) * 8;
+  slqr_status st = ensure_workspace(ctx, bytes);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws.ptr;
+  unsigned *bar = (unsigned *)base;
+  double *rec = (double *)(base + 256);
+  double *prow = rec + rec_doubles;
+  double *wy_store = wy ? wy : prow + prow_doubles;
+  double *work = prow + prow_doubles + wy_doubles;
+
+  cudaError_t e = cudaMemsetAsync(bar, 0, 256, stream);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  // up[k] for k >= K is 0 (no reflector)
+  if (n > K) {
+    e = cudaMemsetAsync(up + K, 0, sizeof(double) * (n - K), stream);
+    if (e != cudaSuccess)
+      return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+
+  unsigned bar_base = 0;
+  for (int pnl = 0; pnl < np; ++pnl) {
+    const int k0 = pnl * NB;
+    const int nbw = std::min(NB, K - k0);
+    const int M = m - k0;
+    const int R = panel_rows_per_cta(M, nbw, Pmax);
+    if (R > max_rows_per_cta(NB))
+      return fail(ctx, SLQR_EINVAL, "m = %d is too large for the shared-memory panel", m);
+    const int P = (M + R - 1) / R;
+    double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
+    PanelParams pp;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.prow = prow; pp.bar = bar;
+    pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
+    pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    void *args[] = {&pp};
+    size_t smem = (size_t)NB * R * sizeof(double);
+    // algorithmic flops of the panel: per column j a norm over M-j entries and,
+    // for each later panel column, a dot and an axpy over M-j entries
+    double pflops = 0.0;
+    for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
+    int slot = prof_begin(ctx, stream);
+    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P), dim3(kThreads), args,
+                                    smem, stream);
+    prof_end(ctx, stream, slot, kPanel, pflops);
+    if (e != cudaSuccess)
+      return fail(ctx, SLQR_ECUDA, "panel launch (P=%d, smem=%zu): %s", P, smem,
+                  cudaGetErrorString(e));
+    bar_base += (unsigned)P * (unsigned)nbw;
+    // trailing columns [k0 + nbw, n)
+    const int N = n - (k0 + nbw);
+    if (N > 0) {
+      st = panel_update_impl<NB>(ctx, m, k0, nbw, A, lda, wy_panel,
+                                 A + (size_t)(k0 + nbw) * lda, lda, N, work, work_doubles,
+                                 stream);
+      if (st != SLQR_OK) return st;
+    }
+  }
+  return check_launch(ctx, "factor");
+}
+
+}  // namespace slqr
+
+using namespace slqr;
+
+extern "C" int slqr_panel_width(int m, int n) { return panel_width(m, n); }
+
+extern "C" size_t slqr_wy_size(int m, int n) {
+  if (m <= 0 || n <= 0) return 0;
+  int nb = panel_width(m, n);
+  int K = num_reflectors(m, n);
+  return wy_panel_doubles(nb) * (size_t)num_panels(K, nb) * sizeof(double);
+}
+
+extern "C" int slqr_max_rows(void) { return 49152; }
+
+extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
+                                   double *wy, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (m < 0 || n < 0 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 0 (m=%d n=%d)", m, n);
+  if (n == 0) return SLQR_OK;
+  if (lda < std::max(1, m)) return fail(ctx, SLQR_EINVAL, "lda=%d < m=%d", lda, m);
+  if (!A || !up) return fail(ctx, SLQR_EINVAL, "NULL A or up");
+  if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (panel_width(m, n) == 32) return factor_impl<32>(ctx, m, n, A, lda, up, wy, s);
+  return factor_impl<64>(ctx, m, n, A, lda, up, wy, s);
+}

@@ -1,0 +1,119 @@
+// slqr_internal.cuh -- shared declarations of the libslqr CUDA sources.
+//
+// Layout conventions: matrices are FP64, column-major, element (i, j) of a
+// matrix with leading dimension ld at p[i + j*ld].  The factorization runs in
+// panels of NB reflectors (compact-WY form, see factor.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <mutex>
+#include <vector>
+
+#include "../../include/slqr.h"
+
+#define SLQR_IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+namespace slqr {
+
+constexpr int kThreads = 256;          // threads per CTA of the tiled kernels
+constexpr int kMaxPanelRowsPerCta = 384;  // rows of a panel one CTA holds in smem (NB=64)
+
+// Upper bound on spin iterations of a device-side wait (each iteration sleeps
+// ~100 ns), after which the kernel records SLQR_ETIMEOUT and returns.
+constexpr unsigned kSpinLimit = 1u << 24;
+
+// Device status word codes (same values as the C ABI).
+constexpr int kStatusOk = 0;
+
+struct Workspace {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Kernel families timed by the optional profiler (slqr_profile).
+enum KernelId { kPanel = 0, kVtx = 1, kTw = 2, kUpd = 3, kWyRebuild = 4, kTrsm = 5, kNumKernelIds = 6 };
+
+struct ProfRecord {
+  cudaEvent_t start, stop;
+  int kid;
+  double flops;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRecord> pending;
+  std::vector<cudaEvent_t> free_events;
+  double ms[kNumKernelIds] = {0};
+  long long launches[kNumKernelIds] = {0};
+  double flops[kNumKernelIds] = {0};
+};
+
+}  // namespace slqr
+
+struct slqr_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t hbm_budget = 0;
+  size_t smem_optin = 0;
+  int *d_status = nullptr;             // device status word
+  slqr::Workspace ws;                  // grown on demand
+  slqr::Profiler prof;                 // optional CUDA-event timing per kernel family
+  long long launch_count = 0;          // kernels launched by this context
+  std::string last_error;
+  std::mutex mu;
+};
+
+namespace slqr {
+
+// Record an error message in the context and return the status.
+slqr_status fail(slqr_ctx *ctx, slqr_status st, const char *fmt, ...);
+
+// Make sure the workspace holds at least `bytes`; returns SLQR_OK or an error.
+slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes);
+
+// Check the last launch; returns SLQR_OK or SLQR_ECUDA with the message set.
+slqr_status check_launch(slqr_ctx *ctx, const char *what);
+
+// Profiling around one launch: begin returns a slot (or -1 when off); end
+// records the stop event and the algorithmic flops of that launch.  Both also
+// count the launch.
+int prof_begin(slqr_ctx *ctx, cudaStream_t stream);
+void prof_end(slqr_ctx *ctx, cudaStream_t stream, int slot, int kid, double flops);
+
+// Opt kernels into large dynamic shared memory (once per device).
+slqr_status init_kernel_attrs(slqr_ctx *ctx);
+
+// Panel width used for an m x n factorization.
+int panel_width(int m, int n);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// --------------------------------------------------------------------------
+// Compact-WY store: per panel p, at offset p * wy_panel_doubles(nb):
+//   [0, nb*nb)          Vtop: top nb x nb block of V (column-major, ld nb):
+//                       0 above the diagonal, up on it, reflector tails below
+//   [nb*nb, 2*nb*nb)    G: strict upper triangle of V^T V (column-major, ld nb)
+//   [2*nb*nb, +nb)      tau_j = -1/b_j (0 for a skipped or absent reflector)
+// --------------------------------------------------------------------------
+__host__ __device__ inline size_t wy_panel_doubles(int nb) { return 2 * (size_t)nb * nb + nb; }
+__host__ __device__ inline int num_panels(int K, int nb) { return (K + nb - 1) / nb; }
+
+// Number of reflectors min(m-1, n).
+__host__ __device__ inline int num_reflectors(int m, int n) {
+  int k = m - 1 < n ? m - 1 : n;
+  return k < 0 ? 0 : k;
+}
+
+// --- launchers (defined in factor.cu / apply.cu / solve.cu) -------------
+// Trailing update of columns [c0, c0+N) of the matrix X (rows [k0, m), leading
+// dimension ldx) by the panel (V from A/Vtop, G, tau) at offset k0 of width nbw.
+slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
+                               const double *A, int lda, const double *wy_panel,
+                               double *X, int ldx, int N, double *work, size_t work_doubles,
+                               cudaStream_t stream);
+size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
+
+}  // namespace slqr

@@ -1,0 +1,72 @@
+"""CPU checks of the boundary: libslqr.so builds for sm_103a, loads, and
+exports every entry point that include/*.h declares (no compute call: there is
+no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(slqr_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_09463_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ["slqr_create", "slqr_destroy", "slqr_factor", "slqr_apply_qt",
+                     "slqr_solve_r", "slqr_sync", "slqr_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_2506_09463_gb300 import abi
+    bound = {name for name, _, _ in abi.SIGNATURES}
+    assert set(declared_symbols()) <= bound | {"slqr_create"}
+
+
+def test_host_only_queries(lib):
+    from paper_2506_09463_gb300 import abi
+    assert abi.slqr_panel_width(256, 128) in (32, 64)
+    nb = abi.slqr_panel_width(8192, 8192)
+    K = 8191
+    panels = (K + nb - 1) // nb
+    assert abi.slqr_wy_size(8192, 8192) == panels * (2 * nb * nb + nb) * 8
+    assert abi.slqr_wy_size(0, 0) == 0
+    assert abi.slqr_max_rows() >= 16384
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2506_09463_gb300 import abi
+    with pytest.raises(abi.SlqrError):
+        abi.slqr_create(0, 0)
+
+
+def test_null_context_is_rejected(lib):
+    from paper_2506_09463_gb300 import abi
+    assert abi.slqr_factor(None, 4, 2, None, 4, None, None, None) == abi.SLQR_EINVAL
+    assert abi.slqr_solve_r(None, 2, None, 2, 1, None, 2, None) == abi.SLQR_EINVAL
