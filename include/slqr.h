@@ -150,6 +150,39 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
                          double *B, int ldb, void *stream);
 
 /*
+ * slqr_factor_noalloc -- the factorization of slqr_factor for callers that
+ * must not allocate device memory.  The paper has no counterpart: this entry
+ * point exists for embedding.  Some callers cannot call cudaMalloc: a host
+ * framework that has reserved all device memory for its own pool, or a
+ * latency-bound loop in which cudaMalloc / cudaFree (which may synchronise the
+ * whole device) are forbidden.  This call needs no context and allocates
+ * nothing: the caller passes the inputs and outputs, and every other buffer
+ * the factorization needs (barrier counter, reduction records, compact-WY
+ * store when wy is NULL, partial sums) lives in one fixed array of about
+ * 5.3 MB that the library declares in device memory.  Every GPU that loads
+ * libslqr holds that array until the process exits.
+ *   m, n     m >= n >= 0, m <= slqr_noalloc_max_rows() (8192),
+ *            n <= slqr_noalloc_max_cols() (1024); larger sizes return
+ *            SLQR_EINVAL and enqueue nothing
+ *   A, lda, up, wy   as for slqr_factor (wy may be NULL)
+ *   status   device int, or NULL: receives SLQR_ETIMEOUT if a bounded device
+ *            wait gives up; the caller clears it before the call
+ *   stream   cudaStream_t as void*; the work is enqueued on it
+ * It runs on the device that is current for the calling thread.  The first
+ * call on a device does a one-time set-up there (it looks up the device
+ * address of the array and sets kernel attributes); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents: each call clears the parts that must start at
+ * zero.  Calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on the array and give wrong results: order them.
+ * Errors: SLQR_EINVAL, SLQR_ECUDA.
+ */
+slqr_status slqr_factor_noalloc(int m, int n, double *A, int lda, double *up, double *wy,
+                                int *status, void *stream);
+int slqr_noalloc_max_rows(void);
+int slqr_noalloc_max_cols(void);
+
+/*
  * Optional CUDA-event profiler (tracing aid; no counterpart in the paper).
  * slqr_profile(ctx, 1) clears the totals and starts recording a pair of CUDA
  * events on the launching stream around every kernel the context launches;

@@ -51,6 +51,9 @@ SIGNATURES = [
     ("slqr_profile_read", _c_int, [_vp, _c_int, ctypes.POINTER(_dbl),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_dbl)]),
     ("slqr_launch_count", ctypes.c_longlong, [_vp]),
+    ("slqr_factor_noalloc", _c_int, [_c_int, _c_int, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    ("slqr_noalloc_max_rows", _c_int, []),
+    ("slqr_noalloc_max_cols", _c_int, []),
 ]
 
 KERNEL_PANEL, KERNEL_VTX, KERNEL_TW, KERNEL_UPD, KERNEL_WY_REBUILD, KERNEL_TRSM = range(6)
@@ -137,6 +140,19 @@ def slqr_profile_read(ctx: int, kernel: int):
 
 def slqr_launch_count(ctx: int) -> int:
     return _lib.slqr_launch_count(ctx)
+
+
+def slqr_factor_noalloc(m, n, A, lda, up, wy, status, stream) -> int:
+    """Allocation-free factorization (no context; fixed-size library scratch)."""
+    return _lib.slqr_factor_noalloc(m, n, A, lda, up, wy, status, stream)
+
+
+def slqr_noalloc_max_rows() -> int:
+    return _lib.slqr_noalloc_max_rows()
+
+
+def slqr_noalloc_max_cols() -> int:
+    return _lib.slqr_noalloc_max_cols()
 
 
 def check(ctx: int, status: int, what: str) -> None:

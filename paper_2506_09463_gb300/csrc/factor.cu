@@ -647,3 +647,174 @@ extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int l
   if (panel_width(m, n) == 32) return factor_impl<32>(ctx, m, n, A, lda, up, wy, s);
   return factor_impl<64>(ctx, m, n, A, lda, up, wy, s);
 }
+
+// ==========================================================================
+// slqr_factor_noalloc: the same factorization for callers that cannot
+// allocate device memory.  Its scratch (barrier counter, reduction records,
+// compact-WY store, partial sums) lives in one file-scope __device__ array of
+// fixed size instead of a context workspace.  It has no counterpart in the
+// paper.
+// ==========================================================================
+namespace slqr {
+
+constexpr int kNoAllocMaxRows = 8192;
+constexpr int kNoAllocMaxCols = 1024;
+constexpr int kNoAllocMaxSms = 256;
+constexpr int kNoAllocMaxDevices = 64;
+constexpr size_t kNoAllocHeadDoubles = 32;                       // 256 B: counter + status
+constexpr size_t kNoAllocRecDoubles = 2 * (64 + 2) * (size_t)kNoAllocMaxSms;
+constexpr size_t kNoAllocProwDoubles = 2 * 64;
+constexpr size_t kNoAllocWyDoubles = (kNoAllocMaxCols / 64) * (2 * 64 * 64 + 64);
+constexpr size_t kNoAllocWorkDoubles = 512 * 1024;
+constexpr size_t kNoAllocScratchDoubles = kNoAllocHeadDoubles + kNoAllocRecDoubles +
+                                          kNoAllocProwDoubles + kNoAllocWyDoubles +
+                                          kNoAllocWorkDoubles;
+
+// About 5.3 MB on every device that loads the library, held until exit.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[kNoAllocMaxDevices];
+static int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the device address of the
+// scratch array (its name in host code is only a host-side stand-in) and the
+// shared-memory opt-in of the kernels.
+static slqr_status noalloc_setup(int dev, double **ptr, int *sms) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev]) {
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return SLQR_OK;
+  }
+  double *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return SLQR_ECUDA;
+  }
+  int n_sms = 0;
+  e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess || n_sms <= 0 || n_sms > kNoAllocMaxSms) {
+    cudaGetLastError();
+    return SLQR_ECUDA;
+  }
+  const int max_smem = 200 * 1024;
+  e = cudaFuncSetAttribute(panel_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             64 * (kBM + kBN) * 8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             32 * (kBM + kBN) * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SLQR_ECUDA;
+  }
+  g_noalloc_ptr[dev] = p;
+  g_noalloc_sms[dev] = n_sms;
+  *ptr = p;
+  *sms = n_sms;
+  return SLQR_OK;
+}
+
+// Trailing update with the row-split count capped so the partial sums fit
+// the fixed scratch.
+template <int NB>
+static slqr_status noalloc_update(int num_sms, int m, int k0, int nbw, const double *A, int lda,
+                                  const double *wy_panel, double *X, int ldx, int N,
+                                  double *work, size_t work_doubles, cudaStream_t stream) {
+  const int M = m - k0;
+  const int ntiles = (N + kBN - 1) / kBN;
+  int S = split_count(M, ntiles, num_sms);
+  const long long maxS = ((long long)(work_doubles / NB) - N) / N;
+  if (maxS < 1) return SLQR_EINVAL;
+  S = (int)std::max(1LL, std::min((long long)S, maxS));
+  int RS = (M + S - 1) / S;
+  RS = (RS + kBK - 1) / kBK * kBK;
+  const int Seff = (M + RS - 1) / RS;
+  if ((size_t)Seff * N * NB + (size_t)NB * N > work_doubles) return SLQR_EINVAL;
+  double *Wp = work;
+  double *Wt = work + (size_t)Seff * N * NB;
+  gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
+      A, lda, wy_panel, k0, nbw, M, X, ldx, N, RS, Wp);
+  tw_kernel<NB><<<(N + 63) / 64, 64, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
+  gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+      A, lda, wy_panel, k0, nbw, M, X, ldx, N, Wt);
+  return cudaGetLastError() == cudaSuccess ? SLQR_OK : SLQR_ECUDA;
+}
+
+template <int NB>
+static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int n, double *A,
+                                       int lda, double *up, double *wy, int *status,
+                                       cudaStream_t stream) {
+  const int K = num_reflectors(m, n);
+  const int np = num_panels(K, NB);
+  unsigned *bar = (unsigned *)scratch;
+  if (!status) status = (int *)(scratch + 16);
+  double *rec = scratch + kNoAllocHeadDoubles;
+  double *prow = rec + kNoAllocRecDoubles;
+  double *wy_store = wy ? wy : prow + kNoAllocProwDoubles;
+  double *work = prow + kNoAllocProwDoubles + kNoAllocWyDoubles;
+  // the array keeps the previous call's contents: clear the counter and status
+  cudaError_t e = cudaMemsetAsync(scratch, 0, kNoAllocHeadDoubles * sizeof(double), stream);
+  if (e == cudaSuccess && n > K) e = cudaMemsetAsync(up + K, 0, sizeof(double) * (n - K), stream);
+  if (e != cudaSuccess) return SLQR_ECUDA;
+  unsigned bar_base = 0;
+  for (int pnl = 0; pnl < np; ++pnl) {
+    const int k0 = pnl * NB;
+    const int nbw = std::min(NB, K - k0);
+    const int M = m - k0;
+    const int R = panel_rows_per_cta(M, nbw, num_sms);
+    if (R > max_rows_per_cta(NB)) return SLQR_EINVAL;
+    const int P = (M + R - 1) / R;
+    double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
+    PanelParams pp;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.prow = prow; pp.bar = bar;
+    pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
+    pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    void *args[] = {&pp};
+    size_t smem = (size_t)NB * R * sizeof(double);
+    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P), dim3(kThreads), args,
+                                    smem, stream);
+    if (e != cudaSuccess) return SLQR_ECUDA;
+    bar_base += (unsigned)P * (unsigned)nbw;
+    const int N = n - (k0 + nbw);
+    if (N > 0) {
+      slqr_status st = noalloc_update<NB>(num_sms, m, k0, nbw, A, lda, wy_panel,
+                                          A + (size_t)(k0 + nbw) * lda, lda, N, work,
+                                          kNoAllocWorkDoubles, stream);
+      if (st != SLQR_OK) return st;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? SLQR_OK : SLQR_ECUDA;
+}
+
+}  // namespace slqr
+
+extern "C" int slqr_noalloc_max_rows(void) { return kNoAllocMaxRows; }
+extern "C" int slqr_noalloc_max_cols(void) { return kNoAllocMaxCols; }
+
+extern "C" slqr_status slqr_factor_noalloc(int m, int n, double *A, int lda, double *up,
+                                           double *wy, int *status, void *stream) {
+  if (m < 0 || n < 0 || m < n) return SLQR_EINVAL;
+  if (n == 0) return SLQR_OK;
+  if (m > kNoAllocMaxRows || n > kNoAllocMaxCols) return SLQR_EINVAL;
+  if (lda < std::max(1, m) || !A || !up) return SLQR_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return SLQR_ECUDA;
+  }
+  double *scratch = nullptr;
+  int sms = 0;
+  slqr_status st = noalloc_setup(dev, &scratch, &sms);
+  if (st != SLQR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (panel_width(m, n) == 32)
+    return noalloc_factor_impl<32>(scratch, sms, m, n, A, lda, up, wy, status, s);
+  return noalloc_factor_impl<64>(scratch, sms, m, n, A, lda, up, wy, status, s);
+}
