@@ -85,6 +85,8 @@ __device__ __forceinline__ void record_status(int *status, int code) {
 // --------------------------------------------------------------------------
 // panel kernel
 // --------------------------------------------------------------------------
+constexpr int kPanelQpl = 5;                  // record loads per lane: P <= 32 * 5
+constexpr int kMaxPanelCtas = 32 * kPanelQpl;
 struct PanelParams {
   double *A;
   double *up;          // global up array (n doubles)
@@ -199,15 +201,39 @@ panel_kernel(PanelParams p) {
     }
 
     // ---- phase 2: every CTA reduces the partials in the same fixed order ---
-    for (int e = warp; e < nbw + 1; e += NW) {
-      // e == 0: the norm pair; e >= 1: dot with panel column c = e - 1
-      if (e == 0) {
-        int E = kNoExp;
-        double S = 0.0;
-        for (int q = lane; q < p.P; q += 32) {
-          double Eq = __ldcg(rec + q), Sq = __ldcg(rec + p.P + q);
-          ssq_merge(E, S, (int)Eq, Sq);
+    // Warp w owns entries e = w, w + NW, ... (e == 0: the norm pair, e >= 1:
+    // the dot with panel column e - 1).  All loads of a lane are issued before
+    // any is used, so the reduction costs about one L2 round trip.
+    {
+      constexpr int EPW = (NB + 1 + NW - 1) / NW;
+      double sum[EPW];
+#pragma unroll
+      for (int ee = 0; ee < EPW; ++ee) sum[ee] = 0.0;
+      int E = kNoExp;
+      double S = 0.0;
+#pragma unroll
+      for (int i = 0; i < kPanelQpl; ++i) {
+        const int q = lane + 32 * i;
+        if (q < p.P) {
+#pragma unroll
+          for (int ee = 0; ee < EPW; ++ee) {
+            const int e = warp + NW * ee;
+            if (e >= 1 && e <= nbw && e - 1 != j)
+              sum[ee] += __ldcg(rec + (size_t)(2 + (e - 1)) * p.P + q);
+          }
+          if (warp == 0) {
+            double Eq = __ldcg(rec + q), Sq = __ldcg(rec + p.P + q);
+            ssq_merge(E, S, (int)Eq, Sq);
+          }
         }
+      }
+#pragma unroll
+      for (int ee = 0; ee < EPW; ++ee) {
+        const int e = warp + NW * ee;
+        double v = warp_sum(sum[ee]);
+        if (lane == 0 && e >= 1 && e <= nbw) s_D[e - 1] = v;
+      }
+      if (warp == 0) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           int E2 = __shfl_xor_sync(0xffffffffu, E, o);
@@ -215,13 +241,6 @@ panel_kernel(PanelParams p) {
           ssq_merge(E, S, E2, S2);
         }
         if (lane == 0) s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
-      } else {
-        int c = e - 1;
-        if (c == j) continue;
-        double v = 0.0;
-        for (int q = lane; q < p.P; q += 32) v += __ldcg(rec + (size_t)(2 + c) * p.P + q);
-        v = warp_sum(v);
-        if (lane == 0) s_D[c] = v;
       }
     }
     __syncthreads();
@@ -374,29 +393,61 @@ gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict_
   }
 }
 
-// W'[a][c] = (T^T W)[a][c]: reduce the S partials of column c, then forward
-// substitution  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q).
+// W'[a][c] = (T^T W)[a][c] for 64 columns per CTA: reduce the S partials of
+// each column (coalesced, all loads of a thread in flight together), then the
+// forward substitution  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)  with four
+// lanes per column splitting the inner sum.
 template <int NB>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kThreads)
 tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
           double *__restrict__ Wt) {
-  __shared__ double w[NB][65];
+  constexpr int COLS = 64;
+  constexpr int EPT = NB * COLS / kThreads;     // entries per thread
+  __shared__ double w[NB][COLS + 1];
   const int tid = threadIdx.x;
   const double *G = wy + (size_t)NB * NB;
   const double *tau = wy + 2 * (size_t)NB * NB;
-  const int c = blockIdx.x * 64 + tid;
-  if (c >= N) return;
-  for (int a = 0; a < nbw; ++a) {
-    double v = 0.0;
-    for (int s = 0; s < S; ++s) v += Wp[((size_t)s * N + c) * NB + a];
-    w[a][tid] = v;
+  const int c0 = blockIdx.x * COLS;
+  double acc[EPT];
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) acc[i] = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const double *src = Wp + ((size_t)s * N + c0) * NB;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int idx = tid + kThreads * i;       // (c, a) with a fastest
+      const int c = idx / NB, a = idx - c * NB;
+      if (c0 + c < N) acc[i] += src[idx];
+      (void)a;
+    }
   }
-  for (int j = 0; j < nbw; ++j) {
-    double t = w[j][tid];
-    for (int q = 0; q < j; ++q) t = fma(-__ldg(G + q + j * NB), w[q][tid], t);
-    w[j][tid] = __ldg(tau + j) * t;
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int idx = tid + kThreads * i;
+    const int c = idx / NB, a = idx - c * NB;
+    w[a][c] = acc[i];
   }
-  for (int a = 0; a < NB; ++a) Wt[(size_t)a * N + c] = (a < nbw) ? w[a][tid] : 0.0;
+  __syncthreads();
+  {
+    const int c = tid >> 2, part = tid & 3;
+    for (int j = 0; j < nbw; ++j) {
+      double t = 0.0;
+      for (int q = part; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      const double wj = __ldg(tau + j) * (w[j][c] - t);
+      __syncwarp();
+      if (part == 0) w[j][c] = wj;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int idx = tid + kThreads * i;         // (a, c) with c fastest
+    const int a = idx / COLS, c = idx - a * COLS;
+    if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? w[a][c] : 0.0;
+  }
 }
 
 // X(i, c) -= sum_a V(i, a) W'[a][c] on a kBM x kBN tile; grid (ceil(M/kBM), ceil(N/kBN))
@@ -498,7 +549,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
       A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  tw_kernel<NB><<<(N + 63) / 64, 64, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  tw_kernel<NB><<<(N + 63) / 64, kThreads, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
   slot = prof_begin(ctx, stream);
@@ -539,7 +590,8 @@ slqr_status init_kernel_attrs(slqr_ctx *ctx) {
 
 // rows per CTA of the panel kernel
 static int panel_rows_per_cta(int M, int nbw, int num_sms) {
-  int R = (M + num_sms - 1) / num_sms;
+  const int ctas = std::min(num_sms, kMaxPanelCtas);
+  int R = (M + ctas - 1) / ctas;
   R = std::max(R, nbw);
   R = std::max(R, 32);
   return R;
@@ -740,7 +792,7 @@ static slqr_status noalloc_update(int num_sms, int m, int k0, int nbw, const dou
   double *Wt = work + (size_t)Seff * N * NB;
   gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, RS, Wp);
-  tw_kernel<NB><<<(N + 63) / 64, 64, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  tw_kernel<NB><<<(N + 63) / 64, kThreads, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
   gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, Wt);
