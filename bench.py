@@ -42,6 +42,8 @@ WORKLOAD = ("plain FP64 H12 least squares: tall 16384x2048 + square 8192x8192 ii
 # FP64 FMA pipe: 2 DFMA (4 flops) per clock per SM x 152 SMs x 2070 MHz
 FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12
 CPU_SAMPLE_COLS = 512   # oracle sample: leading m x 512 block of each matrix
+# factorization-only timings reported beside the step (N(0,1), seeds 2, 3, 4)
+FACTOR_ONLY_SHAPES = [(16384, 2048, 2), (8192, 8192, 3), (8192, 4096, 4)]
 
 
 def step_flops(shapes=SHAPES, nrhs=NRHS):
@@ -297,6 +299,29 @@ def run_ours(args, rank, world, local_rank):
     if ctx.sync() != 0:
         raise RuntimeError(abi.slqr_last_error(ctx.ctx))
 
+    # ---- factorization alone, per shape (context for the paper's QR-only times) ----
+    factor_only = {}
+    for (m, n, seed) in FACTOR_ONLY_SHAPES:
+        A0 = colmajor_cuda(workloads.gaussian(m, n, seed)[0], device)
+        Aw = A0.t().clone().t()
+        up = torch.empty(n, dtype=torch.float64, device=device)
+        times = []
+        for rep in range(3):
+            Aw.copy_(A0)
+            barrier()
+            e0.record(stream)
+            ctx.factor(Aw, up)
+            e1.record(stream)
+            barrier()
+            times.append(e0.elapsed_time(e1))
+        t = min(times)
+        fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+        factor_only[f"{m}x{n}"] = {"ms": t, "gflops": fl / (t / 1e3) / 1e9,
+                                   "frac_of_fp64_peak": fl / (t / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+        del A0, Aw
+    if ctx.sync() != 0:
+        raise RuntimeError(abi.slqr_last_error(ctx.ctx))
+
     # ---- roofline of the dominant kernel (most device time in the timed region) ----
     dom = max(prof, key=lambda k: prof[k][0])
     dms, dn, dfl = prof[dom]
@@ -329,9 +354,35 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "gpu_launches": launches,
         "kernels": kernels,
+        "factor_only": factor_only,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
+    return 0
+
+
+def run_ncu_case(m, n):
+    """One factorization + Q^T (64 RHS) + back-substitution of an m x n N(0,1)
+    matrix after one warm-up pass: a small, short program for ncu captures."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import api
+    A, _ = workloads.gaussian(m, n, 4)
+    dev = torch.device("cuda", 0)
+    A0 = colmajor_cuda(A, dev)
+    B0 = colmajor_cuda(workloads.gaussian_rhs(m, 64, 4), dev)
+    with api.Context(0) as ctx:
+        for _ in range(2):
+            Aw, Bw = A0.t().clone().t(), B0.t().clone().t()
+            up = torch.empty(n, dtype=torch.float64, device=dev)
+            wy = ctx.wy_buffer(m, n)
+            ctx.factor(Aw, up, wy)
+            ctx.apply_qt(Aw, up, Bw, wy=wy)
+            ctx.solve_r(Aw, Bw)
+            st = ctx.sync()
+            if st != 0:
+                raise RuntimeError(f"device status {st}")
+    print(f"ncu case {m}x{n} done")
     return 0
 
 
@@ -342,7 +393,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
+                    help="run one small factor/apply/solve pass for profiling and exit")
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(*args.ncu_case)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -159,6 +159,10 @@ extern "C" slqr_status slqr_create(slqr_ctx **out, int device, size_t hbm_budget
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -182,6 +186,10 @@ extern "C" void slqr_destroy(slqr_ctx *ctx) {
   cudaDeviceSynchronize();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->prof.free_events) cudaEventDestroy(e);
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  if (ctx->ev_ready) cudaEventDestroy(ctx->ev_ready);
+  if (ctx->ev_panel) cudaEventDestroy(ctx->ev_panel);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
@@ -201,6 +209,10 @@ extern "C" slqr_status slqr_sync(slqr_ctx *ctx, void *stream) {
   int st = 0;
   e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "status word: %s", cudaGetErrorString(e));
   if (st != 0) {
     if (st == SLQR_ERANK) fail(ctx, st, "R has an exact zero on its diagonal");

@@ -111,6 +111,7 @@ panel_kernel(PanelParams p) {
   __shared__ double s_D[NB];                  // reduced dot products
   __shared__ double s_sig[NB];                // sigma per column
   __shared__ double s_up[NB];
+  __shared__ double s_prow[NB];               // pivot row of the current column
   __shared__ double s_norm;
   __shared__ int s_ok;
 
@@ -206,6 +207,7 @@ panel_kernel(PanelParams p) {
     // any is used, so the reduction costs about one L2 round trip.
     {
       constexpr int EPW = (NB + 1 + NW - 1) / NW;
+      const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;  // in flight with the rest
       double sum[EPW];
 #pragma unroll
       for (int ee = 0; ee < EPW; ++ee) sum[ee] = 0.0;
@@ -242,12 +244,13 @@ panel_kernel(PanelParams p) {
         }
         if (lane == 0) s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
       }
+      if (tid < nbw) s_prow[tid] = prow_v;
     }
     __syncthreads();
 
     // pivot quantities (every thread computes the same values)
     const double s = s_norm;
-    const double x0 = __ldcg(prow + j);
+    const double x0 = s_prow[j];
     double cl = 0.0, upk = 0.0, bk = 0.0, tk = 0.0;
     const bool defined = (s != 0.0);
     if (defined) {
@@ -258,7 +261,7 @@ panel_kernel(PanelParams p) {
     }
     if (tid < nbw) {
       int c = tid;
-      double pr = __ldcg(prow + c);
+      double pr = s_prow[c];
       if (c > j) {
         s_sig[c] = defined ? (upk * pr + s_D[c]) / bk : 0.0;
       } else if (c < j && cta == 0) {
@@ -629,8 +632,13 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
       return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
 
+  // Look-ahead: after panel p, the columns of panel p+1 are updated first;
+  // panel p+1 is then factored on the auxiliary stream while the rest of the
+  // trailing update of panel p runs on the caller's stream (the GPU form of
+  // running the critical path T_{i,i} early).
+  cudaStream_t aux = ctx->aux_stream;
   unsigned bar_base = 0;
-  for (int pnl = 0; pnl < np; ++pnl) {
+  auto launch_panel = [&](int pnl, cudaStream_t s) -> slqr_status {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     const int M = m - k0;
@@ -649,20 +657,52 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     // for each later panel column, a dot and an axpy over M-j entries
     double pflops = 0.0;
     for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
-    int slot = prof_begin(ctx, stream);
-    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P), dim3(kThreads), args,
-                                    smem, stream);
-    prof_end(ctx, stream, slot, kPanel, pflops);
-    if (e != cudaSuccess)
+    int slot = prof_begin(ctx, s);
+    cudaError_t le = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P),
+                                                 dim3(kThreads), args, smem, s);
+    prof_end(ctx, s, slot, kPanel, pflops);
+    if (le != cudaSuccess)
       return fail(ctx, SLQR_ECUDA, "panel launch (P=%d, smem=%zu): %s", P, smem,
-                  cudaGetErrorString(e));
+                  cudaGetErrorString(le));
     bar_base += (unsigned)P * (unsigned)nbw;
-    // trailing columns [k0 + nbw, n)
-    const int N = n - (k0 + nbw);
-    if (N > 0) {
-      st = panel_update_impl<NB>(ctx, m, k0, nbw, A, lda, wy_panel,
-                                 A + (size_t)(k0 + nbw) * lda, lda, N, work, work_doubles,
-                                 stream);
+    return SLQR_OK;
+  };
+  auto update = [&](int pnl, int c_begin, int c_end) -> slqr_status {
+    const int k0 = pnl * NB;
+    const int nbw = std::min(NB, K - k0);
+    if (c_end <= c_begin) return SLQR_OK;
+    return panel_update_impl<NB>(ctx, m, k0, nbw, A, lda,
+                                 wy_store + (size_t)pnl * wy_panel_doubles(NB),
+                                 A + (size_t)c_begin * lda, lda, c_end - c_begin, work,
+                                 work_doubles, stream);
+  };
+  // order the auxiliary stream after everything already on the caller's stream
+  e = cudaEventRecord(ctx->ev_start, stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ctx->ev_start, 0);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+  st = launch_panel(0, stream);
+  if (st != SLQR_OK) return st;
+  for (int pnl = 0; pnl < np; ++pnl) {
+    const int k0 = pnl * NB;
+    const int nbw = std::min(NB, K - k0);
+    const int c0 = k0 + nbw;                       // first trailing column
+    if (pnl + 1 < np) {
+      const int next_w = std::min(NB, K - (k0 + NB));
+      st = update(pnl, c0, c0 + next_w);           // columns of panel p+1
+      if (st != SLQR_OK) return st;
+      e = cudaEventRecord(ctx->ev_ready, stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ctx->ev_ready, 0);
+      if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+      st = launch_panel(pnl + 1, aux);
+      if (st != SLQR_OK) return st;
+      e = cudaEventRecord(ctx->ev_panel, aux);
+      if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+      st = update(pnl, c0 + next_w, n);            // the rest, concurrently with the panel
+      if (st != SLQR_OK) return st;
+      e = cudaStreamWaitEvent(stream, ctx->ev_panel, 0);
+      if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+    } else {
+      st = update(pnl, c0, n);
       if (st != SLQR_OK) return st;
     }
   }

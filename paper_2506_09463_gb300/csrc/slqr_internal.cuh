@@ -61,6 +61,8 @@ struct slqr_ctx {
   int *d_status = nullptr;             // device status word
   slqr::Workspace ws;                  // grown on demand
   slqr::Profiler prof;                 // optional CUDA-event timing per kernel family
+  cudaStream_t aux_stream = nullptr;   // look-ahead panels run here
+  cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_panel = nullptr;
   long long launch_count = 0;          // kernels launched by this context
   std::string last_error;
   std::mutex mu;
