@@ -322,6 +322,9 @@ def run_ours(args, rank, world, local_rank):
     if ctx.sync() != 0:
         raise RuntimeError(abi.slqr_last_error(ctx.ctx))
 
+    # ---- batched workload: 20,000 uneven problems in one persistent launch ----
+    batch = run_batch_workload(ctx, device, stream, barrier) if not args.no_batch else None
+
     # ---- roofline of the dominant kernel (most device time in the timed region) ----
     dom = max(prof, key=lambda k: prof[k][0])
     dms, dn, dfl = prof[dom]
@@ -355,10 +358,107 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "kernels": kernels,
         "factor_only": factor_only,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+BATCH_COUNT = 20000
+
+
+def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, serial=300):
+    """Factor + Q^T b + solve of `count` problems (m ~ U{16..512}, n ~ U{m/4..m},
+    N(0,1), seed 7) in one persistent launch, FP64 and mixed FP32 (FP32
+    factorization + FP64-residual refinement); beside it the plain
+    one-at-a-time FP64 path (slqr_factor + slqr_apply_qt + slqr_solve_r per
+    problem, serially on one stream) timed on the first `serial` problems."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi
+    ms, ns = workloads.batch_shapes(count)
+    A_flat, b_flat, a_off, b_off = workloads.batch_problems_device(ms, ns, workloads.SEED_BATCH,
+                                                                   device=device)
+    A0, b0 = A_flat.clone(), b_flat.clone()
+    up_flat = torch.zeros(int(ns.sum()) + 1, dtype=torch.float64, device=device)
+    up_off = np.concatenate([[0], np.cumsum(ns)[:-1]])
+    A_ptrs = [A_flat.data_ptr() + int(o) * 8 for o in a_off]
+    b_ptrs = [b_flat.data_ptr() + int(o) * 8 for o in b_off]
+    up_ptrs = [up_flat.data_ptr() + int(o) * 8 for o in up_off]
+    lda = [int(m) for m in ms]
+    status = torch.zeros(count, dtype=torch.int32, device=device)
+    err = torch.zeros(count, dtype=torch.float64, device=device)
+    flops = float(np.sum(2.0 * ms * ns * ns - 2.0 * ns ** 3 / 3.0 + 6.0 * ms * ns))
+    out = {"problems": count, "shapes": "m ~ U{16..512}, n ~ U{ceil(m/4)..m}, N(0,1), seed 7",
+           "algorithmic_gflop": flops / 1e9}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, prec in (("fp64", abi.SLQR_FP64), ("mixed_fp32", abi.SLQR_FP32)):
+        times = []
+        for rep in range(reps + 1):
+            A_flat.copy_(A0)
+            b_flat.copy_(b0)
+            barrier()
+            e0.record(stream)
+            st = abi.slqr_batch_factor(ctx.ctx, list(ms), list(ns), A_ptrs, lda,
+                                       up_ptrs if prec == abi.SLQR_FP64 else None, b_ptrs, prec,
+                                       status.data_ptr(), err.data_ptr(), stream.cuda_stream)
+            abi.check(ctx.ctx, st, "slqr_batch_factor")
+            e1.record(stream)
+            barrier()
+            if rep:
+                times.append(e0.elapsed_time(e1))
+        t = min(times)
+        stv = status.cpu().numpy()
+        rec = {"ms": t, "problems_per_s": count / (t / 1e3), "gflops": flops / (t / 1e3) / 1e9,
+               "ok": int(np.sum(stv == 0)), "erank": int(np.sum(stv == abi.SLQR_ERANK)),
+               "no_conv": int(np.sum(stv == abi.SLQR_ENOCONV))}
+        if prec == abi.SLQR_FP32:
+            ev = err.cpu().numpy()
+            rec["refine_err_max"] = float(ev[stv == 0].max()) if np.any(stv == 0) else None
+            # refined solutions against the FP64 batch solutions of the same problems
+            x32 = b_flat.clone()
+            rec["max_rel_diff_vs_fp64_batch"] = None
+            if x64 is not None:
+                worst = 0.0
+                for i in range(0, count, max(1, count // 400)):
+                    o, n_ = int(b_off[i]), int(ns[i])
+                    a, c = x32[o:o + n_], x64[o:o + n_]
+                    worst = max(worst, float(torch.linalg.norm(a - c) / torch.linalg.norm(c)))
+                rec["max_rel_diff_vs_fp64_batch"] = worst
+        else:
+            x64 = b_flat.clone()
+        out[name] = rec
+    # plain one-at-a-time FP64 GPU path on the first `serial` problems
+    A_flat.copy_(A0)
+    b_flat.copy_(b0)
+    barrier()
+    e0.record(stream)
+    sflops = 0.0
+    for i in range(serial):
+        m, n = int(ms[i]), int(ns[i])
+        Ai = A_flat[int(a_off[i]):int(a_off[i]) + m * n].view(n, m).t()
+        bi = b_flat[int(b_off[i]):int(b_off[i]) + m]
+        upi = up_flat[int(up_off[i]):int(up_off[i]) + n]
+        ctx.factor(Ai, upi)
+        ctx.apply_qt(Ai, upi, bi)
+        ctx.solve_r(Ai, bi)
+        sflops += 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + 6.0 * m * n
+    e1.record(stream)
+    barrier()
+    t = e0.elapsed_time(e1)
+    out["one_at_a_time_fp64"] = {"problems": serial, "ms": t,
+                                 "problems_per_s": serial / (t / 1e3),
+                                 "gflops": sflops / (t / 1e3) / 1e9}
+    out["speedup_fp64_batch_vs_one_at_a_time"] = (out["fp64"]["problems_per_s"] /
+                                                  out["one_at_a_time_fp64"]["problems_per_s"])
+    out["speedup_mixed_batch_vs_one_at_a_time"] = (out["mixed_fp32"]["problems_per_s"] /
+                                                   out["one_at_a_time_fp64"]["problems_per_s"])
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the batch workload")
+    del A_flat, b_flat, A0, b0
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ncu_case(m, n):
@@ -393,6 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
                     help="run one small factor/apply/solve pass for profiling and exit")
     args = ap.parse_args()

@@ -61,6 +61,7 @@ typedef int slqr_status;
 #define SLQR_ERANK     (-5)  /* R has an exact zero on its diagonal */
 #define SLQR_EBUSY     (-6)  /* over the HBM budget of the context */
 #define SLQR_ENOTFOUND (-7)  /* unknown ticket or handle */
+#define SLQR_ENOCONV   (-8)  /* iterative refinement did not reach its tolerance */
 
 typedef struct slqr_ctx slqr_ctx;
 
@@ -150,6 +151,49 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
                          double *B, int ldb, void *stream);
 
 /*
+ * slqr_batch_factor -- `count` independent least-squares problems in one
+ * persistent launch.  Each problem is the factorization of slqr_factor
+ * (Alg. 2, Task 1 skip rule) and, when its b is given, Q^T b and the
+ * back-substitution fused after it (the reuse of the stored reflectors named
+ * in Section 1).  Persistent CTAs take problems from a device-side queue
+ * ordered costliest first; one CTA owns one problem at a time.
+ *   count        number of problems, >= 0
+ *   m, n, lda    HOST arrays of count ints: 0 <= n <= m <= slqr_batch_max_rows(),
+ *                lda >= max(1, m)
+ *   A            HOST array of count DEVICE pointers (column-major m x n)
+ *   up           HOST array of count DEVICE pointers (n doubles each)
+ *   b            HOST array of count DEVICE pointers (m doubles each) or NULL
+ *                (whole array) / a NULL entry: no solve for that problem
+ *   prec         SLQR_FP64 or SLQR_FP32
+ *   status       DEVICE array of count ints or NULL: per problem SLQR_OK,
+ *                SLQR_ERANK (a zero diagonal of R) or, for SLQR_FP32,
+ *                SLQR_ENOCONV (refinement stopped above its tolerance)
+ *   err          DEVICE array of count doubles or NULL: for SLQR_FP32 the
+ *                last refinement step ||dx||_inf / ||x||_inf of each problem
+ *                (an estimate of its remaining relative error); not written
+ *                for SLQR_FP64
+ * Outputs, SLQR_FP64: A[i] and up[i] hold the H12 factorization (storage
+ * form above); b[i][0:n] = x_i, b[i][n:m] = the residual part of Q^T b.
+ * Outputs, SLQR_FP32 (b required, up may be NULL): A[i] is left unchanged;
+ * the H12 factorization is computed in FP32 (reflector norm, up and b in
+ * FP64) on a scratch copy, and the LS solution is refined against the FP64
+ * A[i] by the augmented-system iteration [I A; A^T 0][r; x] = [b; 0] with
+ * FP64 residuals (up to 12 sweeps; SLQR_OK at ||dx|| <= 1e-14 ||x||, or
+ * when the steps stop contracting below 1e-11 ||x||, the FP64 noise level of
+ * an ill-conditioned problem);
+ * b[i][0:n] = x_i, b[i][n:m] is unspecified.
+ * The host arrays are read before the call returns.  The problems must not
+ * overlap in memory.  Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
+ */
+#define SLQR_FP64 0   /* FP64 throughout (DFMA)                                   */
+#define SLQR_FP32 1   /* FP32 factorization + FP64-residual refinement (batches)  */
+slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
+                              double *const *A, const int *lda, double *const *up,
+                              double *const *b, int prec, int *status, double *err,
+                              void *stream);
+int slqr_batch_max_rows(void);
+
+/*
  * slqr_factor_noalloc -- the factorization of slqr_factor for callers that
  * must not allocate device memory.  The paper has no counterpart: this entry
  * point exists for embedding.  Some callers cannot call cudaMalloc: a host
@@ -159,7 +203,7 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
  * nothing: the caller passes the inputs and outputs, and every other buffer
  * the factorization needs (barrier counter, reduction records, compact-WY
  * store when wy is NULL, partial sums) lives in one fixed array of about
- * 5.3 MB that the library declares in device memory.  Every GPU that loads
+ * 6.9 MB that the library declares in device memory.  Every GPU that loads
  * libslqr holds that array until the process exits.
  *   m, n     m >= n >= 0, m <= slqr_noalloc_max_rows() (8192),
  *            n <= slqr_noalloc_max_cols() (1024); larger sizes return
@@ -198,6 +242,7 @@ int slqr_noalloc_max_cols(void);
 #define SLQR_KERNEL_UPD        3  /* X -= V W'                                   */
 #define SLQR_KERNEL_WY_REBUILD 4  /* compact-WY rebuild inside slqr_apply_qt     */
 #define SLQR_KERNEL_TRSM       5  /* back-substitution steps                     */
+#define SLQR_KERNEL_BATCH      6  /* persistent batched factor (+ solve)         */
 int slqr_profile(slqr_ctx *ctx, int enable);
 slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms, long long *launches,
                               double *flops);

@@ -52,12 +52,20 @@ SIGNATURES = [
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_dbl)]),
     ("slqr_launch_count", ctypes.c_longlong, [_vp]),
     ("slqr_factor_noalloc", _c_int, [_c_int, _c_int, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    ("slqr_batch_factor", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                   ctypes.POINTER(_vp), ctypes.POINTER(_c_int),
+                                   ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, _vp, _vp,
+                                   _vp]),
+    ("slqr_batch_max_rows", _c_int, []),
     ("slqr_noalloc_max_rows", _c_int, []),
     ("slqr_noalloc_max_cols", _c_int, []),
 ]
 
-KERNEL_PANEL, KERNEL_VTX, KERNEL_TW, KERNEL_UPD, KERNEL_WY_REBUILD, KERNEL_TRSM = range(6)
-KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm"]
+KERNEL_PANEL, KERNEL_VTX, KERNEL_TW, KERNEL_UPD, KERNEL_WY_REBUILD, KERNEL_TRSM, KERNEL_BATCH = \
+    range(7)
+KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm", "batch"]
+SLQR_FP64 = 0
+SLQR_FP32 = 1
 
 
 def _load() -> ctypes.CDLL:
@@ -140,6 +148,28 @@ def slqr_profile_read(ctx: int, kernel: int):
 
 def slqr_launch_count(ctx: int) -> int:
     return _lib.slqr_launch_count(ctx)
+
+
+def _int_array(values):
+    return (_c_int * len(values))(*[int(v) for v in values])
+
+
+def _ptr_array(values):
+    return (_vp * len(values))(*[v if v else None for v in values])
+
+
+def slqr_batch_factor(ctx, m_list, n_list, A_ptrs, lda_list, up_ptrs, b_ptrs, prec, status,
+                      err, stream) -> int:
+    """Host lists of sizes and of device pointers; status / err device pointers or None."""
+    count = len(m_list)
+    return _lib.slqr_batch_factor(
+        ctx, count, _int_array(m_list), _int_array(n_list), _ptr_array(A_ptrs),
+        _int_array(lda_list), _ptr_array(up_ptrs) if up_ptrs is not None else None,
+        _ptr_array(b_ptrs) if b_ptrs is not None else None, prec, status, err, stream)
+
+
+def slqr_batch_max_rows() -> int:
+    return _lib.slqr_batch_max_rows()
 
 
 def slqr_factor_noalloc(m, n, A, lda, up, wy, status, stream) -> int:

@@ -1,0 +1,643 @@
+// batch.cu -- many independent H12 least-squares problems in one persistent
+// launch (slqr_batch_factor).
+//
+// Each problem is the factorization of Alg. 2 (update_pivot_row, then
+// update_trailing_non_pivot_row on every later column; Task 1 skip rule),
+// optionally followed by Q^T b and the back-substitution (Section 1: the
+// stored reflectors are reused by the solve).  Problems are independent, so
+// one CTA owns one problem at a time; persistent CTAs take the next problem
+// from a device-side atomic counter over a list ordered costliest first
+// (longest-processing-time first), the GPU descendant of the paper's shared
+// main_queue of ready tasks (Alg. 5).
+//
+// Inside a CTA a problem is factored in panels of kBNB reflectors:
+//  * the panel (rows k0..m-1, kBNB columns) sits in shared memory; each column
+//    is one block-level reduction (scaled norm, dots of the column tail with
+//    the other panel columns, which also give striu(V^T V)), then the update
+//    of the later panel columns;
+//  * the trailing columns (and b, as one more column) are updated in tiles of
+//    32 columns: W = V^T C (one warp per column, lanes over rows), then
+//    W' = T^T W by forward substitution (one lane per column), then C -= V W'.
+// All arithmetic is FP64 (DFMA).
+#include "slqr_internal.cuh"
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+namespace slqr {
+
+constexpr int kBNB = 16;          // reflectors per panel
+constexpr int kBMaxRows = 512;    // rows of a batched problem (panel slice in smem)
+constexpr int kBCols = 32;        // trailing columns per tile
+constexpr int kBWarps = kThreads / 32;
+constexpr int kBMaxRefine = 12;        // refinement sweeps of the mixed path
+constexpr double kBRefineTol = 1e-14;  // stop when ||dx||_inf <= tol ||x||_inf
+constexpr double kBStallOk = 1e-11;    // a stalled refinement is accepted below this
+
+struct BatchProblem {
+  double *A;
+  double *up;
+  double *b;
+  int m, n, lda, pad;
+};
+
+struct BatchParams {
+  const BatchProblem *probs;
+  const int *order;
+  int count;
+  unsigned *counter;
+  int *status;
+};
+
+constexpr int kNoExpB = -4000;
+
+__device__ __forceinline__ void b_ssq_add(int &E, double &S, double x) {
+  if (x != 0.0) {
+    int ex = ilogb(x);
+    if (ex > E) {
+      S = ldexp(S, 2 * (E - ex));
+      E = ex;
+    }
+    double y = ldexp(x, -E);
+    S = fma(y, y, S);
+  }
+}
+
+__device__ __forceinline__ void b_ssq_merge(int &E, double &S, int E2, double S2) {
+  if (S2 == 0.0) return;
+  if (S == 0.0) { E = E2; S = S2; return; }
+  if (E2 > E) { S = ldexp(S, 2 * (E - E2)) + S2; E = E2; }
+  else S = S + ldexp(S2, 2 * (E2 - E));
+}
+
+__device__ __forceinline__ double b_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Shared-memory layout of the batched kernels.  The panel slice Ps and the
+// W tile are of the working type T (double for SLQR_FP64, float for the
+// mixed-precision path); the small per-panel quantities are double.
+__host__ __device__ constexpr size_t align_up_c(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+struct BatchSmem {
+  static constexpr int kPanel = kBNB * kBMaxRows;       // Ps[c][r]
+  static constexpr int kW = kBNB * (kBCols + 1);        // Wt[a][col]
+  static constexpr size_t kBytesT = (size_t)(kPanel + kW) * sizeof(T);
+  static constexpr int kG = kBNB * kBNB;                // G[q][j] (ld kBNB)
+  static constexpr int kMisc = 4 * kBNB + 8;            // dots, sigma, tau, up, norm
+  static constexpr size_t kBytes = align_up_c(kBytesT, 16) + (size_t)(kG + kMisc) * sizeof(double);
+};
+
+// The H12 factorization of one m x n problem by one CTA (see the file
+// header).  Reflector constants (norm, cl, up, b, tau, sigma) are FP64; dot
+// products and updates run in T.  When G_out/tau_out are given, each panel's
+// striu(V^T V) and tau are kept there (the mixed path reuses them to apply Q).
+// Bcol (T == double only) is an extra right-hand-side column updated with the
+// trailing columns, giving Q^T b.
+template <typename T>
+__device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, double *Bcol,
+                                  double *G_out, double *tau_out, char *smraw) {
+  using SM = BatchSmem<T>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T *Ps = (T *)smraw;
+  T *Wt = Ps + SM::kPanel;
+  double *Gs = (double *)(smraw + align_up_c(SM::kBytesT, 16));
+  double *dots = Gs + SM::kG;
+  double *sig = dots + kBNB;
+  double *tau = sig + kBNB;
+  double *ups = tau + kBNB;
+  double *misc = ups + kBNB;        // [0] = norm
+  const int K = num_reflectors(m, n);
+  for (int k = K + tid; k < n; k += kThreads) up_out[k] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += kBNB) {
+    const int nbw = min(kBNB, K - k0);
+    const int M = m - k0;
+    for (int idx = tid; idx < kBNB * M; idx += kThreads) {
+      int c = idx / M, r = idx - c * M;
+      Ps[c * kBMaxRows + r] = (c < nbw) ? A[SLQR_IDX(k0 + r, k0 + c, lda)] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < nbw; ++j) {
+      const T *x = Ps + j * kBMaxRows;
+      // phase 1: warp w takes panel columns w and w + 8
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int c = warp + kBWarps * t;
+        if (c >= nbw) continue;
+        if (c == j) {
+          int E = kNoExpB;
+          double S = 0.0;
+          for (int r = j + lane; r < M; r += 32) b_ssq_add(E, S, (double)x[r]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            int E2 = __shfl_xor_sync(0xffffffffu, E, o);
+            double S2 = __shfl_xor_sync(0xffffffffu, S, o);
+            b_ssq_merge(E, S, E2, S2);
+          }
+          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
+        } else {
+          const T *col = Ps + c * kBMaxRows;
+          T acc = T(0);
+          for (int r = j + 1 + lane; r < M; r += 32) acc = fma(x[r], col[r], acc);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) dots[c] = (double)acc;
+        }
+      }
+      __syncthreads();
+      const double s = misc[0];
+      const double x0 = (double)x[j];
+      const bool defined = (s != 0.0);
+      double cl = 0.0, upk = 0.0, bk = 1.0, tk = 0.0;
+      if (defined) {
+        cl = (x0 > 0.0) ? -s : s;
+        upk = x0 - cl;
+        bk = upk * cl;
+        tk = -1.0 / bk;
+      }
+      if (tid < nbw) {
+        const int c = tid;
+        const double pr_c = (double)Ps[c * kBMaxRows + j];
+        if (c > j) sig[c] = defined ? (upk * pr_c + dots[c]) / bk : 0.0;
+        else if (c < j) Gs[c + j * kBNB] = pr_c * upk + dots[c];
+      }
+      __syncthreads();
+      if (defined) {
+        const T upT = (T)upk;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int c = warp + kBWarps * t;
+          if (c > j && c < nbw) {
+            T *col = Ps + c * kBMaxRows;
+            const T sg = (T)sig[c];
+            for (int r = j + 1 + lane; r < M; r += 32) col[r] = fma(sg, x[r], col[r]);
+            if (lane == 0) col[j] = fma(sg, upT, col[j]);
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        if (defined) Ps[j * kBMaxRows + j] = (T)cl;
+        tau[j] = tk;
+        ups[j] = upk;
+      }
+      __syncthreads();
+    }
+    // write the panel back; keep G and tau if asked; then turn the slice into
+    // V (zero above the diagonal, up on it) for the trailing update
+    for (int idx = tid; idx < nbw * M; idx += kThreads) {
+      int c = idx / M, r = idx - c * M;
+      A[SLQR_IDX(k0 + r, k0 + c, lda)] = Ps[c * kBMaxRows + r];
+    }
+    if (tid < nbw) up_out[k0 + tid] = ups[tid];
+    if (G_out) {
+      double *Gp = G_out + (size_t)(k0 / kBNB) * kBNB * kBNB;
+      for (int idx = tid; idx < kBNB * kBNB; idx += kThreads) {
+        int jj = idx / kBNB, q = idx - jj * kBNB;
+        Gp[idx] = (q < jj && jj < nbw) ? Gs[idx] : 0.0;
+      }
+      if (tid < kBNB) tau_out[k0 + tid] = (tid < nbw) ? tau[tid] : 0.0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kBNB * kBNB; idx += kThreads) {
+      int c = idx / kBNB, r = idx - c * kBNB;
+      if (r <= c && r < M) Ps[c * kBMaxRows + r] = (r == c && c < nbw) ? (T)ups[c] : T(0);
+    }
+    __syncthreads();
+
+    // trailing columns [k0 + nbw, n), plus Bcol as one more column
+    const int NT = n - (k0 + nbw);
+    const int NC = NT + (Bcol ? 1 : 0);
+    for (int t0 = 0; t0 < NC; t0 += kBCols) {
+      // phase A: W[a][col] = sum_r V[a][r] C[r][col]
+      for (int cc = warp; cc < kBCols; cc += kBWarps) {
+        const int col = t0 + cc;
+        if (col >= NC) break;
+        const T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (const T *)(Bcol + k0);
+        T acc[kBNB];
+#pragma unroll
+        for (int a = 0; a < kBNB; ++a) acc[a] = T(0);
+        for (int r = lane; r < M; r += 32) {
+          const T cv = C[r];
+#pragma unroll
+          for (int a = 0; a < kBNB; ++a)
+            if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < kBNB; ++a) {
+          T v = acc[a];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) Wt[a * (kBCols + 1) + cc] = v;
+        }
+      }
+      __syncthreads();
+      // phase B: W' = T^T W, one lane per column (FP64 arithmetic)
+      if (warp == 0 && t0 + lane < NC) {
+        double w[kBNB];
+#pragma unroll
+        for (int jj = 0; jj < kBNB; ++jj) {
+          if (jj < nbw) {
+            double t = (double)Wt[jj * (kBCols + 1) + lane];
+#pragma unroll
+            for (int q = 0; q < jj; ++q) t = fma(-Gs[q + jj * kBNB], w[q], t);
+            w[jj] = tau[jj] * t;
+            Wt[jj * (kBCols + 1) + lane] = (T)w[jj];
+          }
+        }
+      }
+      __syncthreads();
+      // phase C: C -= V W'
+      for (int cc = warp; cc < kBCols; cc += kBWarps) {
+        const int col = t0 + cc;
+        if (col >= NC) break;
+        T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (T *)(Bcol + k0);
+        T w[kBNB];
+#pragma unroll
+        for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
+        for (int r = lane; r < M; r += 32) {
+          T cv = C[r];
+#pragma unroll
+          for (int a = 0; a < kBNB; ++a)
+            if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
+          C[r] = cv;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Back-substitution R x = (Q^T b)[0:n] of the FP64 path, column-oriented.
+__device__ void batch_solve_fp64(const double *A, int lda, int n, double *b, double *xs,
+                                 int *status_out) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += kThreads) xs[i] = b[i];
+  __syncthreads();
+  bool rank_def = false;
+  for (int i = n - 1; i >= 0; --i) {
+    const double d = A[SLQR_IDX(i, i, lda)];
+    if (tid == 0) xs[i] = (d != 0.0) ? xs[i] / d : 0.0;
+    if (d == 0.0) rank_def = true;
+    __syncthreads();
+    const double xi = xs[i];
+    for (int l = tid; l < i; l += kThreads) xs[l] = fma(-A[SLQR_IDX(l, i, lda)], xi, xs[l]);
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += kThreads) b[i] = xs[i];
+  if (tid == 0) *status_out = rank_def ? SLQR_ERANK : SLQR_OK;
+  __syncthreads();
+}
+
+constexpr size_t kBSmemBytes = BatchSmem<double>::kBytes;
+
+__global__ void __launch_bounds__(kThreads)
+batch_factor_fp64_kernel(BatchParams bp) {
+  extern __shared__ __align__(16) char smraw[];
+  __shared__ int s_item;
+  __shared__ int s_status;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= bp.count) break;
+    const int p = bp.order[item];
+    const BatchProblem pr = bp.probs[p];
+    if (pr.n > 0) {
+      batch_factor_core<double>(pr.A, pr.lda, pr.m, pr.n, pr.up, pr.b, nullptr, nullptr, smraw);
+      if (pr.b) {
+        batch_solve_fp64(pr.A, pr.lda, pr.n, pr.b, (double *)smraw, &s_status);
+      } else if (threadIdx.x == 0) {
+        s_status = SLQR_OK;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && bp.status) bp.status[p] = s_status;
+    } else if (threadIdx.x == 0 && bp.status) {
+      bp.status[p] = SLQR_OK;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Mixed precision (SLQR_FP32): the factorization runs in FP32 on a scratch
+// copy of A (FP64 reflector constants), and the LS solution is recovered by
+// iterative refinement of the augmented system [I A; A^T 0][r; x] = [b; 0]
+// (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64 from the
+// original A, the correction through the FP32 QR:
+//   h = R^-T g,  d = Q^T f,  dx = R^-1 (d[0:n] - h),  dr = Q [h; d[n:m]].
+// This converges to the FP64 LS solution when kappa * u_fp32 < 1, for
+// consistent and inconsistent right-hand sides alike.
+// --------------------------------------------------------------------------
+struct BatchMixedParams {
+  const BatchProblem *probs;
+  const int *order;
+  int count;
+  unsigned *counter;
+  int *status;
+  double *err;
+  float *af;            // per CTA: kBMaxRows * kBMaxRows floats
+  double *gt;           // per CTA: G (kMaxPanels * kBNB^2) + tau (kBMaxRows) + up (kBMaxRows)
+  int max_it;
+  double tol;
+};
+
+constexpr int kBMaxPanels = kBMaxRows / kBNB;
+constexpr size_t kBGtDoubles = (size_t)kBMaxPanels * kBNB * kBNB + 2 * kBMaxRows;
+
+// V(i, a) of panel p from the FP32 factorization (rows relative to k0 = p*kBNB)
+__device__ __forceinline__ float mixed_v(const float *Af, int m, const double *up, int k0,
+                                         int nbw, int i, int a) {
+  if (a >= nbw || i < a) return 0.f;
+  if (i == a) return (float)up[k0 + a];
+  return Af[SLQR_IDX(k0 + i, k0 + a, m)];
+}
+
+// y <- Q^T y (forward = true) or y <- Q y, panel by panel, FP32 arithmetic.
+__device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, const double *tau,
+                              const double *up, float *y, float *w, bool forward) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = num_reflectors(m, n);
+  const int np = num_panels(K, kBNB);
+  for (int s = 0; s < np; ++s) {
+    const int pnl = forward ? s : np - 1 - s;
+    const int k0 = pnl * kBNB;
+    const int nbw = min(kBNB, K - k0);
+    const int M = m - k0;
+    // w[a] = sum_i V(i, a) y[k0 + i]
+    for (int a = warp; a < nbw; a += kBWarps) {
+      float acc = 0.f;
+      for (int i = lane; i < M; i += 32) acc = fmaf(mixed_v(Af, m, up, k0, nbw, i, a), y[k0 + i], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) w[a] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double *Gp = G + (size_t)pnl * kBNB * kBNB;
+      const double *tp = tau + k0;
+      double ww[kBNB];
+      if (forward) {      // T^T w: w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)
+        for (int j = 0; j < nbw; ++j) {
+          double t = w[j];
+          for (int q = 0; q < j; ++q) t -= Gp[q + j * kBNB] * ww[q];
+          ww[j] = tp[j] * t;
+        }
+      } else {            // T w: w''_j = tau_j (w_j - sum_{q>j} G[j,q] w''_q)
+        for (int j = nbw - 1; j >= 0; --j) {
+          double t = w[j];
+          for (int q = j + 1; q < nbw; ++q) t -= Gp[j + q * kBNB] * ww[q];
+          ww[j] = tp[j] * t;
+        }
+      }
+      for (int j = 0; j < nbw; ++j) w[j] = (float)ww[j];
+    }
+    __syncthreads();
+    for (int i = tid; i < M; i += kThreads) {
+      float v = y[k0 + i];
+      for (int a = 0; a < nbw; ++a) v = fmaf(-mixed_v(Af, m, up, k0, nbw, i, a), w[a], v);
+      y[k0 + i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Triangular solves with R = triu(Af[0:n, 0:n]) in FP32, column-oriented.
+// upper == true: R x = y (back); false: R^T x = y (forward).  y is replaced.
+__device__ bool mixed_trsv(const float *Af, int m, int n, float *y, bool upper) {
+  const int tid = threadIdx.x;
+  bool zero = false;
+  for (int s = 0; s < n; ++s) {
+    const int i = upper ? n - 1 - s : s;
+    const float d = Af[SLQR_IDX(i, i, m)];
+    if (d == 0.f) zero = true;
+    if (tid == 0) y[i] = (d != 0.f) ? y[i] / d : 0.f;
+    __syncthreads();
+    const float yi = y[i];
+    if (upper) {
+      for (int l = tid; l < i; l += kThreads) y[l] = fmaf(-Af[SLQR_IDX(l, i, m)], yi, y[l]);
+    } else {
+      for (int l = i + 1 + tid; l < n; l += kThreads) y[l] = fmaf(-Af[SLQR_IDX(i, l, m)], yi, y[l]);
+    }
+    __syncthreads();
+  }
+  return zero;
+}
+
+__device__ double block_max_abs(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = fabs(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < kBWarps; ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads)
+batch_factor_mixed_kernel(BatchMixedParams bp) {
+  extern __shared__ __align__(16) char smraw[];
+  __shared__ int s_item;
+  __shared__ double red[kBWarps];
+  float *Af = bp.af + (size_t)blockIdx.x * kBMaxRows * kBMaxRows;
+  double *G = bp.gt + (size_t)blockIdx.x * kBGtDoubles;
+  double *tau = G + (size_t)kBMaxPanels * kBNB * kBNB;
+  double *up = tau + kBMaxRows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(bp.counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= bp.count) break;
+    const int p = bp.order[item];
+    const BatchProblem pr = bp.probs[p];
+    const int m = pr.m, n = pr.n;
+    if (n == 0) {
+      if (tid == 0) {
+        if (bp.status) bp.status[p] = SLQR_OK;
+        if (bp.err) bp.err[p] = 0.0;
+      }
+      continue;
+    }
+    // FP32 working copy (ld = m), then the FP32 factorization
+    for (int idx = tid; idx < m * n; idx += kThreads) {
+      int c = idx / m, r = idx - c * m;
+      Af[idx] = (float)pr.A[SLQR_IDX(r, c, pr.lda)];
+    }
+    __syncthreads();
+    batch_factor_core<float>(Af, m, m, n, up, nullptr, G, tau, smraw);
+    __syncthreads();
+    // refinement vectors in shared memory (the panel area is free now)
+    double *x = (double *)smraw;          // n
+    double *r = x + kBMaxRows;            // m
+    double *dx = r + kBMaxRows;           // n (FP64 copy of the correction)
+    float *f = (float *)(dx + kBMaxRows); // m   f, then d = Q^T f, then dr
+    float *g = f + kBMaxRows;             // n   g, then h
+    float *e = g + kBMaxRows;             // m
+    float *w = e + kBMaxRows;             // kBNB
+    for (int i = tid; i < m; i += kThreads) r[i] = pr.b[i];
+    for (int i = tid; i < n; i += kThreads) x[i] = 0.0;
+    __syncthreads();
+    int status = SLQR_ENOCONV;
+    double err = 1.0, prev = 1e300;
+    for (int it = 0; it < bp.max_it; ++it) {
+      // f = b - r - A x (FP64), one thread per row
+      for (int i = tid; i < m; i += kThreads) {
+        double acc = pr.b[i] - r[i];
+        for (int j = 0; j < n; ++j) acc = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], acc);
+        f[i] = (float)acc;
+      }
+      // g = -A^T r (FP64), one warp per column
+      for (int j = warp; j < n; j += kBWarps) {
+        double acc = 0.0;
+        for (int i = lane; i < m; i += 32) acc = fma(pr.A[SLQR_IDX(i, j, pr.lda)], r[i], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) g[j] = (float)(-acc);
+      }
+      __syncthreads();
+      bool zero = mixed_trsv(Af, m, n, g, false);            // h = R^-T g (in g)
+      mixed_apply_q(Af, m, n, G, tau, up, f, w, true);        // d = Q^T f (in f)
+      for (int i = tid; i < m; i += kThreads) e[i] = (i < n) ? f[i] - g[i] : f[i];
+      __syncthreads();
+      zero |= mixed_trsv(Af, m, n, e, true);                 // dx = R^-1 (d1 - h) (in e[0:n])
+      for (int i = tid; i < n; i += kThreads) dx[i] = (double)e[i];
+      for (int i = tid; i < m; i += kThreads) f[i] = (i < n) ? g[i] : f[i];   // [h; d2]
+      __syncthreads();
+      mixed_apply_q(Af, m, n, G, tau, up, f, w, false);       // dr = Q [h; d2] (in f)
+      double dmax = 0.0, xmax = 0.0;
+      for (int i = tid; i < n; i += kThreads) {
+        x[i] += dx[i];
+        dmax = fmax(dmax, fabs(dx[i]));
+        xmax = fmax(xmax, fabs(x[i]));
+      }
+      for (int i = tid; i < m; i += kThreads) r[i] += (double)f[i];
+      dmax = block_max_abs(dmax, red);
+      xmax = block_max_abs(xmax, red);
+      err = (xmax > 0.0) ? dmax / xmax : 0.0;
+      if (zero) { status = SLQR_ERANK; break; }
+      if (err <= bp.tol) { status = SLQR_OK; break; }
+      if (it >= 2 && err > 0.5 * prev) {        // no longer contracting: FP64 noise level
+        status = (err <= kBStallOk) ? SLQR_OK : SLQR_ENOCONV;
+        break;
+      }
+      prev = err;
+    }
+    for (int i = tid; i < n; i += kThreads) pr.b[i] = x[i];
+    if (tid == 0) {
+      if (bp.status) bp.status[p] = status;
+      if (bp.err) bp.err[p] = err;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr size_t kBMixedSmemBytes = BatchSmem<float>::kBytes > 6 * kBMaxRows * sizeof(double)
+                                        ? BatchSmem<float>::kBytes
+                                        : 6 * kBMaxRows * sizeof(double);
+
+slqr_status init_batch_attrs(slqr_ctx *ctx) {
+  cudaError_t e = cudaFuncSetAttribute(batch_factor_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_factor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBMixedSmemBytes);
+  if (e != cudaSuccess)
+    return fail(ctx, SLQR_ECUDA, "cudaFuncSetAttribute(batch): %s", cudaGetErrorString(e));
+  return SLQR_OK;
+}
+
+}  // namespace slqr
+
+using namespace slqr;
+
+extern "C" int slqr_batch_max_rows(void) { return kBMaxRows; }
+
+extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
+                                         double *const *A, const int *lda, double *const *up,
+                                         double *const *b, int prec, int *status, double *err,
+                                         void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
+  if (count == 0) return SLQR_OK;
+  if (!m || !n || !A || !lda) return fail(ctx, SLQR_EINVAL, "NULL size or pointer array");
+  if (prec != SLQR_FP64 && prec != SLQR_FP32)
+    return fail(ctx, SLQR_EINVAL, "precision %d not available for batches", prec);
+  if (prec == SLQR_FP64 && !up) return fail(ctx, SLQR_EINVAL, "SLQR_FP64 needs the up arrays");
+  if (prec == SLQR_FP32 && !b) return fail(ctx, SLQR_EINVAL, "SLQR_FP32 needs the b arrays");
+  std::vector<BatchProblem> probs(count);
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 0 || m[i] < n[i] || m[i] > kBMaxRows)
+      return fail(ctx, SLQR_EINVAL, "problem %d: need %d >= m >= n >= 0 (m=%d n=%d)", i,
+                  kBMaxRows, m[i], n[i]);
+    if (n[i] > 0 && (lda[i] < std::max(1, m[i]) || !A[i] ||
+                     (prec == SLQR_FP64 && !up[i]) || (prec == SLQR_FP32 && !b[i])))
+      return fail(ctx, SLQR_EINVAL, "problem %d: bad lda or NULL pointer", i);
+    probs[i] = BatchProblem{A[i], up ? up[i] : nullptr, b ? b[i] : nullptr, m[i], n[i], lda[i], 0};
+    cost[i] = 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0 +
+              (b && b[i] ? 6.0 * m[i] * (double)n[i] : 0.0);
+  }
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  const bool mixed = (prec == SLQR_FP32);
+  int per_sm = 0;
+  if (mixed)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_factor_mixed_kernel, kThreads,
+                                                      kBMixedSmemBytes);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_factor_fp64_kernel, kThreads,
+                                                      kBSmemBytes);
+  if (e != cudaSuccess || per_sm < 1)
+    return fail(ctx, SLQR_ECUDA, "batch occupancy: %s", cudaGetErrorString(e));
+  const int grid = std::min(count, per_sm * ctx->num_sms);
+  // workspace: [counter 256 B][problem table][order][per-CTA scratch (mixed)]
+  const size_t table_bytes = align_up(sizeof(BatchProblem) * count, 256);
+  const size_t head = align_up(256 + table_bytes + sizeof(int) * count, 256);
+  const size_t af_bytes = mixed ? (size_t)grid * kBMaxRows * kBMaxRows * sizeof(float) : 0;
+  const size_t gt_bytes = mixed ? (size_t)grid * kBGtDoubles * sizeof(double) : 0;
+  slqr_status st = ensure_workspace(ctx, head + af_bytes + gt_bytes);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws.ptr;
+  unsigned *counter = (unsigned *)base;
+  BatchProblem *d_probs = (BatchProblem *)(base + 256);
+  int *d_order = (int *)(base + 256 + table_bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaMemsetAsync(counter, 0, 256, s);
+  // (copies from pageable host memory return once the source has been staged)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_probs, probs.data(), sizeof(BatchProblem) * count,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
+  double flops = 0.0;
+  for (int i = 0; i < count; ++i) flops += cost[i];
+  int slot = prof_begin(ctx, s);
+  if (!mixed) {
+    BatchParams bp{d_probs, d_order, count, counter, status};
+    batch_factor_fp64_kernel<<<grid, kThreads, kBSmemBytes, s>>>(bp);
+  } else {
+    BatchMixedParams mp{d_probs, d_order, count, counter, status, err,
+                        (float *)(base + head), (double *)(base + head + af_bytes),
+                        kBMaxRefine, kBRefineTol};
+    batch_factor_mixed_kernel<<<grid, kThreads, kBMixedSmemBytes, s>>>(mp);
+  }
+  prof_end(ctx, s, slot, kBatch, flops);
+  return check_launch(ctx, "batch_factor");
+}

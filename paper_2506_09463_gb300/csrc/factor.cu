@@ -85,13 +85,14 @@ __device__ __forceinline__ void record_status(int *status, int code) {
 // --------------------------------------------------------------------------
 // panel kernel
 // --------------------------------------------------------------------------
-constexpr int kPanelQpl = 5;                  // record loads per lane: P <= 32 * 5
-constexpr int kMaxPanelCtas = 32 * kPanelQpl;
+constexpr int kMaxPanelCtas = 160;
+
 struct PanelParams {
   double *A;
   double *up;          // global up array (n doubles)
   double *wy;          // this panel's compact-WY block (Vtop | G | tau)
-  double *rec;         // 2 * (NB+2) * P doubles, layout [buf][entry][cta]
+  double *rec;         // 2 * P * (NB+2) doubles, layout [buf][cta][entry]
+  double *gpart;       // P * NB*(NB-1)/2 doubles: per-CTA partial Gram terms
   double *prow;        // 2 * NB doubles
   unsigned *bar;       // monotonic arrival counter
   int *status;
@@ -100,15 +101,56 @@ struct PanelParams {
   unsigned bar_base;   // counter value when this panel starts
 };
 
+// Arrive at the grid barrier and wait (bounded) until `target` arrivals.
+// Returns false after recording SLQR_ETIMEOUT.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
+                                             int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    unsigned it = 0;
+    int ok = 1;
+    while (ld_acquire_u32(bar) < target) {
+      if (++it > kSpinLimit) { ok = 0; break; }
+      if (it > 256) __nanosleep(64);
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  if (!*s_ok) {
+    if (threadIdx.x == 0) record_status(status, SLQR_ETIMEOUT);
+    return false;
+  }
+  return true;
+}
+
+// One CTA per slice of R rows of the panel (rows [k0, m), NB columns); the
+// slice stays in shared memory for the whole panel.  Per column j:
+//   phase 1  local partials: scaled sum of squares of the column (from the
+//            pivot down) and dots of its tail with the later panel columns;
+//            the dots with the earlier columns (Gram terms of V^T V) are kept
+//            in a CTA-local accumulator;
+//   barrier
+//   phase 2  every CTA reduces the published partials: thread (g, c) sums
+//            entry c over its slice g of the CTAs, then the slices are added
+//            in a fixed order (the same order in every CTA);
+//   phase 3  pivot (cl, up, b, tau), sigma per later column, update.
+// At the end the local Gram terms are published and reduced once, each CTA
+// reducing its share of the entries into the compact-WY store.
 template <int NB>
 __global__ void __launch_bounds__(kThreads)
 panel_kernel(PanelParams p) {
   extern __shared__ double smem[];
   constexpr int NW = kThreads / 32;
   constexpr int CPW = (NB + NW - 1) / NW;     // columns per warp
-  constexpr int RECLEN = NB + 2;
+  constexpr int RECW = NB + 2;                // record: E, S, d_0 .. d_{NB-1}
+  constexpr int GROUPS = kThreads / NB;       // CTA slices of the reduction
   double *Ps = smem;                          // [NB][R] column-major panel slice
-  __shared__ double s_D[NB];                  // reduced dot products
+  double *Gloc = smem + (size_t)NB * p.R;     // [NB][NB] local Gram terms
+  __shared__ double s_part[GROUPS][NB];
+  __shared__ double s_partE[GROUPS], s_partS[GROUPS];
   __shared__ double s_sig[NB];                // sigma per column
   __shared__ double s_up[NB];
   __shared__ double s_prow[NB];               // pivot row of the current column
@@ -124,24 +166,24 @@ panel_kernel(PanelParams p) {
   double *A = p.A;
   const int lda = p.lda;
 
-  // load the slice of the panel
   for (int idx = tid; idx < nbw * R; idx += kThreads) {
     int c = idx / R, r = idx - c * R;
     Ps[c * R + r] = (r < RO) ? A[SLQR_IDX(row0 + r, p.k0 + c, lda)] : 0.0;
   }
+  for (int idx = tid; idx < NB * NB; idx += kThreads) Gloc[idx] = 0.0;
   double *G = p.wy + (size_t)NB * NB;
   double *tau = p.wy + 2 * (size_t)NB * NB;
   __syncthreads();
 
   for (int j = 0; j < nbw; ++j) {
     const int buf = j & 1;
-    double *rec = p.rec + (size_t)buf * RECLEN * p.P;
+    double *rec = p.rec + (size_t)buf * RECW * p.P;
+    double *myrec = rec + (size_t)cta * RECW;
     double *prow = p.prow + buf * NB;
-    // rows strictly below the pivot (tail) and from the pivot on (norm)
-    const int r_tail = (cta == 0) ? j + 1 : 0;
+    const int r_tail = (cta == 0) ? j + 1 : 0;       // rows strictly below the pivot
     const double *x = Ps + j * R;
 
-    // ---- phase 1: local partials ---------------------------------------
+    // ---- phase 1 ---------------------------------------------------------
     {
       double acc[CPW];
 #pragma unroll
@@ -162,8 +204,13 @@ panel_kernel(PanelParams p) {
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
         int c = warp + t * NW;
-        double v = warp_sum(acc[t]);
-        if (lane == 0 && c < nbw && c != j) rec[(size_t)(2 + c) * p.P + cta] = v;
+        if (c < nbw && c != j) {
+          double v = warp_sum(acc[t]);
+          if (lane == 0) {
+            if (c > j) myrec[2 + c] = v;                 // published: needed for sigma
+            else Gloc[c + j * NB] = v;                   // kept: Gram term
+          }
+        }
       }
       if (norm_warp) {
 #pragma unroll
@@ -173,78 +220,46 @@ panel_kernel(PanelParams p) {
           ssq_merge(E, S, E2, S2);
         }
         if (lane == 0) {
-          rec[0 * (size_t)p.P + cta] = (double)E;
-          rec[1 * (size_t)p.P + cta] = S;
+          myrec[0] = (double)E;
+          myrec[1] = S;
         }
       }
       if (cta == 0 && tid < nbw) prow[tid] = Ps[tid * R + j];
     }
 
-    // ---- grid barrier -----------------------------------------------------
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(p.bar, 1u);
-      const unsigned target = p.bar_base + (unsigned)(j + 1) * (unsigned)p.P;
-      unsigned it = 0;
-      int ok = 1;
-      while (ld_acquire_u32(p.bar) < target) {
-        if (++it > kSpinLimit) { ok = 0; break; }
-        if (it > 256) __nanosleep(64);
-      }
-      __threadfence();
-      s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) {
-      if (tid == 0) record_status(p.status, SLQR_ETIMEOUT);
+    // ---- grid barrier ----------------------------------------------------
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(j + 1) * (unsigned)p.P, p.status, &s_ok))
       return;
-    }
 
-    // ---- phase 2: every CTA reduces the partials in the same fixed order ---
-    // Warp w owns entries e = w, w + NW, ... (e == 0: the norm pair, e >= 1:
-    // the dot with panel column e - 1).  All loads of a lane are issued before
-    // any is used, so the reduction costs about one L2 round trip.
+    // ---- phase 2 ---------------------------------------------------------
     {
-      constexpr int EPW = (NB + 1 + NW - 1) / NW;
-      const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;  // in flight with the rest
-      double sum[EPW];
-#pragma unroll
-      for (int ee = 0; ee < EPW; ++ee) sum[ee] = 0.0;
-      int E = kNoExp;
-      double S = 0.0;
-#pragma unroll
-      for (int i = 0; i < kPanelQpl; ++i) {
-        const int q = lane + 32 * i;
-        if (q < p.P) {
-#pragma unroll
-          for (int ee = 0; ee < EPW; ++ee) {
-            const int e = warp + NW * ee;
-            if (e >= 1 && e <= nbw && e - 1 != j)
-              sum[ee] += __ldcg(rec + (size_t)(2 + (e - 1)) * p.P + q);
-          }
-          if (warp == 0) {
-            double Eq = __ldcg(rec + q), Sq = __ldcg(rec + p.P + q);
-            ssq_merge(E, S, (int)Eq, Sq);
-          }
+      const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
+      const int g = tid / NB, c = tid - g * NB;
+      const int per = (p.P + GROUPS - 1) / GROUPS;
+      const int q0 = g * per, q1 = min(p.P, q0 + per);
+      if (c > j && c < nbw) {
+        double v = 0.0;
+#pragma unroll 4
+        for (int q = q0; q < q1; ++q) v += __ldcg(rec + (size_t)q * RECW + 2 + c);
+        s_part[g][c] = v;
+      } else if (c == j) {
+        int E = kNoExp;
+        double S = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          double Eq = __ldcg(rec + (size_t)q * RECW), Sq = __ldcg(rec + (size_t)q * RECW + 1);
+          ssq_merge(E, S, (int)Eq, Sq);
         }
-      }
-#pragma unroll
-      for (int ee = 0; ee < EPW; ++ee) {
-        const int e = warp + NW * ee;
-        double v = warp_sum(sum[ee]);
-        if (lane == 0 && e >= 1 && e <= nbw) s_D[e - 1] = v;
-      }
-      if (warp == 0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          int E2 = __shfl_xor_sync(0xffffffffu, E, o);
-          double S2 = __shfl_xor_sync(0xffffffffu, S, o);
-          ssq_merge(E, S, E2, S2);
-        }
-        if (lane == 0) s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
+        s_partE[g] = (double)E;
+        s_partS[g] = S;
       }
       if (tid < nbw) s_prow[tid] = prow_v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int E = kNoExp;
+      double S = 0.0;
+      for (int g = 0; g < GROUPS; ++g) ssq_merge(E, S, (int)s_partE[g], s_partS[g]);
+      s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
     }
     __syncthreads();
 
@@ -260,13 +275,16 @@ panel_kernel(PanelParams p) {
       tk = -1.0 / bk;
     }
     if (tid < nbw) {
-      int c = tid;
-      double pr = s_prow[c];
+      const int c = tid;
       if (c > j) {
-        s_sig[c] = defined ? (upk * pr + s_D[c]) / bk : 0.0;
+        double D = s_part[0][c];
+#pragma unroll
+        for (int g = 1; g < GROUPS; ++g) D += s_part[g][c];
+        s_sig[c] = defined ? (upk * s_prow[c] + D) / bk : 0.0;
       } else if (c < j && cta == 0) {
-        // G[c, j] = v_c^T v_j = v_c[k] * up_j + sum_{r > k} v_c[r] x_r
-        G[c + j * NB] = pr * upk + s_D[c];
+        // G[c, j] = v_c^T v_j = v_c[k] up_j + sum_{r > k} v_c[r] x_r: the first
+        // term is added once, by CTA 0
+        Gloc[c + j * NB] += s_prow[c] * upk;
       }
     }
     if (cta == 0 && tid == 0) {
@@ -300,6 +318,26 @@ panel_kernel(PanelParams p) {
     int c = idx / R, r = idx - c * R;
     if (r < RO) A[SLQR_IDX(row0 + r, p.k0 + c, lda)] = Ps[c * R + r];
   }
+  // publish the local Gram terms and reduce them: CTA q owns entries q, q+P, ..
+  constexpr int NT = NB * (NB - 1) / 2;       // strict upper triangle, packed by column
+  {
+    double *mine = p.gpart + (size_t)cta * NT;
+    for (int idx = tid; idx < NB * NB; idx += kThreads) {
+      const int jj = idx / NB, c = idx - jj * NB;
+      if (c < jj) mine[jj * (jj - 1) / 2 + c] = Gloc[idx];
+    }
+  }
+  if (!grid_barrier(p.bar, p.bar_base + (unsigned)(nbw + 1) * (unsigned)p.P, p.status, &s_ok))
+    return;
+  for (int idx = cta + tid * p.P; idx < NB * NB; idx += kThreads * p.P) {
+    const int jj = idx / NB, c = idx - jj * NB;
+    double v = 0.0;
+    if (c < jj && jj < nbw) {
+      const int pos = jj * (jj - 1) / 2 + c;
+      for (int q = 0; q < p.P; ++q) v += __ldcg(p.gpart + (size_t)q * NT + pos);
+    }
+    G[idx] = v;
+  }
   if (cta == 0) {
     // Vtop (ld NB): zero above the diagonal, up on it, tails below
     double *Vtop = p.wy;
@@ -311,8 +349,6 @@ panel_kernel(PanelParams p) {
         else if (r > c) v = Ps[c * R + r];
       }
       Vtop[idx] = v;
-      if (r >= c) G[idx] = 0.0;                 // keep only the strict upper part
-      if (c >= nbw && r < c) G[idx] = 0.0;
     }
     for (int c = nbw + tid; c < NB; c += kThreads) tau[c] = 0.0;
   }
@@ -396,43 +432,37 @@ gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict_
   }
 }
 
-// W'[a][c] = (T^T W)[a][c] for 64 columns per CTA: reduce the S partials of
-// each column (coalesced, all loads of a thread in flight together), then the
-// forward substitution  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)  with four
-// lanes per column splitting the inner sum.
+// W'[a][c] = (T^T W)[a][c].  Each CTA owns kThreads / NB columns and each
+// thread one (column, reflector) entry: it sums that entry's S partials in a
+// fixed order (coalesced loads, all of a thread's loads independent).  Then
+// one warp does the forward substitution
+//   w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)
+// with four lanes per column splitting the inner sum.
 template <int NB>
 __global__ void __launch_bounds__(kThreads)
 tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
           double *__restrict__ Wt) {
-  constexpr int COLS = 64;
-  constexpr int EPT = NB * COLS / kThreads;     // entries per thread
+  constexpr int COLS = kThreads / NB;           // 4 (NB = 64) or 8 (NB = 32)
   __shared__ double w[NB][COLS + 1];
   const int tid = threadIdx.x;
   const double *G = wy + (size_t)NB * NB;
   const double *tau = wy + 2 * (size_t)NB * NB;
   const int c0 = blockIdx.x * COLS;
-  double acc[EPT];
-#pragma unroll
-  for (int i = 0; i < EPT; ++i) acc[i] = 0.0;
-  for (int s = 0; s < S; ++s) {
-    const double *src = Wp + ((size_t)s * N + c0) * NB;
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int idx = tid + kThreads * i;       // (c, a) with a fastest
-      const int c = idx / NB, a = idx - c * NB;
-      if (c0 + c < N) acc[i] += src[idx];
-      (void)a;
+  {
+    const int c = tid / NB, a = tid - c * NB;    // entry (column c0 + c, reflector a)
+    double acc = 0.0;
+    if (c0 + c < N) {
+      const double *src = Wp + (size_t)(c0 + c) * NB + a;
+      const size_t stride = (size_t)N * NB;
+#pragma unroll 8
+      for (int s = 0; s < S; ++s) acc += src[(size_t)s * stride];
     }
-  }
-#pragma unroll
-  for (int i = 0; i < EPT; ++i) {
-    const int idx = tid + kThreads * i;
-    const int c = idx / NB, a = idx - c * NB;
-    w[a][c] = acc[i];
+    w[a][c] = acc;
   }
   __syncthreads();
-  {
-    const int c = tid >> 2, part = tid & 3;
+  if (tid < 32) {                               // the whole first warp takes part
+    const int c = min(tid >> 2, COLS - 1), part = tid & 3;
+    const bool owner = (tid >> 2) < COLS && part == 0;
     for (int j = 0; j < nbw; ++j) {
       double t = 0.0;
       for (int q = part; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
@@ -440,15 +470,13 @@ tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict_
       t += __shfl_xor_sync(0xffffffffu, t, 2);
       const double wj = __ldg(tau + j) * (w[j][c] - t);
       __syncwarp();
-      if (part == 0) w[j][c] = wj;
+      if (owner) w[j][c] = wj;
       __syncwarp();
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < EPT; ++i) {
-    const int idx = tid + kThreads * i;         // (a, c) with c fastest
-    const int a = idx / COLS, c = idx - a * COLS;
+  {
+    const int a = tid / COLS, c = tid - a * COLS;
     if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? w[a][c] : 0.0;
   }
 }
@@ -552,7 +580,8 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
       A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  tw_kernel<NB><<<(N + 63) / 64, kThreads, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  tw_kernel<NB><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
+      Wp, Seff, N, wy_panel, nbw, Wt);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
   slot = prof_begin(ctx, stream);
@@ -600,7 +629,9 @@ static int panel_rows_per_cta(int M, int nbw, int num_sms) {
   return R;
 }
 
-static int max_rows_per_cta(int nb) { return (200 * 1024) / (nb * (int)sizeof(double)); }
+static int max_rows_per_cta(int nb) {
+  return (200 * 1024 - nb * nb * (int)sizeof(double)) / (nb * (int)sizeof(double));
+}
 
 template <int NB>
 static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
@@ -610,16 +641,19 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
   // workspace: [bar (256 B)] [records] [prow] [wy if none given] [trailing work]
   const int Pmax = ctx->num_sms;
   const size_t rec_doubles = 2 * (size_t)(NB + 2) * Pmax;
+  const size_t gpart_doubles = (size_t)Pmax * NB * (NB - 1) / 2;
   const size_t prow_doubles = 2 * (size_t)NB;
   const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
   const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms);
-  const size_t bytes = 256 + (rec_doubles + prow_doubles + wy_doubles + work_doubles) * 8;
+  const size_t bytes =
+      256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles + work_doubles) * 8;
   slqr_status st = ensure_workspace(ctx, bytes);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws.ptr;
   unsigned *bar = (unsigned *)base;
   double *rec = (double *)(base + 256);
-  double *prow = rec + rec_doubles;
+  double *gpart = rec + rec_doubles;
+  double *prow = gpart + gpart_doubles;
   double *wy_store = wy ? wy : prow + prow_doubles;
   double *work = prow + prow_doubles + wy_doubles;
 
@@ -648,11 +682,12 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
     PanelParams pp;
-    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.prow = prow; pp.bar = bar;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
+    pp.bar = bar;
     pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
-    size_t smem = (size_t)NB * R * sizeof(double);
+    size_t smem = ((size_t)NB * R + (size_t)NB * NB) * sizeof(double);
     // algorithmic flops of the panel: per column j a norm over M-j entries and,
     // for each later panel column, a dot and an axpy over M-j entries
     double pflops = 0.0;
@@ -664,7 +699,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     if (le != cudaSuccess)
       return fail(ctx, SLQR_ECUDA, "panel launch (P=%d, smem=%zu): %s", P, smem,
                   cudaGetErrorString(le));
-    bar_base += (unsigned)P * (unsigned)nbw;
+    bar_base += (unsigned)P * (unsigned)(nbw + 1);
     return SLQR_OK;
   };
   auto update = [&](int pnl, int c_begin, int c_end) -> slqr_status {
@@ -755,14 +790,15 @@ constexpr int kNoAllocMaxSms = 256;
 constexpr int kNoAllocMaxDevices = 64;
 constexpr size_t kNoAllocHeadDoubles = 32;                       // 256 B: counter + status
 constexpr size_t kNoAllocRecDoubles = 2 * (64 + 2) * (size_t)kNoAllocMaxSms;
+constexpr size_t kNoAllocGpartDoubles = (size_t)kMaxPanelCtas * 64 * 63 / 2;
 constexpr size_t kNoAllocProwDoubles = 2 * 64;
 constexpr size_t kNoAllocWyDoubles = (kNoAllocMaxCols / 64) * (2 * 64 * 64 + 64);
-constexpr size_t kNoAllocWorkDoubles = 512 * 1024;
+constexpr size_t kNoAllocWorkDoubles = 384 * 1024;
 constexpr size_t kNoAllocScratchDoubles = kNoAllocHeadDoubles + kNoAllocRecDoubles +
-                                          kNoAllocProwDoubles + kNoAllocWyDoubles +
-                                          kNoAllocWorkDoubles;
+                                          kNoAllocGpartDoubles + kNoAllocProwDoubles +
+                                          kNoAllocWyDoubles + kNoAllocWorkDoubles;
 
-// About 5.3 MB on every device that loads the library, held until exit.
+// About 6.9 MB on every device that loads the library, held until exit.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 static std::mutex g_noalloc_mu;
@@ -832,7 +868,8 @@ static slqr_status noalloc_update(int num_sms, int m, int k0, int nbw, const dou
   double *Wt = work + (size_t)Seff * N * NB;
   gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, RS, Wp);
-  tw_kernel<NB><<<(N + 63) / 64, kThreads, 0, stream>>>(Wp, Seff, N, wy_panel, nbw, Wt);
+  tw_kernel<NB><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
+      Wp, Seff, N, wy_panel, nbw, Wt);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
   gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, Wt);
@@ -848,7 +885,8 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
   unsigned *bar = (unsigned *)scratch;
   if (!status) status = (int *)(scratch + 16);
   double *rec = scratch + kNoAllocHeadDoubles;
-  double *prow = rec + kNoAllocRecDoubles;
+  double *gpart = rec + kNoAllocRecDoubles;
+  double *prow = gpart + kNoAllocGpartDoubles;
   double *wy_store = wy ? wy : prow + kNoAllocProwDoubles;
   double *work = prow + kNoAllocProwDoubles + kNoAllocWyDoubles;
   // the array keeps the previous call's contents: clear the counter and status
@@ -865,15 +903,16 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
     PanelParams pp;
-    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.prow = prow; pp.bar = bar;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
+    pp.bar = bar;
     pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
-    size_t smem = (size_t)NB * R * sizeof(double);
+    size_t smem = ((size_t)NB * R + (size_t)NB * NB) * sizeof(double);
     e = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P), dim3(kThreads), args,
                                     smem, stream);
     if (e != cudaSuccess) return SLQR_ECUDA;
-    bar_base += (unsigned)P * (unsigned)nbw;
+    bar_base += (unsigned)P * (unsigned)(nbw + 1);
     const int N = n - (k0 + nbw);
     if (N > 0) {
       slqr_status st = noalloc_update<NB>(num_sms, m, k0, nbw, A, lda, wy_panel,

@@ -34,7 +34,10 @@ struct Workspace {
 };
 
 // Kernel families timed by the optional profiler (slqr_profile).
-enum KernelId { kPanel = 0, kVtx = 1, kTw = 2, kUpd = 3, kWyRebuild = 4, kTrsm = 5, kNumKernelIds = 6 };
+enum KernelId {
+  kPanel = 0, kVtx = 1, kTw = 2, kUpd = 3, kWyRebuild = 4, kTrsm = 5, kBatch = 6,
+  kNumKernelIds = 7
+};
 
 struct ProfRecord {
   cudaEvent_t start, stop;
@@ -87,6 +90,7 @@ void prof_end(slqr_ctx *ctx, cudaStream_t stream, int slot, int kid, double flop
 
 // Opt kernels into large dynamic shared memory (once per device).
 slqr_status init_kernel_attrs(slqr_ctx *ctx);
+slqr_status init_batch_attrs(slqr_ctx *ctx);
 
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);

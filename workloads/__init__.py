@@ -99,6 +99,27 @@ def batch_problems(ms, ns, seed: int = SEED_BATCH):
     return out
 
 
+def batch_problems_device(ms, ns, seed: int = SEED_BATCH, device="cuda", with_rhs=True):
+    """All problems of a batch drawn on the device in one seeded stream.
+
+    Returns (A_flat, b_flat, a_off, b_off): problem i is the column-major
+    m_i x n_i block A_flat[a_off[i] : a_off[i] + m_i*n_i] (lda = m_i) and its
+    right-hand side b_flat[b_off[i] : b_off[i] + m_i]; entries iid N(0,1).
+    """
+    import torch
+    ms = [int(m) for m in ms]
+    ns = [int(n) for n in ns]
+    a_sizes = np.array([m * n for m, n in zip(ms, ns)], dtype=np.int64)
+    b_sizes = np.array(ms, dtype=np.int64)
+    a_off = np.concatenate([[0], np.cumsum(a_sizes)[:-1]]) if len(ms) else np.zeros(0, np.int64)
+    b_off = np.concatenate([[0], np.cumsum(b_sizes)[:-1]]) if len(ms) else np.zeros(0, np.int64)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A_flat = torch.randn(int(a_sizes.sum()) + 1, generator=g, dtype=torch.float64, device=device)
+    b_flat = torch.randn(int(b_sizes.sum()) + 1, generator=g, dtype=torch.float64, device=device)
+    return A_flat, b_flat, a_off, b_off
+
+
 def slsqp_stack(n: int, m_eq: int, seed: int):
     """(A, b): A = [L^T; C] of shape (n + m_eq) x n, b ~ N(0,1).
 
