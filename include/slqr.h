@@ -194,6 +194,66 @@ slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int 
 int slqr_batch_max_rows(void);
 
 /*
+ * Request loop: continuous batching of least-squares subproblems from many
+ * concurrent SLSQP runs (each one factors its QP matrix and later
+ * back-substitutes with the stored factorization, Section 1).  The first
+ * slqr_submit starts a worker thread in the context; slqr_destroy stops it
+ * after the requests in flight finish.
+ *
+ * Kinds:
+ *   SLQR_REQ_FACTOR        factor A (m x n, m >= n >= 1) and keep the
+ *                          factorization on the device under a new handle
+ *                          (returned in slqr_result.handle)
+ *   SLQR_REQ_SOLVE         x = argmin ||A x - b|| with the resident
+ *                          factorization of `handle` (Q^T b, back-substitution)
+ *   SLQR_REQ_FACTOR_SOLVE  both, nothing kept
+ *   SLQR_REQ_RELEASE       free the factorization of `handle`
+ * Admission is in arrival order and by the context's HBM budget (bytes held
+ * by resident factorizations and requests in flight); a request that cannot
+ * fit waits until memory is freed, and one larger than the whole budget
+ * fails with SLQR_EBUSY.  Admitted requests with m <= slqr_batch_max_rows()
+ * of one precision share one persistent batched launch; larger ones run one
+ * per stream on a pool of streams; all of them overlap on the device.
+ * Requests that arrive while others run are admitted as memory frees up.
+ *
+ * A, b and x are HOST pointers owned by the caller; they must stay valid
+ * until slqr_poll reports the request done (A and b are copied in at
+ * admission; x receives n doubles at completion).  prec: SLQR_FP64, or
+ * SLQR_FP32 for FACTOR_SOLVE with m <= slqr_batch_max_rows() (FP32
+ * factorization with FP64-residual refinement, see slqr_batch_factor).
+ * slqr_poll returns SLQR_PENDING until the request is done, then SLQR_OK with
+ * *out filled (out->status is the request's own status) and forgets the
+ * ticket; SLQR_ENOTFOUND for an unknown or already collected ticket.
+ */
+#define SLQR_REQ_FACTOR       1
+#define SLQR_REQ_SOLVE        2
+#define SLQR_REQ_FACTOR_SOLVE 3
+#define SLQR_REQ_RELEASE      4
+
+typedef struct {
+  int kind;
+  int m, n, lda;
+  const double *A;      /* host, column-major m x n (FACTOR, FACTOR_SOLVE) */
+  const double *b;      /* host, m doubles (SOLVE, FACTOR_SOLVE) */
+  double *x;            /* host, n doubles, written at completion */
+  uint64_t handle;      /* SOLVE, RELEASE */
+  int prec;             /* SLQR_FP64 or SLQR_FP32 */
+} slqr_request;
+
+typedef struct {
+  int status;           /* SLQR_OK, SLQR_ERANK, SLQR_ENOCONV, SLQR_EBUSY, SLQR_ENOTFOUND, ... */
+  uint64_t handle;      /* FACTOR: the handle of the resident factorization */
+  double residual_norm; /* solves: ||b - A x|| (FP64: ||(Q^T b)[n:m]||) */
+  double latency_ms;    /* from slqr_submit to completion */
+  double err;           /* SLQR_FP32: last refinement step ||dx|| / ||x|| */
+} slqr_result;
+
+slqr_status slqr_submit(slqr_ctx *ctx, const slqr_request *req, uint64_t *ticket);
+slqr_status slqr_poll(slqr_ctx *ctx, uint64_t ticket, slqr_result *out);
+/* Device bytes the request loop holds now (resident factorizations included). */
+size_t slqr_server_bytes_in_use(slqr_ctx *ctx);
+
+/*
  * slqr_factor_noalloc -- the factorization of slqr_factor for callers that
  * must not allocate device memory.  The paper has no counterpart: this entry
  * point exists for embedding.  Some callers cannot call cudaMalloc: a host

@@ -29,10 +29,27 @@ SLQR_EBUSY = -6
 SLQR_ENOTFOUND = -7
 
 STATUS_NAMES = {
+    -8: "SLQR_ENOCONV",
     SLQR_OK: "SLQR_OK", SLQR_PENDING: "SLQR_PENDING", SLQR_EINVAL: "SLQR_EINVAL",
     SLQR_ENOMEM: "SLQR_ENOMEM", SLQR_ECUDA: "SLQR_ECUDA", SLQR_ETIMEOUT: "SLQR_ETIMEOUT",
     SLQR_ERANK: "SLQR_ERANK", SLQR_EBUSY: "SLQR_EBUSY", SLQR_ENOTFOUND: "SLQR_ENOTFOUND",
 }
+
+SLQR_ENOCONV = -8
+SLQR_REQ_FACTOR, SLQR_REQ_SOLVE, SLQR_REQ_FACTOR_SOLVE, SLQR_REQ_RELEASE = 1, 2, 3, 4
+
+
+class SlqrRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("lda", ctypes.c_int), ("A", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("handle", ctypes.c_uint64), ("prec", ctypes.c_int)]
+
+
+class SlqrResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("handle", ctypes.c_uint64),
+                ("residual_norm", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("err", ctypes.c_double)]
+
 
 # (name, restype, argtypes) of every entry point declared in include/slqr.h
 _c_int, _c_size, _vp, _dbl = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_double
@@ -57,6 +74,9 @@ SIGNATURES = [
                                    ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, _vp, _vp,
                                    _vp]),
     ("slqr_batch_max_rows", _c_int, []),
+    ("slqr_submit", _c_int, [_vp, ctypes.POINTER(SlqrRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    ("slqr_poll", _c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(SlqrResult)]),
+    ("slqr_server_bytes_in_use", _c_size, [_vp]),
     ("slqr_noalloc_max_rows", _c_int, []),
     ("slqr_noalloc_max_cols", _c_int, []),
 ]
@@ -170,6 +190,24 @@ def slqr_batch_factor(ctx, m_list, n_list, A_ptrs, lda_list, up_ptrs, b_ptrs, pr
 
 def slqr_batch_max_rows() -> int:
     return _lib.slqr_batch_max_rows()
+
+
+def slqr_submit(ctx, req: SlqrRequest):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64()
+    st = _lib.slqr_submit(ctx, ctypes.byref(req), ctypes.byref(t))
+    return st, t.value
+
+
+def slqr_poll(ctx, ticket: int):
+    """Returns (status, SlqrResult): SLQR_PENDING until the request is done."""
+    out = SlqrResult()
+    st = _lib.slqr_poll(ctx, ticket, ctypes.byref(out))
+    return st, out
+
+
+def slqr_server_bytes_in_use(ctx) -> int:
+    return _lib.slqr_server_bytes_in_use(ctx)
 
 
 def slqr_factor_noalloc(m, n, A, lda, up, wy, status, stream) -> int:

@@ -119,3 +119,62 @@ class Context:
         self.apply_qt(A, up, b, stream=stream)
         self.solve_r(A, b, stream=stream)
         return b[:A.shape[1]], up
+
+
+class Server:
+    """Host-side helper over slqr_submit / slqr_poll for numpy inputs.
+
+    Keeps every request's host buffers alive until its result is collected
+    (the C ABI reads A and b at admission and writes x at completion)."""
+
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+        self._live = {}
+
+    def submit(self, kind, A=None, b=None, handle=0, prec=abi.SLQR_FP64, m=None, n=None):
+        import numpy as np
+        req = abi.SlqrRequest()
+        req.kind = kind
+        keep = []
+        if A is not None:
+            A = np.asfortranarray(A, dtype=np.float64)
+            keep.append(A)
+            req.m, req.n = A.shape
+            req.lda = A.shape[0]
+            req.A = A.ctypes.data
+        if b is not None:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            keep.append(b)
+            req.b = b.ctypes.data
+            nx = n if n is not None else (A.shape[1] if A is not None else b.shape[0])
+            x = np.zeros(nx, dtype=np.float64)
+            keep.append(x)
+            req.x = x.ctypes.data
+        else:
+            x = None
+        req.handle = handle
+        req.prec = prec
+        st, t = abi.slqr_submit(self.ctx.ctx, req)
+        abi.check(self.ctx.ctx, st, "slqr_submit")
+        self._live[t] = (keep, x)
+        return t
+
+    def poll(self, ticket):
+        """None while pending; (result, x) when done."""
+        st, res = abi.slqr_poll(self.ctx.ctx, ticket)
+        if st == abi.SLQR_PENDING:
+            return None
+        abi.check(self.ctx.ctx, st, "slqr_poll")
+        keep, x = self._live.pop(ticket)
+        return res, x
+
+    def wait(self, ticket, timeout_s=120.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
+            time.sleep(0.0002)

@@ -182,6 +182,7 @@ extern "C" slqr_status slqr_create(slqr_ctx **out, int device, size_t hbm_budget
 
 extern "C" void slqr_destroy(slqr_ctx *ctx) {
   if (!ctx) return;
+  server_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   prof_collect(ctx);

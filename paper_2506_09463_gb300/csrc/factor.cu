@@ -88,7 +88,7 @@ __device__ __forceinline__ void record_status(int *status, int code) {
 constexpr int kMaxPanelCtas = 160;
 
 struct PanelParams {
-  double *A;
+  void *A;             // T * (the storage type of the factorization)
   double *up;          // global up array (n doubles)
   double *wy;          // this panel's compact-WY block (Vtop | G | tau)
   double *rec;         // 2 * P * (NB+2) doubles, layout [buf][cta][entry]
@@ -139,16 +139,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
 //   phase 3  pivot (cl, up, b, tau), sigma per later column, update.
 // At the end the local Gram terms are published and reduced once, each CTA
 // reducing its share of the entries into the compact-WY store.
-template <int NB>
+template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads)
 panel_kernel(PanelParams p) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NW = kThreads / 32;
   constexpr int CPW = (NB + NW - 1) / NW;     // columns per warp
   constexpr int RECW = NB + 2;                // record: E, S, d_0 .. d_{NB-1}
   constexpr int GROUPS = kThreads / NB;       // CTA slices of the reduction
-  double *Ps = smem;                          // [NB][R] column-major panel slice
-  double *Gloc = smem + (size_t)NB * p.R;     // [NB][NB] local Gram terms
+  T *Ps = (T *)smem_raw;                      // [NB][R] column-major panel slice
+  double *Gloc = (double *)(smem_raw + ((size_t)NB * p.R * sizeof(T) + 15) / 16 * 16);
+                                              // [NB][NB] local Gram terms
   __shared__ double s_part[GROUPS][NB];
   __shared__ double s_partE[GROUPS], s_partS[GROUPS];
   __shared__ double s_sig[NB];                // sigma per column
@@ -163,12 +164,12 @@ panel_kernel(PanelParams p) {
   const int row0 = p.k0 + cta * R;                 // first global row of this slice
   const int RO = min(R, p.m - row0);               // rows owned
   const int nbw = p.nbw;
-  double *A = p.A;
+  T *A = (T *)p.A;
   const int lda = p.lda;
 
   for (int idx = tid; idx < nbw * R; idx += kThreads) {
     int c = idx / R, r = idx - c * R;
-    Ps[c * R + r] = (r < RO) ? A[SLQR_IDX(row0 + r, p.k0 + c, lda)] : 0.0;
+    Ps[c * R + r] = (r < RO) ? A[SLQR_IDX(row0 + r, p.k0 + c, lda)] : T(0);
   }
   for (int idx = tid; idx < NB * NB; idx += kThreads) Gloc[idx] = 0.0;
   double *G = p.wy + (size_t)NB * NB;
@@ -181,31 +182,34 @@ panel_kernel(PanelParams p) {
     double *myrec = rec + (size_t)cta * RECW;
     double *prow = p.prow + buf * NB;
     const int r_tail = (cta == 0) ? j + 1 : 0;       // rows strictly below the pivot
-    const double *x = Ps + j * R;
+    const T *x = Ps + j * R;
 
     // ---- phase 1 ---------------------------------------------------------
     {
-      double acc[CPW];
+      T acc[CPW];
 #pragma unroll
-      for (int t = 0; t < CPW; ++t) acc[t] = 0.0;
+      for (int t = 0; t < CPW; ++t) acc[t] = T(0);
       int E = kNoExp;
       double S = 0.0;
       const bool norm_warp = (warp == (j % NW));
       for (int r = r_tail + lane; r < RO; r += 32) {
-        double xv = x[r];
+        T xv = x[r];
 #pragma unroll
         for (int t = 0; t < CPW; ++t) {
           int c = warp + t * NW;
           if (c < nbw && c != j) acc[t] = fma(xv, Ps[c * R + r], acc[t]);
         }
-        if (norm_warp) ssq_add(E, S, xv);
+        if (norm_warp) ssq_add(E, S, (double)xv);
       }
-      if (norm_warp && cta == 0 && lane == 0) ssq_add(E, S, x[j]);  // pivot entry
+      if (norm_warp && cta == 0 && lane == 0) ssq_add(E, S, (double)x[j]);  // pivot entry
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
         int c = warp + t * NW;
         if (c < nbw && c != j) {
-          double v = warp_sum(acc[t]);
+          T vt = acc[t];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) vt += __shfl_xor_sync(0xffffffffu, vt, o);
+          const double v = (double)vt;
           if (lane == 0) {
             if (c > j) myrec[2 + c] = v;                 // published: needed for sigma
             else Gloc[c + j * NB] = v;                   // kept: Gram term
@@ -224,7 +228,7 @@ panel_kernel(PanelParams p) {
           myrec[1] = S;
         }
       }
-      if (cta == 0 && tid < nbw) prow[tid] = Ps[tid * R + j];
+      if (cta == 0 && tid < nbw) prow[tid] = (double)Ps[tid * R + j];
     }
 
     // ---- grid barrier ----------------------------------------------------
@@ -299,15 +303,15 @@ panel_kernel(PanelParams p) {
       for (int t = 0; t < CPW; ++t) {
         int c = warp + t * NW;
         if (c > j && c < nbw) {
-          const double sg = s_sig[c];
-          double *col = Ps + c * R;
+          const T sg = (T)s_sig[c];
+          T *col = Ps + c * R;
           for (int r = r_tail + lane; r < RO; r += 32) col[r] = fma(sg, x[r], col[r]);
         }
       }
       if (cta == 0) {
         int c = tid;
-        if (c > j && c < nbw) Ps[c * R + j] = fma(s_sig[c], upk, Ps[c * R + j]);
-        if (tid == 0) Ps[j * R + j] = cl;
+        if (c > j && c < nbw) Ps[c * R + j] = (T)fma(s_sig[c], upk, (double)Ps[c * R + j]);
+        if (tid == 0) Ps[j * R + j] = (T)cl;
       }
     }
     __syncthreads();
@@ -346,7 +350,7 @@ panel_kernel(PanelParams p) {
       double v = 0.0;
       if (c < nbw && r < nbw) {
         if (r == c) v = s_up[c];
-        else if (r > c) v = Ps[c * R + r];
+        else if (r > c) v = (double)Ps[c * R + r];
       }
       Vtop[idx] = v;
     }
@@ -355,14 +359,16 @@ panel_kernel(PanelParams p) {
 }
 
 // --------------------------------------------------------------------------
-// tiled FP64 kernels of the trailing update
+// tiled kernels of the trailing update (T = double: the FP64 path; T = float:
+// the FP32 factorization of the mixed-precision path)
 // --------------------------------------------------------------------------
 // V(i, a) for the panel at row offset k0: rows i < nbw from Vtop, the rest
 // straight from the reflector tails in A.  Columns a >= nbw read as 0.
-__device__ __forceinline__ double v_at(const double *A, int lda, const double *Vtop, int NB,
-                                       int k0, int nbw, int i, int a) {
-  if (a >= nbw) return 0.0;
-  if (i < nbw) return Vtop[i + a * NB];
+template <typename T>
+__device__ __forceinline__ T v_at(const T *A, int lda, const double *Vtop, int NB, int k0,
+                                  int nbw, int i, int a) {
+  if (a >= nbw) return T(0);
+  if (i < nbw) return (T)Vtop[i + a * NB];
   return A[SLQR_IDX(k0 + i, k0 + a, lda)];
 }
 
@@ -372,36 +378,36 @@ constexpr int kBM = 64;   // rows per tile of the update
 
 // W_part[s][c][a] = sum_{i in slice s} V(i, a) X(i, c)
 // grid: (ceil(N / kBN), S); rows of slice s: [s*RS, min((s+1)*RS, M))
-template <int NB, bool X_IS_V>
+template <typename T, int NB, bool X_IS_V>
 __global__ void __launch_bounds__(kThreads)
-gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
-                int nbw, int M, const double *__restrict__ X, int ldx, int N, int RS,
-                double *__restrict__ Wp) {
-  __shared__ double Vs[NB][kBK + 1];
-  __shared__ double Xs[kBN][kBK + 1];
+gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
+                int nbw, int M, const T *__restrict__ X, int ldx, int N, int RS,
+                T *__restrict__ Wp) {
+  __shared__ T Vs[NB][kBK + 1];
+  __shared__ T Xs[kBN][kBK + 1];
   constexpr int TP = NB / 16;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int c0 = blockIdx.x * kBN;
   const int s = blockIdx.y;
   const int i_begin = s * RS, i_end = min(M, i_begin + RS);
-  double acc[TP][4];
+  T acc[TP][4];
 #pragma unroll
   for (int a = 0; a < TP; ++a)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+    for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
 
   for (int i0 = i_begin; i0 < i_end; i0 += kBK) {
     for (int idx = tid; idx < NB * kBK; idx += kThreads) {
       int a = idx / kBK, ii = idx - a * kBK;
       int i = i0 + ii;
-      Vs[a][ii] = (i < i_end) ? v_at(A, lda, Vtop, NB, k0, nbw, i, a) : 0.0;
+      Vs[a][ii] = (i < i_end) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a) : T(0);
     }
     for (int idx = tid; idx < kBN * kBK; idx += kThreads) {
       int c = idx / kBK, ii = idx - c * kBK;
       int i = i0 + ii, cc = c0 + c;
-      double v = 0.0;
+      T v = T(0);
       if (i < i_end && cc < N) {
-        if (X_IS_V) v = v_at(A, lda, Vtop, NB, k0, nbw, i, cc);
+        if (X_IS_V) v = v_at<T>(A, lda, Vtop, NB, k0, nbw, i, cc);
         else v = X[SLQR_IDX(k0 + i, cc, ldx)];
       }
       Xs[c][ii] = v;
@@ -409,7 +415,7 @@ gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict_
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kBK; ++kk) {
-      double va[TP], xc[4];
+      T va[TP], xc[4];
 #pragma unroll
       for (int a = 0; a < TP; ++a) va[a] = Vs[tx + 16 * a][kk];
 #pragma unroll
@@ -421,7 +427,7 @@ gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict_
     }
     __syncthreads();
   }
-  double *out = Wp + (size_t)s * N * NB;
+  T *out = Wp + (size_t)s * N * NB;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     int cc = c0 + ty + 16 * q;
@@ -432,16 +438,18 @@ gemm_vtx_kernel(const double *__restrict__ A, int lda, const double *__restrict_
   }
 }
 
-// W'[a][c] = (T^T W)[a][c].  Each CTA owns kThreads / NB columns and each
-// thread one (column, reflector) entry: it sums that entry's S partials in a
-// fixed order (coalesced loads, all of a thread's loads independent).  Then
-// one warp does the forward substitution
-//   w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)
-// with four lanes per column splitting the inner sum.
-template <int NB>
+// W'[a][c] = (T^T W)[a][c] (TRANS) or (T W)[a][c].  Each CTA owns kThreads / NB
+// columns and each thread one (column, reflector) entry: it sums that
+// entry's S partials in a fixed order (coalesced loads, all of a thread's
+// loads independent).  Then one warp does the substitution with
+// T^{-1} = striu(G) + diag(1/tau):
+//   T^T w:  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q),  j = 0 .. nbw-1
+//   T w:    w'_j = tau_j (w_j - sum_{q>j} G[j,q] w'_q),  j = nbw-1 .. 0
+// with four lanes per column splitting the inner sum (FP64 arithmetic).
+template <typename T, int NB, bool TRANS>
 __global__ void __launch_bounds__(kThreads)
-tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
-          double *__restrict__ Wt) {
+tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
+          T *__restrict__ Wt) {
   constexpr int COLS = kThreads / NB;           // 4 (NB = 64) or 8 (NB = 32)
   __shared__ double w[NB][COLS + 1];
   const int tid = threadIdx.x;
@@ -452,10 +460,10 @@ tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict_
     const int c = tid / NB, a = tid - c * NB;    // entry (column c0 + c, reflector a)
     double acc = 0.0;
     if (c0 + c < N) {
-      const double *src = Wp + (size_t)(c0 + c) * NB + a;
+      const T *src = Wp + (size_t)(c0 + c) * NB + a;
       const size_t stride = (size_t)N * NB;
 #pragma unroll 8
-      for (int s = 0; s < S; ++s) acc += src[(size_t)s * stride];
+      for (int s = 0; s < S; ++s) acc += (double)src[(size_t)s * stride];
     }
     w[a][c] = acc;
   }
@@ -463,9 +471,14 @@ tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict_
   if (tid < 32) {                               // the whole first warp takes part
     const int c = min(tid >> 2, COLS - 1), part = tid & 3;
     const bool owner = (tid >> 2) < COLS && part == 0;
-    for (int j = 0; j < nbw; ++j) {
+    for (int s = 0; s < nbw; ++s) {
+      const int j = TRANS ? s : nbw - 1 - s;
       double t = 0.0;
-      for (int q = part; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
+      if (TRANS) {
+        for (int q = part; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
+      } else {
+        for (int q = j + 1 + part; q < nbw; q += 4) t = fma(__ldg(G + j + q * NB), w[q][c], t);
+      }
       t += __shfl_xor_sync(0xffffffffu, t, 1);
       t += __shfl_xor_sync(0xffffffffu, t, 2);
       const double wj = __ldg(tau + j) * (w[j][c] - t);
@@ -477,39 +490,38 @@ tw_kernel(const double *__restrict__ Wp, int S, int N, const double *__restrict_
   __syncthreads();
   {
     const int a = tid / COLS, c = tid - a * COLS;
-    if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? w[a][c] : 0.0;
+    if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? (T)w[a][c] : T(0);
   }
 }
 
 // X(i, c) -= sum_a V(i, a) W'[a][c] on a kBM x kBN tile; grid (ceil(M/kBM), ceil(N/kBN))
-template <int NB>
+template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads)
-gemm_upd_kernel(const double *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
-                int nbw, int M, double *__restrict__ X, int ldx, int N,
-                const double *__restrict__ Wt) {
-  extern __shared__ double smem[];
-  double *Vs = smem;                 // [NB][kBM]
-  double *Ws = smem + NB * kBM;      // [NB][kBN]
+gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
+                int nbw, int M, T *__restrict__ X, int ldx, int N, const T *__restrict__ Wt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Vs = (T *)smem_raw;             // [NB][kBM]
+  T *Ws = Vs + NB * kBM;             // [NB][kBN]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
   for (int idx = tid; idx < NB * kBM; idx += kThreads) {
     int a = idx / kBM, ii = idx - a * kBM;
     int i = i0 + ii;
-    Vs[idx] = (i < M) ? v_at(A, lda, Vtop, NB, k0, nbw, i, a) : 0.0;
+    Vs[idx] = (i < M) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a) : T(0);
   }
   for (int idx = tid; idx < NB * kBN; idx += kThreads) {
     int a = idx / kBN, cc = idx - a * kBN;
-    Ws[idx] = (c0 + cc < N) ? Wt[(size_t)a * N + c0 + cc] : 0.0;
+    Ws[idx] = (c0 + cc < N) ? Wt[(size_t)a * N + c0 + cc] : T(0);
   }
   __syncthreads();
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int pp = 0; pp < 4; ++pp)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[pp][q] = 0.0;
+    for (int q = 0; q < 4; ++q) acc[pp][q] = T(0);
 #pragma unroll 4
   for (int a = 0; a < nbw; ++a) {
-    double v[4], ww[4];
+    T v[4], ww[4];
 #pragma unroll
     for (int pp = 0; pp < 4; ++pp) v[pp] = Vs[a * kBM + tx + 16 * pp];
 #pragma unroll
@@ -527,7 +539,7 @@ gemm_upd_kernel(const double *__restrict__ A, int lda, const double *__restrict_
     for (int pp = 0; pp < 4; ++pp) {
       int i = i0 + tx + 16 * pp;
       if (i < M) {
-        double *dst = X + SLQR_IDX(k0 + i, cc, ldx);
+        T *dst = X + SLQR_IDX(k0 + i, cc, ldx);
         *dst -= acc[pp][q];
       }
     }
@@ -558,10 +570,10 @@ size_t panel_update_work_doubles(int m, int N, int nb, int num_sms) {
   return (4 * slots + ntiles + 1) * kBN * nb + (size_t)nb * N;
 }
 
-template <int NB>
-static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const double *A,
-                                     int lda, const double *wy_panel, double *X, int ldx, int N,
-                                     double *work, size_t work_doubles, cudaStream_t stream) {
+template <typename T, int NB, bool TRANS = true>
+static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const T *A, int lda,
+                                     const double *wy_panel, T *X, int ldx, int N, T *work,
+                                     size_t work_elems, cudaStream_t stream) {
   if (N <= 0) return SLQR_OK;
   const int M = m - k0;
   const int ntiles = (N + kBN - 1) / kBN;
@@ -569,23 +581,23 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   int RS = (M + S - 1) / S;
   RS = (RS + kBK - 1) / kBK * kBK;
   const int Seff = (M + RS - 1) / RS;
-  if ((size_t)Seff * N * NB + (size_t)NB * N > work_doubles)
+  if ((size_t)Seff * N * NB + (size_t)NB * N > work_elems)
     return fail(ctx, SLQR_ENOMEM, "internal: trailing-update workspace too small");
-  double *Wp = work;
-  double *Wt = work + (size_t)Seff * N * NB;
+  T *Wp = work;
+  T *Wt = work + (size_t)Seff * N * NB;
   const double *Vtop = wy_panel;
   const double gemm_flops = 2.0 * M * nbw * (double)N;
   int slot = prof_begin(ctx, stream);
-  gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
+  gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
       A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  tw_kernel<NB><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
+  tw_kernel<T, NB, TRANS><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
       Wp, Seff, N, wy_panel, nbw, Wt);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
-  size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
+  size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
-  gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+  gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
       A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
   return check_launch(ctx, "trailing update");
@@ -595,10 +607,10 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb, co
                                int lda, const double *wy_panel, double *X, int ldx, int N,
                                double *work, size_t work_doubles, cudaStream_t stream) {
   if (nb == 32)
-    return panel_update_impl<32>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
-                                 work_doubles, stream);
-  return panel_update_impl<64>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
-                               work_doubles, stream);
+    return panel_update_impl<double, 32>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
+                                         work_doubles, stream);
+  return panel_update_impl<double, 64>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
+                                       work_doubles, stream);
 }
 
 // Opt the kernels that use more than 48 KB of dynamic shared memory in; run
@@ -606,15 +618,23 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb, co
 slqr_status init_kernel_attrs(slqr_ctx *ctx) {
   const int max_smem = 200 * 1024;
   cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(panel_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  e = cudaFuncSetAttribute(panel_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_upd_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             64 * (kBM + kBN) * 8);
+    e = cudaFuncSetAttribute(panel_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_upd_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             32 * (kBM + kBN) * 8);
+    e = cudaFuncSetAttribute(panel_kernel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<double, 64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * (kBM + kBN) * 8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_upd_kernel<double, 32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (kBM + kBN) * 8);
   if (e != cudaSuccess)
     return fail(ctx, SLQR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   return SLQR_OK;
@@ -629,12 +649,18 @@ static int panel_rows_per_cta(int M, int nbw, int num_sms) {
   return R;
 }
 
-static int max_rows_per_cta(int nb) {
-  return (200 * 1024 - nb * nb * (int)sizeof(double)) / (nb * (int)sizeof(double));
+static int max_rows_per_cta(int nb, size_t elem = sizeof(double)) {
+  return (200 * 1024 - nb * nb * (int)sizeof(double) - 16) / (nb * (int)elem);
 }
 
-template <int NB>
-static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
+// dynamic shared memory of the panel kernel: the slice (T) then the local
+// Gram terms (double), 16-byte aligned
+static size_t panel_smem_bytes(int nb, int R, size_t elem) {
+  return ((size_t)nb * R * elem + 15) / 16 * 16 + (size_t)nb * nb * sizeof(double);
+}
+
+template <typename T, int NB>
+static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, double *up,
                                double *wy, cudaStream_t stream) {
   const int K = num_reflectors(m, n);
   const int np = num_panels(K, NB);
@@ -645,8 +671,8 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
   const size_t prow_doubles = 2 * (size_t)NB;
   const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
   const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms);
-  const size_t bytes =
-      256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles + work_doubles) * 8;
+  const size_t bytes = 256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles) * 8 +
+                       work_doubles * sizeof(T) + 256;
   slqr_status st = ensure_workspace(ctx, bytes);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws.ptr;
@@ -655,7 +681,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
   double *gpart = rec + rec_doubles;
   double *prow = gpart + gpart_doubles;
   double *wy_store = wy ? wy : prow + prow_doubles;
-  double *work = prow + prow_doubles + wy_doubles;
+  T *work = (T *)(prow + prow_doubles + wy_doubles);
 
   cudaError_t e = cudaMemsetAsync(bar, 0, 256, stream);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
@@ -677,7 +703,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     const int nbw = std::min(NB, K - k0);
     const int M = m - k0;
     const int R = panel_rows_per_cta(M, nbw, Pmax);
-    if (R > max_rows_per_cta(NB))
+    if (R > max_rows_per_cta(NB, sizeof(T)))
       return fail(ctx, SLQR_EINVAL, "m = %d is too large for the shared-memory panel", m);
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
@@ -687,13 +713,13 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
-    size_t smem = ((size_t)NB * R + (size_t)NB * NB) * sizeof(double);
+    size_t smem = panel_smem_bytes(NB, R, sizeof(T));
     // algorithmic flops of the panel: per column j a norm over M-j entries and,
     // for each later panel column, a dot and an axpy over M-j entries
     double pflops = 0.0;
     for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
     int slot = prof_begin(ctx, s);
-    cudaError_t le = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P),
+    cudaError_t le = cudaLaunchCooperativeKernel((const void *)panel_kernel<T, NB>, dim3(P),
                                                  dim3(kThreads), args, smem, s);
     prof_end(ctx, s, slot, kPanel, pflops);
     if (le != cudaSuccess)
@@ -706,7 +732,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, double *A, int lda, 
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     if (c_end <= c_begin) return SLQR_OK;
-    return panel_update_impl<NB>(ctx, m, k0, nbw, A, lda,
+    return panel_update_impl<T, NB>(ctx, m, k0, nbw, A, lda,
                                  wy_store + (size_t)pnl * wy_panel_doubles(NB),
                                  A + (size_t)c_begin * lda, lda, c_end - c_begin, work,
                                  work_doubles, stream);
@@ -771,8 +797,8 @@ extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int l
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
   cudaStream_t s = (cudaStream_t)stream;
-  if (panel_width(m, n) == 32) return factor_impl<32>(ctx, m, n, A, lda, up, wy, s);
-  return factor_impl<64>(ctx, m, n, A, lda, up, wy, s);
+  if (panel_width(m, n) == 32) return factor_impl<double, 32>(ctx, m, n, A, lda, up, wy, s);
+  return factor_impl<double, 64>(ctx, m, n, A, lda, up, wy, s);
 }
 
 // ==========================================================================
@@ -828,15 +854,17 @@ static slqr_status noalloc_setup(int dev, double **ptr, int *sms) {
     return SLQR_ECUDA;
   }
   const int max_smem = 200 * 1024;
-  e = cudaFuncSetAttribute(panel_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  e = cudaFuncSetAttribute(panel_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_upd_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             64 * (kBM + kBN) * 8);
+    e = cudaFuncSetAttribute(gemm_upd_kernel<double, 64>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * (kBM + kBN) * 8);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_upd_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             32 * (kBM + kBN) * 8);
+    e = cudaFuncSetAttribute(gemm_upd_kernel<double, 32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (kBM + kBN) * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SLQR_ECUDA;
@@ -866,12 +894,12 @@ static slqr_status noalloc_update(int num_sms, int m, int k0, int nbw, const dou
   if ((size_t)Seff * N * NB + (size_t)NB * N > work_doubles) return SLQR_EINVAL;
   double *Wp = work;
   double *Wt = work + (size_t)Seff * N * NB;
-  gemm_vtx_kernel<NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
+  gemm_vtx_kernel<double, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, RS, Wp);
-  tw_kernel<NB><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
+  tw_kernel<double, NB, true><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
       Wp, Seff, N, wy_panel, nbw, Wt);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
-  gemm_upd_kernel<NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+  gemm_upd_kernel<double, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, Wt);
   return cudaGetLastError() == cudaSuccess ? SLQR_OK : SLQR_ECUDA;
 }
@@ -908,9 +936,9 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
-    size_t smem = ((size_t)NB * R + (size_t)NB * NB) * sizeof(double);
-    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<NB>, dim3(P), dim3(kThreads), args,
-                                    smem, stream);
+    size_t smem = panel_smem_bytes(NB, R, sizeof(double));
+    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<double, NB>, dim3(P), dim3(kThreads),
+                                    args, smem, stream);
     if (e != cudaSuccess) return SLQR_ECUDA;
     bar_base += (unsigned)P * (unsigned)(nbw + 1);
     const int N = n - (k0 + nbw);

@@ -56,6 +56,8 @@ struct Profiler {
 
 }  // namespace slqr
 
+namespace slqr { struct Server; }
+
 struct slqr_ctx {
   int device = 0;
   int num_sms = 0;
@@ -67,6 +69,7 @@ struct slqr_ctx {
   cudaStream_t aux_stream = nullptr;   // look-ahead panels run here
   cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_panel = nullptr;
   long long launch_count = 0;          // kernels launched by this context
+  slqr::Server *server = nullptr;      // request loop (slqr_submit), started lazily
   std::string last_error;
   std::mutex mu;
 };
@@ -87,6 +90,9 @@ slqr_status check_launch(slqr_ctx *ctx, const char *what);
 // count the launch.
 int prof_begin(slqr_ctx *ctx, cudaStream_t stream);
 void prof_end(slqr_ctx *ctx, cudaStream_t stream, int slot, int kid, double flops);
+
+// Stop the request loop of a context (waits for its requests to finish).
+void server_stop(slqr_ctx *ctx);
 
 // Opt kernels into large dynamic shared memory (once per device).
 slqr_status init_kernel_attrs(slqr_ctx *ctx);
