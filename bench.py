@@ -324,6 +324,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- batched workload: 20,000 uneven problems in one persistent launch ----
     batch = run_batch_workload(ctx, device, stream, barrier) if not args.no_batch else None
+    mixed = run_mixed_workload(ctx, device, stream, barrier) if not args.no_mixed else None
 
     # ---- roofline of the dominant kernel (most device time in the timed region) ----
     dom = max(prof, key=lambda k: prof[k][0])
@@ -359,10 +360,60 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kernels,
         "factor_only": factor_only,
         "batch": batch,
+        "mixed_8192x4096": mixed,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def run_mixed_workload(ctx, device, stream, barrier, kappas=(1e2, 1e6, 1e10), m=8192, n=4096):
+    """8192 x 4096 matrices U diag(sigma) V^T with cond 1e2 / 1e6 / 1e10: the FP64
+    path (factor + Q^T b + solve) against the mixed path (FP32 factorization +
+    FP64-residual refinement), errors stated against x_true (consistent b) and
+    against the FP64 solution (random b)."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flops = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + (4.0 * m * n - 2.0 * n * n) + n * n
+    for kappa in kappas:
+        A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa, device=device)
+        rec = {}
+        # FP64 path
+        for name, b in (("consistent", b_cons), ("random", b_rand)):
+            Aw, bw = A.t().clone().t(), b.clone()
+            barrier()
+            e0.record(stream)
+            x64, _ = ctx.lstsq(Aw, bw)
+            e1.record(stream)
+            barrier()
+            t64 = e0.elapsed_time(e1)
+            x64 = x64.clone()
+            xm = torch.zeros(n, dtype=torch.float64, device=device)
+            barrier()
+            e0.record(stream)
+            st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
+                                                xm.data_ptr(), abi.SLQR_FP32, 0, 0.0,
+                                                stream.cuda_stream)
+            e1.record(stream)
+            barrier()
+            tm = e0.elapsed_time(e1)
+            r = {"fp64_ms": t64, "fp64_gflops": flops / (t64 / 1e3) / 1e9,
+                 "mixed_fp32_ms": tm, "mixed_gflops_equiv": flops / (tm / 1e3) / 1e9,
+                 "mixed_status": abi.STATUS_NAMES.get(st, st), "refine_iters": its,
+                 "refine_last_step": err,
+                 "mixed_vs_fp64_rel": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))}
+            if name == "consistent":
+                r["fp64_err_vs_x_true"] = float(torch.linalg.norm(x64 - x_true) / torch.linalg.norm(x_true))
+                r["mixed_err_vs_x_true"] = float(torch.linalg.norm(xm - x_true) / torch.linalg.norm(x_true))
+            rec[name] = r
+        out[f"kappa_{kappa:.0e}"] = rec
+        del A, b_cons, x_true, b_rand
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the mixed workload")
+    return out
 
 
 BATCH_COUNT = 20000
@@ -494,6 +545,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision workload")
     ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
                     help="run one small factor/apply/solve pass for profiling and exit")
     args = ap.parse_args()

@@ -194,6 +194,30 @@ slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int 
 int slqr_batch_max_rows(void);
 
 /*
+ * slqr_lstsq_mixed -- least squares min ||A x - b|| for one large problem in
+ * mixed precision, error stated against FP64.  The H12 factorization
+ * (Alg. 2) runs on an FP32 copy of A: the reflector norm, up, b and the
+ * compact-WY coefficients are FP64, the trailing-update products FP32.  The
+ * FP64 solution is then recovered by iterative refinement of the augmented
+ * system [I A; A^T 0][r; x] = [b; 0] with residuals computed in FP64 from A
+ * and corrections through the FP32 factorization.
+ *   A      device, m x n column-major FP64, lda >= m, m >= n >= 1 (read only)
+ *   b      device, m doubles (read only);  x  device, n doubles (output)
+ *   prec   SLQR_FP32
+ *   max_iter  refinement sweeps (<= 0: 30);  tol  stop at ||dx||_inf <=
+ *          tol ||x||_inf (<= 0: 1e-14)
+ *   iters, err  HOST ints/doubles or NULL: sweeps done and the last
+ *          ||dx||_inf / ||x||_inf
+ * Synchronous: returns when x is final.  SLQR_OK when the refinement reached
+ * tol (or stopped contracting below 1e-11); SLQR_ENOCONV when it did not
+ * (kappa(A) * u_fp32 too large); SLQR_ERANK for an exact zero diagonal of R;
+ * SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
+ */
+slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                             const double *b, double *x, int prec, int max_iter, double tol,
+                             int *iters, double *err, void *stream);
+
+/*
  * Request loop: continuous batching of least-squares subproblems from many
  * concurrent SLSQP runs (each one factors its QP matrix and later
  * back-substitutes with the stored factorization, Section 1).  The first

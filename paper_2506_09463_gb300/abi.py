@@ -77,6 +77,8 @@ SIGNATURES = [
     ("slqr_submit", _c_int, [_vp, ctypes.POINTER(SlqrRequest), ctypes.POINTER(ctypes.c_uint64)]),
     ("slqr_poll", _c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(SlqrResult)]),
     ("slqr_server_bytes_in_use", _c_size, [_vp]),
+    ("slqr_lstsq_mixed", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _c_int, _dbl,
+                                  ctypes.POINTER(_c_int), ctypes.POINTER(_dbl), _vp]),
     ("slqr_noalloc_max_rows", _c_int, []),
     ("slqr_noalloc_max_cols", _c_int, []),
 ]
@@ -204,6 +206,14 @@ def slqr_poll(ctx, ticket: int):
     out = SlqrResult()
     st = _lib.slqr_poll(ctx, ticket, ctypes.byref(out))
     return st, out
+
+
+def slqr_lstsq_mixed(ctx, m, n, A, lda, b, x, prec, max_iter, tol, stream):
+    """Returns (status, iterations, last relative step)."""
+    it, err = _c_int(), _dbl()
+    st = _lib.slqr_lstsq_mixed(ctx, m, n, A, lda, b, x, prec, max_iter, tol, ctypes.byref(it),
+                               ctypes.byref(err), stream)
+    return st, it.value, err.value
 
 
 def slqr_server_bytes_in_use(ctx) -> int:

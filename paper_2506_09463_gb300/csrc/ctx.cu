@@ -25,18 +25,23 @@ slqr_status check_launch(slqr_ctx *ctx, const char *what) {
   return SLQR_OK;
 }
 
-slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes) {
-  if (bytes <= ctx->ws.bytes) return SLQR_OK;
+static slqr_status grow(slqr_ctx *ctx, Workspace &ws, size_t bytes);
+
+slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes) { return grow(ctx, ctx->ws, bytes); }
+slqr_status ensure_workspace2(slqr_ctx *ctx, size_t bytes) { return grow(ctx, ctx->ws2, bytes); }
+
+static slqr_status grow(slqr_ctx *ctx, Workspace &ws, size_t bytes) {
+  if (bytes <= ws.bytes) return SLQR_OK;
   bytes = align_up(bytes, (size_t)1 << 20);
   if (ctx->hbm_budget && bytes > ctx->hbm_budget)
     return fail(ctx, SLQR_EBUSY, "workspace of %zu bytes exceeds the HBM budget %zu", bytes,
                 ctx->hbm_budget);
-  if (ctx->ws.ptr) {
+  if (ws.ptr) {
     // the old workspace may still be in use by enqueued work
     cudaDeviceSynchronize();
-    cudaFree(ctx->ws.ptr);
-    ctx->ws.ptr = nullptr;
-    ctx->ws.bytes = 0;
+    cudaFree(ws.ptr);
+    ws.ptr = nullptr;
+    ws.bytes = 0;
   }
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
@@ -44,8 +49,8 @@ slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes) {
     cudaGetLastError();
     return fail(ctx, SLQR_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   }
-  ctx->ws.ptr = p;
-  ctx->ws.bytes = bytes;
+  ws.ptr = p;
+  ws.bytes = bytes;
   return SLQR_OK;
 }
 
@@ -192,6 +197,7 @@ extern "C" void slqr_destroy(slqr_ctx *ctx) {
   if (ctx->ev_panel) cudaEventDestroy(ctx->ev_panel);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+  if (ctx->ws2.ptr) cudaFree(ctx->ws2.ptr);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
 }

@@ -236,23 +236,37 @@ panel_kernel(PanelParams p) {
       return;
 
     // ---- phase 2 ---------------------------------------------------------
+    // Thread (g, c) reduces entry c over CTA slice g; all its loads are issued
+    // before the first is used (fixed-size unrolled loop), so the reduction
+    // costs about one L2 round trip.  The thread with c == j reduces the
+    // (E, S) norm pairs of its slice the same way.
     {
+      constexpr int QMAX = (kMaxPanelCtas + GROUPS - 1) / GROUPS;
       const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
       const int g = tid / NB, c = tid - g * NB;
       const int per = (p.P + GROUPS - 1) / GROUPS;
       const int q0 = g * per, q1 = min(p.P, q0 + per);
       if (c > j && c < nbw) {
-        double v = 0.0;
-#pragma unroll 4
-        for (int q = q0; q < q1; ++q) v += __ldcg(rec + (size_t)q * RECW + 2 + c);
-        s_part[g][c] = v;
+        double v[QMAX];
+#pragma unroll
+        for (int t = 0; t < QMAX; ++t)
+          v[t] = (q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + 2 + c) : 0.0;
+        double acc = 0.0;
+#pragma unroll
+        for (int t = 0; t < QMAX; ++t) acc += v[t];
+        s_part[g][c] = acc;
       } else if (c == j) {
+        double ev[QMAX], sv[QMAX];
+#pragma unroll
+        for (int t = 0; t < QMAX; ++t) {
+          const bool in = (q0 + t < q1);
+          ev[t] = in ? __ldcg(rec + (size_t)(q0 + t) * RECW) : (double)kNoExp;
+          sv[t] = in ? __ldcg(rec + (size_t)(q0 + t) * RECW + 1) : 0.0;
+        }
         int E = kNoExp;
         double S = 0.0;
-        for (int q = q0; q < q1; ++q) {
-          double Eq = __ldcg(rec + (size_t)q * RECW), Sq = __ldcg(rec + (size_t)q * RECW + 1);
-          ssq_merge(E, S, (int)Eq, Sq);
-        }
+#pragma unroll
+        for (int t = 0; t < QMAX; ++t) ssq_merge(E, S, (int)ev[t], sv[t]);
         s_partE[g] = (double)E;
         s_partS[g] = S;
       }
@@ -446,38 +460,55 @@ gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 //   T^T w:  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q),  j = 0 .. nbw-1
 //   T w:    w'_j = tau_j (w_j - sum_{q>j} G[j,q] w'_q),  j = nbw-1 .. 0
 // with four lanes per column splitting the inner sum (FP64 arithmetic).
-template <typename T, int NB, bool TRANS>
+template <typename T, int NB, bool TRANS, int COLS>
 __global__ void __launch_bounds__(kThreads)
 tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
           T *__restrict__ Wt) {
-  constexpr int COLS = kThreads / NB;           // 4 (NB = 64) or 8 (NB = 32)
+  static_assert(COLS * NB <= kThreads, "one entry needs at least one thread");
+  constexpr int TPE = kThreads / (COLS * NB);   // threads per entry (split over s)
   __shared__ double w[NB][COLS + 1];
+  __shared__ double part[TPE][COLS * NB];
   const int tid = threadIdx.x;
   const double *G = wy + (size_t)NB * NB;
   const double *tau = wy + 2 * (size_t)NB * NB;
   const int c0 = blockIdx.x * COLS;
   {
-    const int c = tid / NB, a = tid - c * NB;    // entry (column c0 + c, reflector a)
-    double acc = 0.0;
+    const int e = tid % (COLS * NB), h = tid / (COLS * NB);
+    const int c = e / NB, a = e - c * NB;        // entry (column c0 + c, reflector a)
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
     if (c0 + c < N) {
       const T *src = Wp + (size_t)(c0 + c) * NB + a;
       const size_t stride = (size_t)N * NB;
-#pragma unroll 8
-      for (int s = 0; s < S; ++s) acc += (double)src[(size_t)s * stride];
+      int s = h;
+      for (; s + 3 * TPE < S; s += 4 * TPE) {
+        acc0 += (double)src[(size_t)s * stride];
+        acc1 += (double)src[(size_t)(s + TPE) * stride];
+        acc2 += (double)src[(size_t)(s + 2 * TPE) * stride];
+        acc3 += (double)src[(size_t)(s + 3 * TPE) * stride];
+      }
+      for (; s < S; s += TPE) acc0 += (double)src[(size_t)s * stride];
     }
-    w[a][c] = acc;
+    part[h][e] = (acc0 + acc1) + (acc2 + acc3);
+  }
+  __syncthreads();
+  if (tid < COLS * NB) {
+    double v = part[0][tid];
+#pragma unroll
+    for (int h = 1; h < TPE; ++h) v += part[h][tid];
+    const int c = tid / NB, a = tid - c * NB;
+    w[a][c] = v;
   }
   __syncthreads();
   if (tid < 32) {                               // the whole first warp takes part
-    const int c = min(tid >> 2, COLS - 1), part = tid & 3;
-    const bool owner = (tid >> 2) < COLS && part == 0;
+    const int c = min(tid >> 2, COLS - 1), part_id = tid & 3;
+    const bool owner = (tid >> 2) < COLS && part_id == 0;
     for (int s = 0; s < nbw; ++s) {
       const int j = TRANS ? s : nbw - 1 - s;
       double t = 0.0;
       if (TRANS) {
-        for (int q = part; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
+        for (int q = part_id; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
       } else {
-        for (int q = j + 1 + part; q < nbw; q += 4) t = fma(__ldg(G + j + q * NB), w[q][c], t);
+        for (int q = j + 1 + part_id; q < nbw; q += 4) t = fma(__ldg(G + j + q * NB), w[q][c], t);
       }
       t += __shfl_xor_sync(0xffffffffu, t, 1);
       t += __shfl_xor_sync(0xffffffffu, t, 2);
@@ -488,9 +519,23 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
     }
   }
   __syncthreads();
-  {
-    const int a = tid / COLS, c = tid - a * COLS;
+  for (int idx = tid; idx < NB * COLS; idx += kThreads) {
+    const int a = idx / COLS, c = idx - a * COLS;
     if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? (T)w[a][c] : T(0);
+  }
+}
+
+// Launch W' = T^T W (TRANS) or T W: one column per CTA (4 threads per entry)
+// while there are few columns, kThreads / NB columns per CTA otherwise.
+template <typename T, int NB, bool TRANS>
+static void launch_tw(const T *Wp, int S, int N, const double *wy, int nbw, T *Wt,
+                      cudaStream_t stream) {
+  constexpr int WIDE = kThreads / NB;
+  if (N <= 4 * 152) {
+    tw_kernel<T, NB, TRANS, 1><<<N, kThreads, 0, stream>>>(Wp, S, N, wy, nbw, Wt);
+  } else {
+    tw_kernel<T, NB, TRANS, WIDE><<<(N + WIDE - 1) / WIDE, kThreads, 0, stream>>>(Wp, S, N, wy,
+                                                                                 nbw, Wt);
   }
 }
 
@@ -592,8 +637,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
       A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  tw_kernel<T, NB, TRANS><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
-      Wp, Seff, N, wy_panel, nbw, Wt);
+  launch_tw<T, NB, TRANS>(Wp, Seff, N, wy_panel, nbw, Wt, stream);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
@@ -770,6 +814,27 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   return check_launch(ctx, "factor");
 }
 
+slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
+                       cudaStream_t stream) {
+  if (panel_width(m, n) == 32) return factor_impl<float, 32>(ctx, m, n, A, lda, up, wy, stream);
+  return factor_impl<float, 64>(ctx, m, n, A, lda, up, wy, stream);
+}
+
+slqr_status apply_panel_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const float *A,
+                                   int lda, const double *wy_panel, float *X, int ldx, int N,
+                                   float *work, size_t work_elems, cudaStream_t stream,
+                                   bool trans) {
+  if (nb == 32)
+    return trans ? panel_update_impl<float, 32, true>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx,
+                                                      N, work, work_elems, stream)
+                 : panel_update_impl<float, 32, false>(ctx, m, k0, nbw, A, lda, wy_panel, X,
+                                                       ldx, N, work, work_elems, stream);
+  return trans ? panel_update_impl<float, 64, true>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N,
+                                                    work, work_elems, stream)
+               : panel_update_impl<float, 64, false>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx,
+                                                     N, work, work_elems, stream);
+}
+
 }  // namespace slqr
 
 using namespace slqr;
@@ -896,8 +961,7 @@ static slqr_status noalloc_update(int num_sms, int m, int k0, int nbw, const dou
   double *Wt = work + (size_t)Seff * N * NB;
   gemm_vtx_kernel<double, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, RS, Wp);
-  tw_kernel<double, NB, true><<<(N + kThreads / NB - 1) / (kThreads / NB), kThreads, 0, stream>>>(
-      Wp, Seff, N, wy_panel, nbw, Wt);
+  launch_tw<double, NB, true>(Wp, Seff, N, wy_panel, nbw, Wt, stream);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(double);
   gemm_upd_kernel<double, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
       A, lda, wy_panel, k0, nbw, M, X, ldx, N, Wt);

@@ -1,0 +1,331 @@
+// mixed.cu -- mixed-precision least squares for large matrices
+// (slqr_lstsq_mixed).
+//
+// The factorization (Alg. 2, H12 storage) runs on an FP32 copy of A: reflector
+// norm, up, b and the compact-WY coefficients are FP64, the trailing-update
+// products FP32 (SLQR_FP32: FP32 FMA pipe).  The LS solution is then refined
+// against the FP64 A with the augmented system [I A; A^T 0][r; x] = [b; 0]
+// (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64, the correction
+// through the FP32 QR, h = R^-T g, d = Q^T f, dx = R^-1 (d[0:n] - h),
+// dr = Q [h; d[n:m]].  This converges to the FP64 LS solution when
+// kappa * u_low < 1, for consistent and inconsistent right-hand sides.
+#include "slqr_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace slqr {
+
+constexpr int kRowsPerCta = 256;
+constexpr int kColChunk = 256;
+
+// A32 = (float) A
+__global__ void to_f32_kernel(const double *__restrict__ A, int lda, int m, int n,
+                              float *__restrict__ A32) {
+  const size_t total = (size_t)m * n;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / m), i = (int)(idx - (size_t)j * m);
+    A32[idx] = (float)A[SLQR_IDX(i, j, lda)];
+  }
+}
+
+// partial row sums of A x over column chunks: part[chunk][i]
+__global__ void __launch_bounds__(kRowsPerCta)
+ax_partial_kernel(const double *__restrict__ A, int lda, int m, int n,
+                  const double *__restrict__ x, double *__restrict__ part) {
+  const int i = blockIdx.x * kRowsPerCta + threadIdx.x;
+  const int j0 = blockIdx.y * kColChunk, j1 = min(n, j0 + kColChunk);
+  __shared__ double xs[kColChunk];
+  for (int j = j0 + threadIdx.x; j < j1; j += kRowsPerCta) xs[j - j0] = x[j];
+  __syncthreads();
+  if (i >= m) return;
+  double acc = 0.0;
+  for (int j = j0; j < j1; ++j) acc = fma(A[SLQR_IDX(i, j, lda)], xs[j - j0], acc);
+  part[(size_t)blockIdx.y * m + i] = acc;
+}
+
+// f = b - r - sum_chunks part (fixed order); f32 = (float) f
+__global__ void resid_f_kernel(const double *__restrict__ b, const double *__restrict__ r,
+                               const double *__restrict__ part, int chunks, int m,
+                               float *__restrict__ f32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double ax = 0.0;
+  for (int c = 0; c < chunks; ++c) ax += part[(size_t)c * m + i];
+  f32[i] = (float)(b[i] - r[i] - ax);
+}
+
+// g = -A^T r (one warp per column), g32 = (float) g
+__global__ void resid_g_kernel(const double *__restrict__ A, int lda, int m, int n,
+                               const double *__restrict__ r, float *__restrict__ g32) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double acc = 0.0;
+  for (int i = lane; i < m; i += 32) acc = fma(A[SLQR_IDX(i, warp, lda)], r[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) g32[warp] = (float)(-acc);
+}
+
+// e[0:n] = d[0:n] - h ; keep d[n:m] in e (e aliases nothing)
+__global__ void form_e_kernel(const float *__restrict__ d, const float *__restrict__ h, int m,
+                              int n, float *__restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) e[i] = (i < n) ? d[i] - h[i] : d[i];
+}
+
+// d[0:n] = h (so that d = [h; d2]); x += dx (FP64); per-CTA maxima of |dx|, |x|
+__global__ void update_kernel(float *__restrict__ d, const float *__restrict__ h,
+                              const float *__restrict__ dx, double *__restrict__ x, int n,
+                              double *__restrict__ maxima) {
+  __shared__ double s_dx[256], s_x[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 0.0, c = 0.0;
+  if (i < n) {
+    d[i] = h[i];
+    const double v = (double)dx[i];
+    const double xn = x[i] + v;
+    x[i] = xn;
+    a = fabs(v);
+    c = fabs(xn);
+  }
+  s_dx[threadIdx.x] = a;
+  s_x[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_dx[threadIdx.x] = fmax(s_dx[threadIdx.x], s_dx[threadIdx.x + o]);
+      s_x[threadIdx.x] = fmax(s_x[threadIdx.x], s_x[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    maxima[2 * blockIdx.x] = s_dx[0];
+    maxima[2 * blockIdx.x + 1] = s_x[0];
+  }
+}
+
+// r += dr (FP64)
+__global__ void add_r_kernel(double *__restrict__ r, const float *__restrict__ dr, int m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) r[i] += (double)dr[i];
+}
+
+__global__ void init_kernel(double *__restrict__ r, const double *__restrict__ b, int m,
+                            double *__restrict__ x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) r[i] = b[i];
+  if (i < n) x[i] = 0.0;
+}
+
+// One 64-row block step of an FP32 triangular solve with R = triu(A32[0:n,0:n])
+// (ld = lda).  UPPER: R y = c, blocks from the bottom; else R^T y = c, blocks
+// from the top.  CTA t updates row block t with the solution of block b_src,
+// and CTA t == b_diag then solves its diagonal block (one warp).
+template <bool UPPER>
+__global__ void __launch_bounds__(kThreads)
+trsv_f32_step_kernel(const float *__restrict__ R, int lda, int n, float *__restrict__ y,
+                     int t_first, int b_src, int b_diag, int *zero_flag) {
+  __shared__ float xs[64];
+  __shared__ float ys[64];
+  __shared__ float Rs[64][65];
+  const int t = t_first + blockIdx.x;
+  const int tid = threadIdx.x;
+  const int row_begin = t * 64;
+  const int rows = min(64, n - row_begin);
+  if (b_src >= 0) {
+    const int col_begin = b_src * 64;
+    const int cols = min(64, n - col_begin);
+    if (tid < 64) xs[tid] = (tid < cols) ? y[col_begin + tid] : 0.f;
+    __syncthreads();
+    // y[rows of t] -= M * xs with M = R[t rows, b_src cols] (UPPER) or
+    // R^T[t rows, b_src cols] = R[b_src rows, t cols]^T
+    const int r = tid & 63, part = tid >> 6;     // 4 threads per row
+    float acc = 0.f;
+    if (r < rows) {
+      for (int c = part; c < cols; c += 4) {
+        const float mv = UPPER ? R[SLQR_IDX(row_begin + r, col_begin + c, lda)]
+                               : R[SLQR_IDX(col_begin + c, row_begin + r, lda)];
+        acc = fmaf(mv, xs[c], acc);
+      }
+    }
+    __shared__ float red[4][64];
+    red[part][r] = acc;
+    __syncthreads();
+    if (tid < rows) y[row_begin + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+    __syncthreads();
+  }
+  if (t != b_diag) return;
+  for (int idx = tid; idx < 64 * 64; idx += kThreads) {
+    const int c = idx >> 6, r = idx & 63;
+    float v = 0.f;
+    if (r < rows && c < rows) {
+      // UPPER: Rs[r][c] = R[r, c] (r <= c); transposed: Rs[r][c] = R[c, r] (r >= c)
+      if (UPPER && r <= c) v = R[SLQR_IDX(row_begin + r, row_begin + c, lda)];
+      if (!UPPER && r >= c) v = R[SLQR_IDX(row_begin + c, row_begin + r, lda)];
+    }
+    Rs[r][c] = v;
+  }
+  if (tid < 64) ys[tid] = (tid < rows) ? y[row_begin + tid] : 0.f;
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    float c0 = ys[lane], c1 = ys[lane + 32];
+    bool zero = false;
+    for (int s = 0; s < rows; ++s) {
+      const int i = UPPER ? rows - 1 - s : s;
+      const float ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
+      const float d = Rs[i][i];
+      float xi = 0.f;
+      if (d != 0.f) xi = ci / d;
+      else zero = true;
+      if (lane == (i & 31)) {
+        if (i < 32) c0 = xi; else c1 = xi;
+      }
+      if (UPPER) {
+        if (lane < i) c0 = fmaf(-Rs[lane][i], xi, c0);
+        if (lane + 32 < i) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+      } else {
+        if (lane > i) c0 = fmaf(-Rs[lane][i], xi, c0);
+        if (lane + 32 > i && lane + 32 < rows) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+      }
+    }
+    if (lane < rows) y[row_begin + lane] = c0;
+    if (lane + 32 < rows) y[row_begin + lane + 32] = c1;
+    if (zero && lane == 0) atomicExch(zero_flag, 1);
+  }
+}
+
+}  // namespace slqr
+
+namespace slqr {
+
+template <bool UPPER>
+static void trsv_f32(const float *R, int lda, int n, float *y, int *zero_flag, cudaStream_t s) {
+  const int nblk = (n + 63) / 64;
+  if (UPPER) {
+    trsv_f32_step_kernel<true><<<1, kThreads, 0, s>>>(R, lda, n, y, nblk - 1, -1, nblk - 1,
+                                                      zero_flag);
+    for (int b = nblk - 1; b >= 1; --b)
+      trsv_f32_step_kernel<true><<<b, kThreads, 0, s>>>(R, lda, n, y, 0, b, b - 1, zero_flag);
+  } else {
+    trsv_f32_step_kernel<false><<<1, kThreads, 0, s>>>(R, lda, n, y, 0, -1, 0, zero_flag);
+    for (int b = 0; b + 1 < nblk; ++b)
+      trsv_f32_step_kernel<false><<<nblk - 1 - b, kThreads, 0, s>>>(R, lda, n, y, b + 1, b,
+                                                                    b + 1, zero_flag);
+  }
+}
+
+}  // namespace slqr
+
+using namespace slqr;
+
+extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                        const double *b, double *x, int prec, int max_iter,
+                                        double tol, int *iters, double *err, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);
+  if (lda < m || !A || !b || !x) return fail(ctx, SLQR_EINVAL, "bad lda or NULL pointer");
+  if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
+  if (prec != SLQR_FP32) return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
+  if (max_iter < 1) max_iter = 30;
+  if (!(tol > 0.0)) tol = 1e-14;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = panel_width(m, n);
+  const int K = num_reflectors(m, n);
+  const int np = num_panels(K, nb);
+  const int chunks = (n + kColChunk - 1) / kColChunk;
+  const int ublocks = (n + 255) / 256;
+  const size_t work_elems = panel_update_work_doubles(m, 1, nb, ctx->num_sms);
+  // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_a32 = take((size_t)m * n * sizeof(float));
+  const size_t o_up = take((size_t)n * sizeof(double));
+  const size_t o_wy = take(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double));
+  const size_t o_r = take((size_t)m * sizeof(double));
+  const size_t o_f = take((size_t)m * sizeof(float));
+  const size_t o_g = take((size_t)n * sizeof(float));
+  const size_t o_e = take((size_t)m * sizeof(float));
+  const size_t o_part = take((size_t)chunks * m * sizeof(double));
+  const size_t o_max = take((size_t)2 * ublocks * sizeof(double));
+  const size_t o_flag = take(sizeof(int));
+  const size_t o_work = take(work_elems * sizeof(float));
+  slqr_status st = ensure_workspace2(ctx, off);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws2.ptr;
+  float *A32 = (float *)(base + o_a32);
+  double *up = (double *)(base + o_up);
+  double *wy = (double *)(base + o_wy);
+  double *r = (double *)(base + o_r);
+  float *f32 = (float *)(base + o_f);
+  float *g32 = (float *)(base + o_g);
+  float *e32 = (float *)(base + o_e);
+  double *part = (double *)(base + o_part);
+  double *maxima = (double *)(base + o_max);
+  int *zero_flag = (int *)(base + o_flag);
+  float *work = (float *)(base + o_work);
+
+  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32);
+  st = factor_f32(ctx, m, n, A32, m, up, wy, s);
+  if (st != SLQR_OK) return st;
+  init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, b, m, x, n);
+  cudaMemsetAsync(zero_flag, 0, sizeof(int), s);
+  std::vector<double> hmax(2 * ublocks);
+  int it = 0, status = SLQR_ENOCONV;
+  double e_cur = 1.0, e_prev = 1e300;
+  for (it = 1; it <= max_iter; ++it) {
+    ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, chunks), kRowsPerCta, 0, s>>>(
+        A, lda, m, n, x, part);
+    resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(b, r, part, chunks, m, f32);
+    resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, r, g32);
+    trsv_f32<false>(A32, m, n, g32, zero_flag, s);                       // h = R^-T g
+    for (int p = 0; p < np; ++p) {                                      // d = Q^T f
+      const int k0 = p * nb, nbw = std::min(nb, K - k0);
+      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, m, wy + (size_t)p * wy_panel_doubles(nb),
+                                  f32, m, 1, work, work_elems, s, true);
+      if (st != SLQR_OK) return st;
+    }
+    form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(f32, g32, m, n, e32);
+    trsv_f32<true>(A32, m, n, e32, zero_flag, s);                        // dx = R^-1 (d1 - h)
+    update_kernel<<<ublocks, 256, 0, s>>>(f32, g32, e32, x, n, maxima);  // d = [h; d2], x += dx
+    for (int q = np - 1; q >= 0; --q) {                                 // dr = Q [h; d2]
+      const int k0 = q * nb, nbw = std::min(nb, K - k0);
+      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, m, wy + (size_t)q * wy_panel_doubles(nb),
+                                  f32, m, 1, work, work_elems, s, false);
+      if (st != SLQR_OK) return st;
+    }
+    add_r_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, f32, m);
+    int zflag = 0;
+    e = cudaMemcpyAsync(hmax.data(), maxima, sizeof(double) * 2 * ublocks, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&zflag, zero_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "refinement: %s", cudaGetErrorString(e));
+    double dmax = 0.0, xmax = 0.0;
+    for (int k = 0; k < ublocks; ++k) {
+      dmax = std::max(dmax, hmax[2 * k]);
+      xmax = std::max(xmax, hmax[2 * k + 1]);
+    }
+    e_cur = (xmax > 0.0) ? dmax / xmax : 0.0;
+    if (zflag) { status = SLQR_ERANK; break; }
+    if (e_cur <= tol) { status = SLQR_OK; break; }
+    if (it >= 3 && e_cur > 0.5 * e_prev) {      // no longer contracting
+      status = (e_cur <= 1e-11) ? SLQR_OK : SLQR_ENOCONV;
+      break;
+    }
+    e_prev = e_cur;
+  }
+  if (iters) *iters = std::min(it, max_iter);
+  if (err) *err = e_cur;
+  st = check_launch(ctx, "lstsq_mixed");
+  if (st != SLQR_OK) return st;
+  if (status != SLQR_OK)
+    fail(ctx, status, status == SLQR_ENOCONV ? "refinement did not reach its tolerance"
+                                             : "R has an exact zero on its diagonal");
+  return status;
+}

@@ -65,6 +65,7 @@ struct slqr_ctx {
   size_t smem_optin = 0;
   int *d_status = nullptr;             // device status word
   slqr::Workspace ws;                  // grown on demand
+  slqr::Workspace ws2;                 // buffers of the mixed-precision driver
   slqr::Profiler prof;                 // optional CUDA-event timing per kernel family
   cudaStream_t aux_stream = nullptr;   // look-ahead panels run here
   cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_panel = nullptr;
@@ -81,6 +82,7 @@ slqr_status fail(slqr_ctx *ctx, slqr_status st, const char *fmt, ...);
 
 // Make sure the workspace holds at least `bytes`; returns SLQR_OK or an error.
 slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes);
+slqr_status ensure_workspace2(slqr_ctx *ctx, size_t bytes);
 
 // Check the last launch; returns SLQR_OK or SLQR_ECUDA with the message set.
 slqr_status check_launch(slqr_ctx *ctx, const char *what);
@@ -127,5 +129,14 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
                                double *X, int ldx, int N, double *work, size_t work_doubles,
                                cudaStream_t stream);
 size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
+
+// FP32 factorization (FP64 reflector constants) and FP32 compact-WY panel
+// application (trans: Q^T, else Q) used by the mixed-precision driver.
+slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
+                       cudaStream_t stream);
+slqr_status apply_panel_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const float *A,
+                                   int lda, const double *wy_panel, float *X, int ldx, int N,
+                                   float *work, size_t work_elems, cudaStream_t stream,
+                                   bool trans);
 
 }  // namespace slqr

@@ -1,0 +1,91 @@
+"""Mixed-precision least squares for large matrices (slqr_lstsq_mixed):
+FP32 factorization with FP64 reflector constants, FP64-residual refinement of
+the augmented system.  Errors are stated against the FP64 oracle (sizes the
+oracle finishes in seconds) or against the FP64 GPU path and x_true (full
+size).  The tolerance is the specification's: refined solution error
+<= 1e-10 relative to the FP64 result, and <= 1e3 kappa 2^-52 to x_true on a
+consistent system; when kappa * u_fp32 >= 1 the refinement must report
+SLQR_ENOCONV instead of returning a wrong answer as converged.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2506_09463_gb300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def mixed(ctx, A, b):
+    from paper_2506_09463_gb300 import abi
+    m, n = A.shape
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), A.stride(1), b.data_ptr(),
+                                        x.data_ptr(), abi.SLQR_FP32, 0, 0.0,
+                                        torch.cuda.current_stream().cuda_stream)
+    return st, its, err, x
+
+
+@pytest.mark.parametrize("m,n,kappa", [(1200, 800, 1e2), (1200, 800, 1e6), (700, 700, 1e4),
+                                       (3000, 300, 1e6)])
+def test_mixed_against_oracle(ctx, m, n, kappa):
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa, seed=int(m + n))
+    for b in (b_cons, b_rand):
+        st, its, err, x = mixed(ctx, A, b)
+        assert st == 0, (st, its, err)
+        x_o = oracle.lstsq(A.cpu().numpy(), b.cpu().numpy())[0]
+        rel = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= max(1e-10, 1e3 * kappa * EPS), (rel, its, err)
+    # consistent system: forward error to x_true
+    st, its, err, x = mixed(ctx, A, b_cons)
+    assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * kappa * EPS
+
+
+def test_mixed_reports_no_convergence_when_kappa_too_large(ctx):
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(1000, 600, 1e10, seed=3)
+    st, its, err, x = mixed(ctx, A, b_rand)
+    assert st == abi.SLQR_ENOCONV
+    assert err > 1e-11
+
+
+def test_mixed_invalid_arguments(ctx):
+    from paper_2506_09463_gb300 import abi
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    p = buf.data_ptr()
+    st = abi.slqr_lstsq_mixed(ctx.ctx, 2, 4, p, 2, p, p, abi.SLQR_FP32, 0, 0.0, 0)[0]
+    assert st == abi.SLQR_EINVAL
+    st = abi.slqr_lstsq_mixed(ctx.ctx, 4, 2, p, 4, p, p, 7, 0, 0.0, 0)[0]
+    assert st == abi.SLQR_EINVAL
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_mixed_full_size_8192x4096(ctx, kappa):
+    """The 8192 x 4096 conditioned workload, as the benchmark runs it: the
+    refined solution against the FP64 GPU path and, on the consistent system,
+    against x_true."""
+    m, n = 8192, 4096
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa)
+    st, its, err, x = mixed(ctx, A, b_cons)
+    assert st == 0, (st, its, err)
+    assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * kappa * EPS
+    st, its, err, x = mixed(ctx, A, b_rand)
+    assert st == 0
+    # FP64 GPU path on the same problem
+    Af = A.t().clone().t()
+    bf = b_rand.clone()
+    xf, _ = ctx.lstsq(Af, bf)
+    assert ctx.sync() == 0
+    rel = float(torch.linalg.norm(x - xf) / torch.linalg.norm(xf))
+    assert rel <= max(1e-10, 1e3 * kappa * EPS), rel

@@ -79,6 +79,36 @@ def conditioned(m: int, n: int, kappa: float, seed: int | None = None):
     return A, b_cons, x_true, b_rand
 
 
+def conditioned_device(m: int, n: int, kappa: float, seed: int | None = None, device="cuda"):
+    """The `conditioned` recipe drawn on the device (torch RNG, library QR):
+    (A, b_consistent, x_true, b_random) as column-major float64 CUDA tensors."""
+    import torch
+    if seed is None:
+        seed = SEED_COND.get(kappa, 4)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+
+    def orth(rows, cols):
+        Gm = torch.randn(rows, cols, generator=g, dtype=torch.float64, device=device)
+        Q, R = torch.linalg.qr(Gm)
+        sgn = torch.sign(torch.diagonal(R))
+        sgn[sgn == 0] = 1.0
+        return Q * sgn
+
+    U = orth(m, n)
+    V = orth(n, n)
+    if n > 1:
+        sigma = kappa ** (-torch.arange(n, dtype=torch.float64, device=device) / (n - 1))
+    else:
+        sigma = torch.ones(1, dtype=torch.float64, device=device)
+    A = (U * sigma) @ V.T
+    A = A.t().contiguous().t()                      # column-major
+    x_true = torch.randn(n, generator=g, dtype=torch.float64, device=device)
+    b_cons = A @ x_true
+    b_rand = torch.randn(m, generator=g, dtype=torch.float64, device=device)
+    return A, b_cons, x_true, b_rand
+
+
 def batch_shapes(count: int, seed: int = SEED_BATCH, m_lo: int = 16, m_hi: int = 512):
     """Shapes of ``count`` independent problems: m ~ U{m_lo..m_hi},
     n ~ U{ceil(m/4)..m}."""
