@@ -179,7 +179,7 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
  * FP64) on a scratch copy, and the LS solution is refined against the FP64
  * A[i] by the augmented-system iteration [I A; A^T 0][r; x] = [b; 0] with
  * FP64 residuals (up to 12 sweeps; SLQR_OK at ||dx|| <= 1e-14 ||x||, or
- * when the steps stop contracting below 1e-11 ||x||, the FP64 noise level of
+ * when the steps stop contracting below 1e-10 ||x||, the FP64 noise level of
  * an ill-conditioned problem);
  * b[i][0:n] = x_i, b[i][n:m] is unspecified.
  * The host arrays are read before the call returns.  The problems must not
@@ -209,7 +209,7 @@ int slqr_batch_max_rows(void);
  *   iters, err  HOST ints/doubles or NULL: sweeps done and the last
  *          ||dx||_inf / ||x||_inf
  * Synchronous: returns when x is final.  SLQR_OK when the refinement reached
- * tol (or stopped contracting below 1e-11); SLQR_ENOCONV when it did not
+ * tol (or stopped contracting below 1e-10); SLQR_ENOCONV when it did not
  * (kappa(A) * u_fp32 too large); SLQR_ERANK for an exact zero diagonal of R;
  * SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
  */

@@ -33,7 +33,7 @@ constexpr int kBCols = 32;        // trailing columns per tile
 constexpr int kBWarps = kThreads / 32;
 constexpr int kBMaxRefine = 12;        // refinement sweeps of the mixed path
 constexpr double kBRefineTol = 1e-14;  // stop when ||dx||_inf <= tol ||x||_inf
-constexpr double kBStallOk = 1e-11;    // a stalled refinement is accepted below this
+constexpr double kBStallOk = 1e-10;    // a stalled refinement is accepted below this
 
 struct BatchProblem {
   double *A;

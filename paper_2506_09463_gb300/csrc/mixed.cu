@@ -18,6 +18,10 @@
 namespace slqr {
 
 constexpr int kRowsPerCta = 256;
+// A refinement whose steps stop contracting is accepted when its last step is
+// below this (the 1e-10 solution-error target): the step then measures the
+// FP64 noise level kappa * eps of an ill-conditioned problem.
+constexpr double kStallOk = 1e-10;
 constexpr int kColChunk = 256;
 
 // A32 = (float) A
@@ -315,7 +319,7 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
     if (zflag) { status = SLQR_ERANK; break; }
     if (e_cur <= tol) { status = SLQR_OK; break; }
     if (it >= 3 && e_cur > 0.5 * e_prev) {      // no longer contracting
-      status = (e_cur <= 1e-11) ? SLQR_OK : SLQR_ENOCONV;
+      status = (e_cur <= kStallOk) ? SLQR_OK : SLQR_ENOCONV;
       break;
     }
     e_prev = e_cur;
