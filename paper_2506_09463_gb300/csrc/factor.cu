@@ -45,33 +45,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   return v;
 }
 
-// Scaled sum of squares: value = 2^(2E) * S.  Entries are scaled by exact
-// powers of two, so neither overflow nor underflow occurs for finite input.
-constexpr int kNoExp = -4000;
-
-__device__ __forceinline__ void ssq_add(int &E, double &S, double x) {
-  if (x != 0.0) {
-    int ex = ilogb(x);
-    if (ex > E) {
-      S = ldexp(S, 2 * (E - ex));
-      E = ex;
-    }
-    double y = ldexp(x, -E);
-    S = fma(y, y, S);
-  }
-}
-
-__device__ __forceinline__ void ssq_merge(int &E, double &S, int E2, double S2) {
-  if (S2 == 0.0) return;
-  if (S == 0.0) { E = E2; S = S2; return; }
-  if (E2 > E) {
-    S = ldexp(S, 2 * (E - E2)) + S2;
-    E = E2;
-  } else {
-    S = S + ldexp(S2, 2 * (E2 - E));
-  }
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -91,7 +64,7 @@ struct PanelParams {
   void *A;             // T * (the storage type of the factorization)
   double *up;          // global up array (n doubles)
   double *wy;          // this panel's compact-WY block (Vtop | G | tau)
-  double *rec;         // 2 * P * (NB+2) doubles, layout [buf][cta][entry]
+  double *rec;         // 2 * P * NB doubles, layout [buf][cta][entry]
   double *gpart;       // P * NB*(NB-1)/2 doubles: per-CTA partial Gram terms
   double *prow;        // 2 * NB doubles
   unsigned *bar;       // monotonic arrival counter
@@ -126,17 +99,42 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
   return true;
 }
 
+// Bits of |x| as an unsigned 64-bit integer: for non-negative doubles the
+// integer order of the bit patterns is the numeric order.
+template <typename T>
+__device__ __forceinline__ unsigned abs_hi_bits(T x) {
+  return (unsigned)((unsigned long long)__double_as_longlong((double)x) >> 32) & 0x7fffffffu;
+}
+
+// 2^e as a double for e in [-1022, 1023] (exact; built from the exponent bits)
+__device__ __forceinline__ double pow2(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // One CTA per slice of R rows of the panel (rows [k0, m), NB columns); the
-// slice stays in shared memory for the whole panel.  Per column j:
-//   phase 1  local partials: scaled sum of squares of the column (from the
-//            pivot down) and dots of its tail with the later panel columns;
-//            the dots with the earlier columns (Gram terms of V^T V) are kept
-//            in a CTA-local accumulator;
+// slice stays in shared memory for the whole panel.
+//
+// Panel start: each column c gets a power-of-two scale 2^-E_c from the
+// largest |entry| of the column (one grid max-reduction of exponent bits, on
+// the integer pipe).  The in-panel reflectors are orthogonal on rows
+// [k0, m), so the column's tail never outgrows that scale: sum (x_i 2^-E_c)^2
+// neither overflows nor, for any column that still carries weight,
+// underflows.  The norm of each column is then a plain scaled sum reduced
+// like the dot products (no exponent bookkeeping per column).
+//
+// Per column j:
+//   phase 1  local partials: the scaled sum of squares of the column (from
+//            the pivot down) and the dots of its tail with the later panel
+//            columns (published); the dots with the earlier columns (Gram
+//            terms of V^T V) are kept in a CTA-local accumulator.  Lane
+//            partials are reduced through shared memory (every FP64
+//            instruction works on 32 useful lanes).
 //   barrier
 //   phase 2  every CTA reduces the published partials: thread (g, c) sums
-//            entry c over its slice g of the CTAs, then the slices are added
-//            in a fixed order (the same order in every CTA);
-//   phase 3  pivot (cl, up, b, tau), sigma per later column, update.
+//            entry c over its slice g of the CTAs (all loads in flight), the
+//            slices are added in a fixed order (the same in every CTA);
+//   pivot    one thread forms s, cl, up, b and 1/b; sigma_c = (up p_c + D_c)/b;
+//   phase 3  update of the later panel columns.
 // At the end the local Gram terms are published and reduced once, each CTA
 // reducing its share of the entries into the compact-WY store.
 template <typename T, int NB>
@@ -145,17 +143,21 @@ panel_kernel(PanelParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NW = kThreads / 32;
   constexpr int CPW = (NB + NW - 1) / NW;     // columns per warp
-  constexpr int RECW = NB + 2;                // record: E, S, d_0 .. d_{NB-1}
+  constexpr int RECW = NB;                    // record: entry c (c == j: norm, c > j: dot)
   constexpr int GROUPS = kThreads / NB;       // CTA slices of the reduction
+  constexpr int LQ = kThreads / NB;           // lane quarters in the phase-1 reduction
   T *Ps = (T *)smem_raw;                      // [NB][R] column-major panel slice
   double *Gloc = (double *)(smem_raw + ((size_t)NB * p.R * sizeof(T) + 15) / 16 * 16);
                                               // [NB][NB] local Gram terms
+  __shared__ double s_lane[NB][33];           // lane partials of phase 1
   __shared__ double s_part[GROUPS][NB];
-  __shared__ double s_partE[GROUPS], s_partS[GROUPS];
   __shared__ double s_sig[NB];                // sigma per column
   __shared__ double s_up[NB];
   __shared__ double s_prow[NB];               // pivot row of the current column
-  __shared__ double s_norm;
+  __shared__ double s_sc[NB];                 // column scales 2^-E_c
+  __shared__ int s_E[NB];
+  __shared__ double s_piv[4];                 // cl, up, 1/b, tau
+  __shared__ int s_defined;
   __shared__ int s_ok;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -176,6 +178,48 @@ panel_kernel(PanelParams p) {
   double *tau = p.wy + 2 * (size_t)NB * NB;
   __syncthreads();
 
+  // ---- panel start: column scales ------------------------------------------
+  {
+    double *rec = p.rec + (size_t)1 * RECW * p.P;    // buffer 1 (column 0 uses buffer 0)
+#pragma unroll
+    for (int t = 0; t < CPW; ++t) {
+      const int c = warp + t * NW;
+      unsigned mx = 0;
+      if (c < nbw) {
+        const int r_from = (cta == 0) ? c : 0;
+        for (int r = r_from + lane; r < RO; r += 32) mx = max(mx, abs_hi_bits(Ps[c * R + r]));
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0 && c < nbw) rec[(size_t)cta * RECW + c] = (double)mx;
+    }
+  }
+  if (!grid_barrier(p.bar, p.bar_base + (unsigned)p.P, p.status, &s_ok)) return;
+  {
+    constexpr int QMAX = (kMaxPanelCtas + GROUPS - 1) / GROUPS;
+    const double *rec = p.rec + (size_t)1 * RECW * p.P;
+    const int g = tid / NB, c = tid - g * NB;
+    const int per = (p.P + GROUPS - 1) / GROUPS;
+    const int q0 = g * per, q1 = min(p.P, q0 + per);
+    unsigned v[QMAX];
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t)
+      v[t] = (c < nbw && q0 + t < q1) ? (unsigned)__ldcg(rec + (size_t)(q0 + t) * RECW + c) : 0u;
+    unsigned mx = 0;
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t) mx = max(mx, v[t]);
+    s_part[g][c] = (double)mx;
+  }
+  __syncthreads();
+  if (tid < NB) {
+    unsigned mx = 0;
+    for (int g = 0; g < GROUPS; ++g) mx = max(mx, (unsigned)s_part[g][tid]);
+    int E = (int)((mx >> 20) & 0x7ff) - 1023;        // exponent of the largest |entry|
+    E = min(max(E, -1000), 1022);
+    s_E[tid] = E;
+    s_sc[tid] = pow2(-E);
+  }
+  __syncthreads();
+
   for (int j = 0; j < nbw; ++j) {
     const int buf = j & 1;
     double *rec = p.rec + (size_t)buf * RECW * p.P;
@@ -186,119 +230,109 @@ panel_kernel(PanelParams p) {
 
     // ---- phase 1 ---------------------------------------------------------
     {
+      // dots in the storage type T, the norm in FP64 on scaled entries
       T acc[CPW];
 #pragma unroll
       for (int t = 0; t < CPW; ++t) acc[t] = T(0);
-      int E = kNoExp;
-      double S = 0.0;
+      double nacc = 0.0;
       const bool norm_warp = (warp == (j % NW));
+      const double sc = s_sc[j];
       for (int r = r_tail + lane; r < RO; r += 32) {
-        T xv = x[r];
+        const T xv = x[r];
 #pragma unroll
         for (int t = 0; t < CPW; ++t) {
-          int c = warp + t * NW;
+          const int c = warp + t * NW;
           if (c < nbw && c != j) acc[t] = fma(xv, Ps[c * R + r], acc[t]);
         }
-        if (norm_warp) ssq_add(E, S, (double)xv);
+        if (norm_warp) {
+          const double xs = (double)xv * sc;
+          nacc = fma(xs, xs, nacc);
+        }
       }
-      if (norm_warp && cta == 0 && lane == 0) ssq_add(E, S, (double)x[j]);  // pivot entry
+      if (cta == 0 && norm_warp && lane == 0) {     // the pivot entry joins the norm
+        const double xs = (double)x[j] * sc;
+        nacc = fma(xs, xs, nacc);
+      }
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
-        int c = warp + t * NW;
-        if (c < nbw && c != j) {
-          T vt = acc[t];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) vt += __shfl_xor_sync(0xffffffffu, vt, o);
-          const double v = (double)vt;
-          if (lane == 0) {
-            if (c > j) myrec[2 + c] = v;                 // published: needed for sigma
-            else Gloc[c + j * NB] = v;                   // kept: Gram term
-          }
-        }
-      }
-      if (norm_warp) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          int E2 = __shfl_xor_sync(0xffffffffu, E, o);
-          double S2 = __shfl_xor_sync(0xffffffffu, S, o);
-          ssq_merge(E, S, E2, S2);
-        }
-        if (lane == 0) {
-          myrec[0] = (double)E;
-          myrec[1] = S;
-        }
+        const int c = warp + t * NW;
+        if (c < NB) s_lane[c][lane] = (c == j) ? nacc : (double)acc[t];
       }
       if (cta == 0 && tid < nbw) prow[tid] = (double)Ps[tid * R + j];
     }
+    __syncthreads();
+    {
+      // thread (c, quarter) sums 32 / LQ lane partials; then one thread per c
+      const int c = tid / LQ, qq = tid - c * LQ;
+      constexpr int LPQ = 32 / LQ;
+      double v = 0.0;
+#pragma unroll
+      for (int l = 0; l < LPQ; ++l) v += s_lane[c][qq * LPQ + l];
+      s_part[qq][c] = v;
+    }
+    __syncthreads();
+    if (tid < nbw) {
+      const int c = tid;
+      double v = s_part[0][c];
+#pragma unroll
+      for (int qq = 1; qq < LQ; ++qq) v += s_part[qq][c];
+      if (c >= j) myrec[c] = v;                       // norm (c == j) and dots: published
+      else Gloc[c + j * NB] = v;                      // Gram term: kept
+    }
 
     // ---- grid barrier ----------------------------------------------------
-    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(j + 1) * (unsigned)p.P, p.status, &s_ok))
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(j + 2) * (unsigned)p.P, p.status, &s_ok))
       return;
 
     // ---- phase 2 ---------------------------------------------------------
-    // Thread (g, c) reduces entry c over CTA slice g; all its loads are issued
-    // before the first is used (fixed-size unrolled loop), so the reduction
-    // costs about one L2 round trip.  The thread with c == j reduces the
-    // (E, S) norm pairs of its slice the same way.
     {
       constexpr int QMAX = (kMaxPanelCtas + GROUPS - 1) / GROUPS;
       const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
       const int g = tid / NB, c = tid - g * NB;
       const int per = (p.P + GROUPS - 1) / GROUPS;
       const int q0 = g * per, q1 = min(p.P, q0 + per);
-      if (c > j && c < nbw) {
+      if (c >= j && c < nbw) {
         double v[QMAX];
 #pragma unroll
         for (int t = 0; t < QMAX; ++t)
-          v[t] = (q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + 2 + c) : 0.0;
+          v[t] = (q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + c) : 0.0;
         double acc = 0.0;
 #pragma unroll
         for (int t = 0; t < QMAX; ++t) acc += v[t];
         s_part[g][c] = acc;
-      } else if (c == j) {
-        double ev[QMAX], sv[QMAX];
-#pragma unroll
-        for (int t = 0; t < QMAX; ++t) {
-          const bool in = (q0 + t < q1);
-          ev[t] = in ? __ldcg(rec + (size_t)(q0 + t) * RECW) : (double)kNoExp;
-          sv[t] = in ? __ldcg(rec + (size_t)(q0 + t) * RECW + 1) : 0.0;
-        }
-        int E = kNoExp;
-        double S = 0.0;
-#pragma unroll
-        for (int t = 0; t < QMAX; ++t) ssq_merge(E, S, (int)ev[t], sv[t]);
-        s_partE[g] = (double)E;
-        s_partS[g] = S;
       }
       if (tid < nbw) s_prow[tid] = prow_v;
     }
     __syncthreads();
     if (tid == 0) {
-      int E = kNoExp;
-      double S = 0.0;
-      for (int g = 0; g < GROUPS; ++g) ssq_merge(E, S, (int)s_partE[g], s_partS[g]);
-      s_norm = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
+      double S = s_part[0][j];
+      for (int g = 1; g < GROUPS; ++g) S += s_part[g][j];
+      const bool defined = (S != 0.0);
+      double cl = 0.0, upk = 0.0, rb = 0.0;
+      if (defined) {
+        const double sn = sqrt(S) * pow2(s_E[j]);
+        const double x0 = s_prow[j];
+        cl = (x0 > 0.0) ? -sn : sn;
+        upk = x0 - cl;
+        rb = 1.0 / (upk * cl);                        // 1 / b
+      }
+      s_piv[0] = cl;
+      s_piv[1] = upk;
+      s_piv[2] = rb;
+      s_piv[3] = -rb;                                 // tau = -1 / b
+      s_defined = defined;
     }
     __syncthreads();
 
-    // pivot quantities (every thread computes the same values)
-    const double s = s_norm;
-    const double x0 = s_prow[j];
-    double cl = 0.0, upk = 0.0, bk = 0.0, tk = 0.0;
-    const bool defined = (s != 0.0);
-    if (defined) {
-      cl = (x0 > 0.0) ? -s : s;
-      upk = x0 - cl;
-      bk = upk * cl;
-      tk = -1.0 / bk;
-    }
+    const bool defined = s_defined != 0;
+    const double cl = s_piv[0], upk = s_piv[1], rb = s_piv[2];
     if (tid < nbw) {
       const int c = tid;
       if (c > j) {
         double D = s_part[0][c];
 #pragma unroll
         for (int g = 1; g < GROUPS; ++g) D += s_part[g][c];
-        s_sig[c] = defined ? (upk * s_prow[c] + D) / bk : 0.0;
+        s_sig[c] = defined ? (upk * s_prow[c] + D) * rb : 0.0;
       } else if (c < j && cta == 0) {
         // G[c, j] = v_c^T v_j = v_c[k] up_j + sum_{r > k} v_c[r] x_r: the first
         // term is added once, by CTA 0
@@ -308,7 +342,7 @@ panel_kernel(PanelParams p) {
     if (cta == 0 && tid == 0) {
       s_up[j] = upk;
       p.up[p.k0 + j] = upk;
-      tau[j] = tk;
+      tau[j] = s_piv[3];
     }
     __syncthreads();
 
@@ -345,7 +379,7 @@ panel_kernel(PanelParams p) {
       if (c < jj) mine[jj * (jj - 1) / 2 + c] = Gloc[idx];
     }
   }
-  if (!grid_barrier(p.bar, p.bar_base + (unsigned)(nbw + 1) * (unsigned)p.P, p.status, &s_ok))
+  if (!grid_barrier(p.bar, p.bar_base + (unsigned)(nbw + 2) * (unsigned)p.P, p.status, &s_ok))
     return;
   for (int idx = cta + tid * p.P; idx < NB * NB; idx += kThreads * p.P) {
     const int jj = idx / NB, c = idx - jj * NB;
@@ -769,7 +803,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     if (le != cudaSuccess)
       return fail(ctx, SLQR_ECUDA, "panel launch (P=%d, smem=%zu): %s", P, smem,
                   cudaGetErrorString(le));
-    bar_base += (unsigned)P * (unsigned)(nbw + 1);
+    bar_base += (unsigned)P * (unsigned)(nbw + 2);
     return SLQR_OK;
   };
   auto update = [&](int pnl, int c_begin, int c_end) -> slqr_status {
@@ -1004,7 +1038,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     e = cudaLaunchCooperativeKernel((const void *)panel_kernel<double, NB>, dim3(P), dim3(kThreads),
                                     args, smem, stream);
     if (e != cudaSuccess) return SLQR_ECUDA;
-    bar_base += (unsigned)P * (unsigned)(nbw + 1);
+    bar_base += (unsigned)P * (unsigned)(nbw + 2);
     const int N = n - (k0 + nbw);
     if (N > 0) {
       slqr_status st = noalloc_update<NB>(num_sms, m, k0, nbw, A, lda, wy_panel,
