@@ -413,6 +413,19 @@ def run_mixed_workload(ctx, device, stream, barrier, kappas=(1e2, 1e6, 1e10), m=
                  "mixed_status": abi.STATUS_NAMES.get(st, st), "refine_iters": its,
                  "refine_last_step": err,
                  "mixed_vs_fp64_rel": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))}
+            # the same with the trailing update on the tensor cores (TF32)
+            xt = torch.zeros(n, dtype=torch.float64, device=device)
+            barrier()
+            e0.record(stream)
+            st2, its2, err2 = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
+                                                   xt.data_ptr(), abi.SLQR_TF32, 0, 0.0,
+                                                   stream.cuda_stream)
+            e1.record(stream)
+            barrier()
+            tt = e0.elapsed_time(e1)
+            r.update({"tf32_tc_ms": tt, "tf32_status": abi.STATUS_NAMES.get(st2, st2),
+                      "tf32_refine_iters": its2, "tf32_refine_last_step": err2,
+                      "tf32_vs_fp64_rel": float(torch.linalg.norm(xt - x64) / torch.linalg.norm(x64))})
             if name == "consistent":
                 r["fp64_err_vs_x_true"] = float(torch.linalg.norm(x64 - x_true) / torch.linalg.norm(x_true))
                 r["mixed_err_vs_x_true"] = float(torch.linalg.norm(xm - x_true) / torch.linalg.norm(x_true))

@@ -186,7 +186,10 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
  * overlap in memory.  Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
  */
 #define SLQR_FP64 0   /* FP64 throughout (DFMA)                                   */
-#define SLQR_FP32 1   /* FP32 factorization + FP64-residual refinement (batches)  */
+#define SLQR_FP32 1   /* FP32 factorization + FP64-residual refinement            */
+#define SLQR_TF32 2   /* as SLQR_FP32, the rank-NB trailing update on the tensor
+                         cores (tcgen05, TF32 operands, FP32 accumulation)
+                         (slqr_lstsq_mixed only)                                  */
 slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
                               double *const *A, const int *lda, double *const *up,
                               double *const *b, int prec, int *status, double *err,
@@ -203,7 +206,9 @@ int slqr_batch_max_rows(void);
  * and corrections through the FP32 factorization.
  *   A      device, m x n column-major FP64, lda >= m, m >= n >= 1 (read only)
  *   b      device, m doubles (read only);  x  device, n doubles (output)
- *   prec   SLQR_FP32
+ *   prec   SLQR_FP32 (trailing-update products on the FP32 FMA pipe) or
+ *          SLQR_TF32 (the X -= V W' products on the tensor cores, TF32
+ *          operands: refinement then converges for kappa * 2^-11 < 1)
  *   max_iter  refinement sweeps (<= 0: 30);  tol  stop at ||dx||_inf <=
  *          tol ||x||_inf (<= 0: 1e-14)
  *   iters, err  HOST ints/doubles or NULL: sweeps done and the last

@@ -88,6 +88,7 @@ KERNEL_PANEL, KERNEL_VTX, KERNEL_TW, KERNEL_UPD, KERNEL_WY_REBUILD, KERNEL_TRSM,
 KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm", "batch"]
 SLQR_FP64 = 0
 SLQR_FP32 = 1
+SLQR_TF32 = 2
 
 
 def _load() -> ctypes.CDLL:

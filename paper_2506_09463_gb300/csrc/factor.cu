@@ -33,6 +33,7 @@
 #include <cstdio>
 #include <cstdarg>
 #include <algorithm>
+#include <type_traits>
 
 namespace slqr {
 
@@ -675,8 +676,17 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
-  gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
-      A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+  if constexpr (std::is_same<T, float>::value) {
+    if (ctx->use_tc && TRANS) {
+      launch_upd_tc(NB, A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt, ctx->d_status, stream);
+    } else {
+      gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+          A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+    }
+  } else {
+    gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
+        A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+  }
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
   return check_launch(ctx, "trailing update");
 }

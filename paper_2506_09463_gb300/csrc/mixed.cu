@@ -234,7 +234,8 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);
   if (lda < m || !A || !b || !x) return fail(ctx, SLQR_EINVAL, "bad lda or NULL pointer");
   if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
-  if (prec != SLQR_FP32) return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
+  if (prec != SLQR_FP32 && prec != SLQR_TF32)
+    return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
   if (max_iter < 1) max_iter = 30;
   if (!(tol > 0.0)) tol = 1e-14;
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -276,7 +277,9 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   float *work = (float *)(base + o_work);
 
   to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32);
+  ctx->use_tc = (prec == SLQR_TF32);
   st = factor_f32(ctx, m, n, A32, m, up, wy, s);
+  ctx->use_tc = false;
   if (st != SLQR_OK) return st;
   init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, b, m, x, n);
   cudaMemsetAsync(zero_flag, 0, sizeof(int), s);

@@ -71,6 +71,7 @@ struct slqr_ctx {
   cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_panel = nullptr;
   long long launch_count = 0;          // kernels launched by this context
   slqr::Server *server = nullptr;      // request loop (slqr_submit), started lazily
+  bool use_tc = false;                 // FP32 factorization: trailing update on tcgen05 (TF32)
   std::string last_error;
   std::mutex mu;
 };
@@ -99,6 +100,12 @@ void server_stop(slqr_ctx *ctx);
 // Opt kernels into large dynamic shared memory (once per device).
 slqr_status init_kernel_attrs(slqr_ctx *ctx);
 slqr_status init_batch_attrs(slqr_ctx *ctx);
+slqr_status init_tc_attrs(slqr_ctx *ctx);
+
+// X -= V W' on a 128 x 128 tile grid with tcgen05 (TF32 operands, FP32
+// accumulation in tensor memory); see tc_update.cu.
+void launch_upd_tc(int nb, const float *A, int lda, const double *Vtop, int k0, int nbw, int M,
+                   float *X, int ldx, int N, const float *Wt, int *status, cudaStream_t stream);
 
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);

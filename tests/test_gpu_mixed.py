@@ -27,13 +27,13 @@ def ctx():
     c.close()
 
 
-def mixed(ctx, A, b):
+def mixed(ctx, A, b, prec=None):
     from paper_2506_09463_gb300 import abi
     m, n = A.shape
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), A.stride(1), b.data_ptr(),
-                                        x.data_ptr(), abi.SLQR_FP32, 0, 0.0,
-                                        torch.cuda.current_stream().cuda_stream)
+                                        x.data_ptr(), abi.SLQR_FP32 if prec is None else prec,
+                                        0, 0.0, torch.cuda.current_stream().cuda_stream)
     return st, its, err, x
 
 
@@ -89,3 +89,37 @@ def test_mixed_full_size_8192x4096(ctx, kappa):
     assert ctx.sync() == 0
     rel = float(torch.linalg.norm(x - xf) / torch.linalg.norm(xf))
     assert rel <= max(1e-10, 1e3 * kappa * EPS), rel
+
+
+# --------------------------------------------------------------------------
+# TF32 tensor-core trailing update (tcgen05): u_tf32 = 2^-11, so refinement
+# converges for kappa up to about 1e2 - 1e3 and must report SLQR_ENOCONV
+# beyond that.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n", [(1200, 800), (700, 700), (3000, 300)])
+def test_tf32_against_oracle(ctx, m, n):
+    from paper_2506_09463_gb300 import abi
+    kappa = 1e2
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa, seed=int(m + 2 * n))
+    for b in (b_cons, b_rand):
+        st, its, err, x = mixed(ctx, A, b, abi.SLQR_TF32)
+        assert st == 0, (st, its, err)
+        x_o = oracle.lstsq(A.cpu().numpy(), b.cpu().numpy())[0]
+        rel = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= 1e-10, (rel, its, err)
+
+
+def test_tf32_reports_no_convergence_when_kappa_too_large(ctx):
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(1000, 600, 1e6, seed=5)
+    st, its, err, x = mixed(ctx, A, b_rand, abi.SLQR_TF32)
+    assert st == abi.SLQR_ENOCONV
+
+
+def test_tf32_full_size_8192x4096(ctx):
+    from paper_2506_09463_gb300 import abi
+    m, n = 8192, 4096
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, 1e2)
+    st, its, err, x = mixed(ctx, A, b_cons, abi.SLQR_TF32)
+    assert st == 0, (st, its, err)
+    assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * 1e2 * EPS
