@@ -503,9 +503,11 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
   constexpr int TPE = kThreads / (COLS * NB);   // threads per entry (split over s)
   __shared__ double w[NB][COLS + 1];
   __shared__ double part[TPE][COLS * NB];
+  __shared__ double G[NB * NB];                // striu(V^T V) of the panel (ld NB)
+  __shared__ double tau[NB];
   const int tid = threadIdx.x;
-  const double *G = wy + (size_t)NB * NB;
-  const double *tau = wy + 2 * (size_t)NB * NB;
+  for (int idx = tid; idx < NB * NB; idx += kThreads) G[idx] = wy[(size_t)NB * NB + idx];
+  if (tid < NB) tau[tid] = wy[2 * (size_t)NB * NB + tid];
   const int c0 = blockIdx.x * COLS;
   {
     const int e = tid % (COLS * NB), h = tid / (COLS * NB);
@@ -541,13 +543,13 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
       const int j = TRANS ? s : nbw - 1 - s;
       double t = 0.0;
       if (TRANS) {
-        for (int q = part_id; q < j; q += 4) t = fma(__ldg(G + q + j * NB), w[q][c], t);
+        for (int q = part_id; q < j; q += 4) t = fma(G[q + j * NB], w[q][c], t);
       } else {
-        for (int q = j + 1 + part_id; q < nbw; q += 4) t = fma(__ldg(G + j + q * NB), w[q][c], t);
+        for (int q = j + 1 + part_id; q < nbw; q += 4) t = fma(G[j + q * NB], w[q][c], t);
       }
       t += __shfl_xor_sync(0xffffffffu, t, 1);
       t += __shfl_xor_sync(0xffffffffu, t, 2);
-      const double wj = __ldg(tau + j) * (w[j][c] - t);
+      const double wj = tau[j] * (w[j][c] - t);
       __syncwarp();
       if (owner) w[j][c] = wj;
       __syncwarp();
