@@ -579,6 +579,45 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
     return out
 
 
+def run_tune():
+    """Factorization times under the panel tuning knobs (panel width, smallest
+    row slice per panel CTA) for the plain-workload shapes and 8192 x 4096;
+    prints one JSON line with the table and the best setting per shape."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi, api
+    dev = torch.device("cuda", 0)
+    shapes = [(8192, 4096, 4), (16384, 2048, 2), (8192, 8192, 3)]
+    settings = [(64, 32), (64, 64), (64, 96), (64, 128), (64, 192), (32, 32), (32, 64), (32, 128)]
+    mats = {(m, n): colmajor_cuda(workloads.gaussian(m, n, seed)[0], dev) for m, n, seed in shapes}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    table = {}
+    with api.Context(0) as ctx:
+        for nb, rmin in settings:
+            abi.slqr_set_tuning(nb, rmin)
+            for (m, n), A0 in mats.items():
+                Aw = A0.t().clone().t()
+                up = torch.empty(n, dtype=torch.float64, device=dev)
+                ts = []
+                for rep in range(3):
+                    Aw.copy_(A0)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    ctx.factor(Aw, up)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                if ctx.sync() != 0:
+                    raise RuntimeError("device status")
+                fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+                table.setdefault(f"{m}x{n}", {})[f"nb{nb}_rmin{rmin}"] = {
+                    "ms": min(ts), "gflops": fl / (min(ts) / 1e3) / 1e9}
+        abi.slqr_set_tuning(0, 0)
+    best = {k: min(v.items(), key=lambda kv: kv[1]["ms"]) for k, v in table.items()}
+    print(json.dumps({"tune": table, "best": {k: {"setting": b[0], **b[1]} for k, b in best.items()}}))
+    return 0
+
+
 def run_ncu_case(m, n):
     """One factorization + Q^T (64 RHS) + back-substitution of an m x n N(0,1)
     matrix after one warm-up pass: a small, short program for ncu captures."""
@@ -614,11 +653,15 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream workload")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the factorization under the panel tuning knobs and exit")
     ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
                     help="run one small factor/apply/solve pass for profiling and exit")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(*args.ncu_case)
+    if args.tune:
+        return run_tune()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

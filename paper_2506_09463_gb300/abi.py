@@ -61,6 +61,7 @@ SIGNATURES = [
     ("slqr_panel_width", _c_int, [_c_int, _c_int]),
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
+    ("slqr_set_tuning", None, [_c_int, _c_int]),
     ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     ("slqr_apply_qt", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _vp, _c_int, _vp]),
     ("slqr_solve_r", _c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int, _vp]),
@@ -143,6 +144,10 @@ def slqr_wy_size(m: int, n: int) -> int:
 
 def slqr_max_rows() -> int:
     return _lib.slqr_max_rows()
+
+
+def slqr_set_tuning(panel_width: int = 0, panel_rows_min: int = 0) -> None:
+    _lib.slqr_set_tuning(panel_width, panel_rows_min)
 
 
 def slqr_factor(ctx, m, n, A, lda, up, wy, stream) -> int:

@@ -60,6 +60,9 @@ __device__ __forceinline__ void record_status(int *status, int code) {
 // panel kernel
 // --------------------------------------------------------------------------
 constexpr int kMaxPanelCtas = 160;
+// The panel kernel sized for at most 64 CTAs holds fewer partials per thread
+// (fewer registers), which lets trailing-update CTAs share the SMs it uses.
+constexpr int kSmallPanelCtas = 64;
 
 struct PanelParams {
   void *A;             // T * (the storage type of the factorization)
@@ -138,7 +141,7 @@ __device__ __forceinline__ double pow2(int e) {
 //   phase 3  update of the later panel columns.
 // At the end the local Gram terms are published and reduced once, each CTA
 // reducing its share of the entries into the compact-WY store.
-template <typename T, int NB>
+template <typename T, int NB, int PMAX>
 __global__ void __launch_bounds__(kThreads)
 panel_kernel(PanelParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -196,7 +199,7 @@ panel_kernel(PanelParams p) {
   }
   if (!grid_barrier(p.bar, p.bar_base + (unsigned)p.P, p.status, &s_ok)) return;
   {
-    constexpr int QMAX = (kMaxPanelCtas + GROUPS - 1) / GROUPS;
+    constexpr int QMAX = (PMAX + GROUPS - 1) / GROUPS;
     const double *rec = p.rec + (size_t)1 * RECW * p.P;
     const int g = tid / NB, c = tid - g * NB;
     const int per = (p.P + GROUPS - 1) / GROUPS;
@@ -287,7 +290,7 @@ panel_kernel(PanelParams p) {
 
     // ---- phase 2 ---------------------------------------------------------
     {
-      constexpr int QMAX = (kMaxPanelCtas + GROUPS - 1) / GROUPS;
+      constexpr int QMAX = (PMAX + GROUPS - 1) / GROUPS;
       const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
       const int g = tid / NB, c = tid - g * NB;
       const int per = (p.P + GROUPS - 1) / GROUPS;
@@ -631,8 +634,14 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 // --------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------
+// Tuning knobs (slqr_set_tuning): panel width override and the smallest
+// slice of rows a panel CTA holds (which sets how many CTAs share a panel).
+static int g_tune_nb = 0;
+static int g_tune_rows_min = 32;
+
 int panel_width(int m, int n) {
   (void)m;
+  if (g_tune_nb == 32 || g_tune_nb == 64) return g_tune_nb;
   return n <= 256 ? 32 : 64;
 }
 
@@ -708,17 +717,29 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb, co
 slqr_status init_kernel_attrs(slqr_ctx *ctx) {
   const int max_smem = 200 * 1024;
   cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(panel_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           max_smem);
+  e = cudaFuncSetAttribute(panel_kernel<double, 32, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 32, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 64, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 64, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 32, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 32, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 64, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 64, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_upd_kernel<double, 64>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * (kBM + kBN) * 8);
@@ -735,8 +756,14 @@ static int panel_rows_per_cta(int M, int nbw, int num_sms) {
   const int ctas = std::min(num_sms, kMaxPanelCtas);
   int R = (M + ctas - 1) / ctas;
   R = std::max(R, nbw);
-  R = std::max(R, 32);
+  R = std::max(R, g_tune_rows_min);
   return R;
+}
+
+template <typename T, int NB>
+static const void *panel_kernel_for(int P) {
+  return P <= kSmallPanelCtas ? (const void *)panel_kernel<T, NB, kSmallPanelCtas>
+                              : (const void *)panel_kernel<T, NB, kMaxPanelCtas>;
 }
 
 static int max_rows_per_cta(int nb, size_t elem = sizeof(double)) {
@@ -809,7 +836,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     double pflops = 0.0;
     for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
     int slot = prof_begin(ctx, s);
-    cudaError_t le = cudaLaunchCooperativeKernel((const void *)panel_kernel<T, NB>, dim3(P),
+    cudaError_t le = cudaLaunchCooperativeKernel(panel_kernel_for<T, NB>(P), dim3(P),
                                                  dim3(kThreads), args, smem, s);
     prof_end(ctx, s, slot, kPanel, pflops);
     if (le != cudaSuccess)
@@ -886,6 +913,11 @@ slqr_status apply_panel_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, int nb
 using namespace slqr;
 
 extern "C" int slqr_panel_width(int m, int n) { return panel_width(m, n); }
+
+extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
+  g_tune_nb = (panel_width == 32 || panel_width == 64) ? panel_width : 0;
+  g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : 32;
+}
 
 extern "C" size_t slqr_wy_size(int m, int n) {
   if (m <= 0 || n <= 0) return 0;
@@ -965,11 +997,29 @@ static slqr_status noalloc_setup(int dev, double **ptr, int *sms) {
     return SLQR_ECUDA;
   }
   const int max_smem = 200 * 1024;
-  e = cudaFuncSetAttribute(panel_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           max_smem);
+  e = cudaFuncSetAttribute(panel_kernel<double, 32, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(panel_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem);
+    e = cudaFuncSetAttribute(panel_kernel<double, 32, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<double, 64, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<double, 64, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 32, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 32, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 64, kSmallPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_kernel<float, 64, kMaxPanelCtas>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_upd_kernel<double, 64>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * (kBM + kBN) * 8);
@@ -1047,8 +1097,8 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(double));
-    e = cudaLaunchCooperativeKernel((const void *)panel_kernel<double, NB>, dim3(P), dim3(kThreads),
-                                    args, smem, stream);
+    e = cudaLaunchCooperativeKernel(panel_kernel_for<double, NB>(P), dim3(P), dim3(kThreads), args,
+                                    smem, stream);
     if (e != cudaSuccess) return SLQR_ECUDA;
     bar_base += (unsigned)P * (unsigned)(nbw + 2);
     const int N = n - (k0 + nbw);
