@@ -588,7 +588,7 @@ def run_tune():
     from paper_2506_09463_gb300 import abi, api
     dev = torch.device("cuda", 0)
     shapes = [(8192, 4096, 4), (16384, 2048, 2), (8192, 8192, 3)]
-    settings = [(64, 32), (64, 64), (64, 96), (64, 128), (64, 192), (32, 32), (32, 64), (32, 128)]
+    settings = [(64, 32), (64, 128), (64, 192), (64, 256), (64, 320), (64, 384), (32, 192), (32, 256)]
     mats = {(m, n): colmajor_cuda(workloads.gaussian(m, n, seed)[0], dev) for m, n, seed in shapes}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     table = {}

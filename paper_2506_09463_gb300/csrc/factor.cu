@@ -637,7 +637,8 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 // Tuning knobs (slqr_set_tuning): panel width override and the smallest
 // slice of rows a panel CTA holds (which sets how many CTAs share a panel).
 static int g_tune_nb = 0;
-static int g_tune_rows_min = 32;
+constexpr int kDefaultRowsMin = 192;   // measured best on GB300 for 2048..8192 columns
+static int g_tune_rows_min = kDefaultRowsMin;
 
 int panel_width(int m, int n) {
   (void)m;
@@ -661,6 +662,15 @@ size_t panel_update_work_doubles(int m, int N, int nb, int num_sms) {
   return (4 * slots + ntiles + 1) * kBN * nb + (size_t)nb * N;
 }
 
+// Partial slice 0 of W = V^T X over the top 64 rows of a panel (where V is
+// the Vtop triangle), on the FP32 FMA pipe; the tensor-core kernel does the
+// remaining rows.
+static void vtop_part_f32(const float *A, int lda, const double *Vtop, int k0, int rows,
+                          const float *X, int ldx, int N, float *Wp, cudaStream_t stream) {
+  gemm_vtx_kernel<float, 64, false><<<dim3((N + kBN - 1) / kBN, 1), kThreads, 0, stream>>>(
+      A, lda, Vtop, k0, 64, rows, X, ldx, N, rows, Wp);
+}
+
 template <typename T, int NB, bool TRANS = true>
 static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const T *A, int lda,
                                      const double *wy_panel, T *X, int ldx, int N, T *work,
@@ -679,11 +689,24 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   const double *Vtop = wy_panel;
   const double gemm_flops = 2.0 * M * nbw * (double)N;
   int slot = prof_begin(ctx, stream);
-  gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
-      A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
+  int slices = 0;
+  if constexpr (std::is_same<T, float>::value && NB == 64) {
+    // TF32 path: W = V^T X on the tensor cores when X lies in A (the factorization)
+    if (ctx->use_tc && TRANS && nbw == 64 && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
+      const int xcol0 = (int)((X - A) / lda);
+      slices = launch_vtx_tc(A, lda, Vtop, k0, M, xcol0, N, Wp, work_elems, ctx->num_sms,
+                             ctx->d_status, stream, &vtop_part_f32);
+      if (slices > 0) Wt = work + (size_t)slices * N * NB;
+    }
+  }
+  if (slices == 0) {
+    slices = Seff;
+    gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
+        A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
+  }
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  launch_tw<T, NB, TRANS>(Wp, Seff, N, wy_panel, nbw, Wt, stream);
+  launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
@@ -916,7 +939,7 @@ extern "C" int slqr_panel_width(int m, int n) { return panel_width(m, n); }
 
 extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
   g_tune_nb = (panel_width == 32 || panel_width == 64) ? panel_width : 0;
-  g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : 32;
+  g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : kDefaultRowsMin;
 }
 
 extern "C" size_t slqr_wy_size(int m, int n) {

@@ -26,12 +26,12 @@ constexpr int kColChunk = 256;
 
 // A32 = (float) A
 __global__ void to_f32_kernel(const double *__restrict__ A, int lda, int m, int n,
-                              float *__restrict__ A32) {
-  const size_t total = (size_t)m * n;
+                              float *__restrict__ A32, int lda32) {
+  const size_t total = (size_t)lda32 * n;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / m), i = (int)(idx - (size_t)j * m);
-    A32[idx] = (float)A[SLQR_IDX(i, j, lda)];
+    const int j = (int)(idx / lda32), i = (int)(idx - (size_t)j * lda32);
+    A32[idx] = (i < m) ? (float)A[SLQR_IDX(i, j, lda)] : 0.f;
   }
 }
 
@@ -250,7 +250,8 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  const size_t o_a32 = take((size_t)m * n * sizeof(float));
+  const int lda32 = (m + 31) / 32 * 32;   // 128-byte aligned columns (TMA-friendly)
+  const size_t o_a32 = take((size_t)lda32 * n * sizeof(float));
   const size_t o_up = take((size_t)n * sizeof(double));
   const size_t o_wy = take(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double));
   const size_t o_r = take((size_t)m * sizeof(double));
@@ -276,9 +277,9 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   int *zero_flag = (int *)(base + o_flag);
   float *work = (float *)(base + o_work);
 
-  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32);
+  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32, lda32);
   ctx->use_tc = (prec == SLQR_TF32);
-  st = factor_f32(ctx, m, n, A32, m, up, wy, s);
+  st = factor_f32(ctx, m, n, A32, lda32, up, wy, s);
   ctx->use_tc = false;
   if (st != SLQR_OK) return st;
   init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, b, m, x, n);
@@ -291,19 +292,19 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
         A, lda, m, n, x, part);
     resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(b, r, part, chunks, m, f32);
     resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, r, g32);
-    trsv_f32<false>(A32, m, n, g32, zero_flag, s);                       // h = R^-T g
+    trsv_f32<false>(A32, lda32, n, g32, zero_flag, s);                   // h = R^-T g
     for (int p = 0; p < np; ++p) {                                      // d = Q^T f
       const int k0 = p * nb, nbw = std::min(nb, K - k0);
-      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, m, wy + (size_t)p * wy_panel_doubles(nb),
+      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, lda32, wy + (size_t)p * wy_panel_doubles(nb),
                                   f32, m, 1, work, work_elems, s, true);
       if (st != SLQR_OK) return st;
     }
     form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(f32, g32, m, n, e32);
-    trsv_f32<true>(A32, m, n, e32, zero_flag, s);                        // dx = R^-1 (d1 - h)
+    trsv_f32<true>(A32, lda32, n, e32, zero_flag, s);                    // dx = R^-1 (d1 - h)
     update_kernel<<<ublocks, 256, 0, s>>>(f32, g32, e32, x, n, maxima);  // d = [h; d2], x += dx
     for (int q = np - 1; q >= 0; --q) {                                 // dr = Q [h; d2]
       const int k0 = q * nb, nbw = std::min(nb, K - k0);
-      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, m, wy + (size_t)q * wy_panel_doubles(nb),
+      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, lda32, wy + (size_t)q * wy_panel_doubles(nb),
                                   f32, m, 1, work, work_elems, s, false);
       if (st != SLQR_OK) return st;
     }

@@ -106,6 +106,12 @@ slqr_status init_tc_attrs(slqr_ctx *ctx);
 // accumulation in tensor memory); see tc_update.cu.
 void launch_upd_tc(int nb, const float *A, int lda, const double *Vtop, int k0, int nbw, int M,
                    float *X, int ldx, int N, const float *Wt, int *status, cudaStream_t stream);
+// W = V^T X partials with TMA + tcgen05 for a full 64-wide panel; returns the
+// number of partial slices written to Wp (0: not applicable).
+int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,
+                  float *Wp, size_t work_elems, int num_sms, int *status, cudaStream_t stream,
+                  void (*vtop_part)(const float *, int, const double *, int, int, const float *, int,
+                                    int, float *, cudaStream_t));
 
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);
