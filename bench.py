@@ -588,7 +588,8 @@ def run_tune():
     from paper_2506_09463_gb300 import abi, api
     dev = torch.device("cuda", 0)
     shapes = [(8192, 4096, 4), (16384, 2048, 2), (8192, 8192, 3)]
-    settings = [(64, 32), (64, 128), (64, 192), (64, 256), (64, 320), (64, 384), (32, 192), (32, 256)]
+    settings = [(64, 32), (64, 128), (64, 160), (64, 192), (64, 224), (64, 256), (64, 320),
+                (32, 192), (32, 256)]
     mats = {(m, n): colmajor_cuda(workloads.gaussian(m, n, seed)[0], dev) for m, n, seed in shapes}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     table = {}
@@ -599,14 +600,17 @@ def run_tune():
                 Aw = A0.t().clone().t()
                 up = torch.empty(n, dtype=torch.float64, device=dev)
                 ts = []
-                for rep in range(3):
-                    Aw.copy_(A0)
-                    torch.cuda.synchronize()
-                    e0.record()
-                    ctx.factor(Aw, up)
-                    e1.record()
-                    torch.cuda.synchronize()
-                    ts.append(e0.elapsed_time(e1))
+                try:
+                    for rep in range(3):
+                        Aw.copy_(A0)
+                        torch.cuda.synchronize()
+                        e0.record()
+                        ctx.factor(Aw, up)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                except abi.SlqrError:
+                    continue                  # setting outside the kernel's limits
                 if ctx.sync() != 0:
                     raise RuntimeError("device status")
                 fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
@@ -615,6 +619,56 @@ def run_tune():
         abi.slqr_set_tuning(0, 0)
     best = {k: min(v.items(), key=lambda kv: kv[1]["ms"]) for k, v in table.items()}
     print(json.dumps({"tune": table, "best": {k: {"setting": b[0], **b[1]} for k, b in best.items()}}))
+    return 0
+
+
+def run_ncu_mixed(m, n):
+    """Two TF32 mixed-precision LS solves of an iid N(0,1) m x n matrix: a
+    small program for ncu captures of the tensor-core kernels (no torch.linalg
+    call, which does not load under the profiler)."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi, api
+    dev = torch.device("cuda", 0)
+    A_h, b_h = workloads.gaussian(m, n, workloads.SEED_TALL)
+    A = colmajor_cuda(A_h, dev)
+    b = torch.from_numpy(b_h).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    with api.Context(0) as ctx:
+        for _ in range(2):
+            st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
+                                                x.data_ptr(), abi.SLQR_TF32, 0, 0.0,
+                                                torch.cuda.current_stream().cuda_stream)
+            if st != 0:
+                raise RuntimeError(f"mixed status {st}")
+    print(f"ncu mixed case {m}x{n} done ({its} sweeps)")
+    return 0
+
+
+def run_ncu_batch(count):
+    """A batch of `count` problems of the batched workload, FP64 then FP32."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi, api
+    ms, ns = workloads.batch_shapes(count)
+    A_flat, b_flat, a_off, b_off = workloads.batch_problems_device(ms, ns, workloads.SEED_BATCH)
+    up = torch.zeros(int(ns.sum()) + 1, dtype=torch.float64, device=A_flat.device)
+    up_off = np.concatenate([[0], np.cumsum(ns)[:-1]])
+    A0, b0 = A_flat.clone(), b_flat.clone()
+    with api.Context(0) as ctx:
+        for prec in (abi.SLQR_FP64, abi.SLQR_FP32):
+            A_flat.copy_(A0)
+            b_flat.copy_(b0)
+            st = abi.slqr_batch_factor(ctx.ctx, list(ms), list(ns),
+                                       [A_flat.data_ptr() + int(o) * 8 for o in a_off],
+                                       [int(m) for m in ms],
+                                       [up.data_ptr() + int(o) * 8 for o in up_off],
+                                       [b_flat.data_ptr() + int(o) * 8 for o in b_off], prec,
+                                       None, None, torch.cuda.current_stream().cuda_stream)
+            abi.check(ctx.ctx, st, "batch")
+            if ctx.sync() != 0:
+                raise RuntimeError("device status")
+    print(f"ncu batch case {count} done")
     return 0
 
 
@@ -653,6 +707,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream workload")
+    ap.add_argument("--ncu-mixed", type=int, nargs=2, metavar=("M", "N"),
+                    help="run one TF32 mixed-precision solve for profiling and exit")
+    ap.add_argument("--ncu-batch", type=int, metavar="COUNT",
+                    help="run one FP64 and one FP32 batch for profiling and exit")
     ap.add_argument("--tune", action="store_true",
                     help="time the factorization under the panel tuning knobs and exit")
     ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
@@ -662,6 +720,10 @@ def main():
         return run_ncu_case(*args.ncu_case)
     if args.tune:
         return run_tune()
+    if args.ncu_mixed:
+        return run_ncu_mixed(*args.ncu_mixed)
+    if args.ncu_batch:
+        return run_ncu_batch(args.ncu_batch)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

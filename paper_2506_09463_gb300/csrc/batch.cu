@@ -331,7 +331,8 @@ batch_factor_fp64_kernel(BatchParams bp) {
 // (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64 from the
 // original A, the correction through the FP32 QR:
 //   h = R^-T g,  d = Q^T f,  dx = R^-1 (d[0:n] - h),  dr = Q [h; d[n:m]].
-// This converges to the FP64 LS solution when kappa * u_fp32 < 1, for
+// This converges to the FP64 LS solution when kappa times the backward error
+// of the FP32 factorization (a modest multiple of u_fp32) is below 1, for
 // consistent and inconsistent right-hand sides alike.
 // --------------------------------------------------------------------------
 struct BatchMixedParams {
@@ -484,7 +485,8 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
     float *g = f + kBMaxRows;             // n   g, then h
     float *e = g + kBMaxRows;             // m
     float *w = e + kBMaxRows;             // kBNB
-    for (int i = tid; i < m; i += kThreads) r[i] = pr.b[i];
+    // r = 0, x = 0: the first sweep is the plain QR solve (see mixed.cu)
+    for (int i = tid; i < m; i += kThreads) r[i] = 0.0;
     for (int i = tid; i < n; i += kThreads) x[i] = 0.0;
     __syncthreads();
     int status = SLQR_ENOCONV;

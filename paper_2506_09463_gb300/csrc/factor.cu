@@ -775,11 +775,16 @@ slqr_status init_kernel_attrs(slqr_ctx *ctx) {
 }
 
 // rows per CTA of the panel kernel
-static int panel_rows_per_cta(int M, int nbw, int num_sms) {
+// Rows per panel CTA: at least the tuning minimum, and enough that the panel
+// fits the small-grid kernel (at most 64 CTAs, fewer registers) whenever the
+// slice still fits shared memory (max_rows).
+static int panel_rows_per_cta(int M, int nbw, int num_sms, int max_rows) {
   const int ctas = std::min(num_sms, kMaxPanelCtas);
   int R = (M + ctas - 1) / ctas;
   R = std::max(R, nbw);
   R = std::max(R, g_tune_rows_min);
+  const int r_small = (M + kSmallPanelCtas - 1) / kSmallPanelCtas;
+  if (r_small <= max_rows) R = std::max(R, r_small);
   return R;
 }
 
@@ -842,7 +847,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     const int M = m - k0;
-    const int R = panel_rows_per_cta(M, nbw, Pmax);
+    const int R = panel_rows_per_cta(M, nbw, Pmax, max_rows_per_cta(NB, sizeof(T)));
     if (R > max_rows_per_cta(NB, sizeof(T)))
       return fail(ctx, SLQR_EINVAL, "m = %d is too large for the shared-memory panel", m);
     const int P = (M + R - 1) / R;
@@ -1109,7 +1114,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     const int M = m - k0;
-    const int R = panel_rows_per_cta(M, nbw, num_sms);
+    const int R = panel_rows_per_cta(M, nbw, num_sms, max_rows_per_cta(NB));
     if (R > max_rows_per_cta(NB)) return SLQR_EINVAL;
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);

@@ -7,8 +7,9 @@
 // against the FP64 A with the augmented system [I A; A^T 0][r; x] = [b; 0]
 // (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64, the correction
 // through the FP32 QR, h = R^-T g, d = Q^T f, dx = R^-1 (d[0:n] - h),
-// dr = Q [h; d[n:m]].  This converges to the FP64 LS solution when
-// kappa * u_low < 1, for consistent and inconsistent right-hand sides.
+// dr = Q [h; d[n:m]].  This converges to the FP64 LS solution when kappa times
+// the backward error of the low-precision factorization (a modest multiple of
+// u_low) is below 1, for consistent and inconsistent right-hand sides.
 #include "slqr_internal.cuh"
 
 #include <algorithm>
@@ -117,10 +118,13 @@ __global__ void add_r_kernel(double *__restrict__ r, const float *__restrict__ d
   if (i < m) r[i] += (double)dr[i];
 }
 
-__global__ void init_kernel(double *__restrict__ r, const double *__restrict__ b, int m,
-                            double *__restrict__ x, int n) {
+// r = 0, x = 0: the first sweep (f = b, g = 0) is then the plain QR solve
+// x = R^-1 (Q^T b)[0:n], r = Q [0; (Q^T b)[n:m]].  Starting from r = b
+// instead would route the first correction through R^-T A^T b, whose error
+// grows like kappa^2 u_fp32.
+__global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ x, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) r[i] = b[i];
+  if (i < m) r[i] = 0.0;
   if (i < n) x[i] = 0.0;
 }
 
@@ -282,7 +286,7 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   st = factor_f32(ctx, m, n, A32, lda32, up, wy, s);
   ctx->use_tc = false;
   if (st != SLQR_OK) return st;
-  init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, b, m, x, n);
+  init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, m, x, n);
   cudaMemsetAsync(zero_flag, 0, sizeof(int), s);
   std::vector<double> hmax(2 * ublocks);
   int it = 0, status = SLQR_ENOCONV;
