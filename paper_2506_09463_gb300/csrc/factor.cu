@@ -498,7 +498,7 @@ gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 //   T^T w:  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q),  j = 0 .. nbw-1
 //   T w:    w'_j = tau_j (w_j - sum_{q>j} G[j,q] w'_q),  j = nbw-1 .. 0
 // with four lanes per column splitting the inner sum (FP64 arithmetic).
-template <typename T, int NB, bool TRANS, int COLS>
+template <typename T, int NB, bool TRANS, int COLS, bool CMAJOR = false>
 __global__ void __launch_bounds__(kThreads)
 tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
           T *__restrict__ Wt) {
@@ -539,43 +539,61 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
     w[a][c] = v;
   }
   __syncthreads();
-  if (tid < 32) {                               // the whole first warp takes part
-    const int c = min(tid >> 2, COLS - 1), part_id = tid & 3;
-    const bool owner = (tid >> 2) < COLS && part_id == 0;
+  // Substitution, right-looking, one warp per column with the column's NB
+  // entries in registers (lane l holds rows l and l + 32): at step j the
+  // owner's entry becomes w'_j = tau_j w_j, which is broadcast and folded into
+  // every row still to come (TRANS: k > j with G[j, k]; else k < j with
+  // G[k, j]).  The chain per step is one shuffle, one multiply and one FMA.
+  static_assert(COLS <= kThreads / 32, "one warp per column");
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp < COLS) {
+    const int c = warp;
+    double r0 = w[lane][c];
+    double r1 = (NB > 32) ? w[(lane + 32) & (NB - 1)][c] : 0.0;
     for (int s = 0; s < nbw; ++s) {
       const int j = TRANS ? s : nbw - 1 - s;
-      double t = 0.0;
+      const double wj = __shfl_sync(0xffffffffu, (j < 32) ? r0 : r1, j & 31);
+      const double wpj = tau[j] * wj;
       if (TRANS) {
-        for (int q = part_id; q < j; q += 4) t = fma(G[q + j * NB], w[q][c], t);
+        if (lane > j) r0 = fma(-G[j + lane * NB], wpj, r0);
+        if (NB > 32 && lane + 32 > j) r1 = fma(-G[j + ((lane + 32) & (NB - 1)) * NB], wpj, r1);
       } else {
-        for (int q = j + 1 + part_id; q < nbw; q += 4) t = fma(G[j + q * NB], w[q][c], t);
+        if (lane < j) r0 = fma(-G[lane + j * NB], wpj, r0);
+        if (NB > 32 && lane + 32 < j) r1 = fma(-G[lane + 32 + j * NB], wpj, r1);
       }
-      t += __shfl_xor_sync(0xffffffffu, t, 1);
-      t += __shfl_xor_sync(0xffffffffu, t, 2);
-      const double wj = tau[j] * (w[j][c] - t);
-      __syncwarp();
-      if (owner) w[j][c] = wj;
-      __syncwarp();
+      if (lane == (j & 31)) {
+        if (j < 32) r0 = wpj;
+        else r1 = wpj;
+      }
     }
+    w[lane][c] = r0;
+    if (NB > 32) w[(lane + 32) & (NB - 1)][c] = r1;
   }
   __syncthreads();
-  for (int idx = tid; idx < NB * COLS; idx += kThreads) {
-    const int a = idx / COLS, c = idx - a * COLS;
-    if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? (T)w[a][c] : T(0);
+  if (CMAJOR) {                                 // W'^T: [column][reflector] (tensor-core path)
+    for (int idx = tid; idx < NB * COLS; idx += kThreads) {
+      const int c = idx / NB, a = idx - c * NB;
+      if (c0 + c < N) Wt[(size_t)(c0 + c) * NB + a] = (a < nbw) ? (T)w[a][c] : T(0);
+    }
+  } else {                                      // W': [reflector][column]
+    for (int idx = tid; idx < NB * COLS; idx += kThreads) {
+      const int a = idx / COLS, c = idx - a * COLS;
+      if (c0 + c < N) Wt[(size_t)a * N + c0 + c] = (a < nbw) ? (T)w[a][c] : T(0);
+    }
   }
 }
 
 // Launch W' = T^T W (TRANS) or T W: one column per CTA (4 threads per entry)
 // while there are few columns, kThreads / NB columns per CTA otherwise.
-template <typename T, int NB, bool TRANS>
+template <typename T, int NB, bool TRANS, bool CMAJOR = false>
 static void launch_tw(const T *Wp, int S, int N, const double *wy, int nbw, T *Wt,
                       cudaStream_t stream) {
   constexpr int WIDE = kThreads / NB;
   if (N <= 4 * 152) {
-    tw_kernel<T, NB, TRANS, 1><<<N, kThreads, 0, stream>>>(Wp, S, N, wy, nbw, Wt);
+    tw_kernel<T, NB, TRANS, 1, CMAJOR><<<N, kThreads, 0, stream>>>(Wp, S, N, wy, nbw, Wt);
   } else {
-    tw_kernel<T, NB, TRANS, WIDE><<<(N + WIDE - 1) / WIDE, kThreads, 0, stream>>>(Wp, S, N, wy,
-                                                                                 nbw, Wt);
+    tw_kernel<T, NB, TRANS, WIDE, CMAJOR><<<(N + WIDE - 1) / WIDE, kThreads, 0, stream>>>(
+        Wp, S, N, wy, nbw, Wt);
   }
 }
 
@@ -690,13 +708,30 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   const double gemm_flops = 2.0 * M * nbw * (double)N;
   int slot = prof_begin(ctx, stream);
   int slices = 0;
+  bool tc = false;
   if constexpr (std::is_same<T, float>::value && NB == 64) {
-    // TF32 path: W = V^T X on the tensor cores when X lies in A (the factorization)
+    // TF32 path: both products on the tensor cores for a full panel whose X
+    // lies in A (the factorization); W'^T and a row-major V follow the partials
     if (ctx->use_tc && TRANS && nbw == 64 && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
       const int xcol0 = (int)((X - A) / lda);
       slices = launch_vtx_tc(A, lda, Vtop, k0, M, xcol0, N, Wp, work_elems, ctx->num_sms,
                              ctx->d_status, stream, &vtop_part_f32);
-      if (slices > 0) Wt = work + (size_t)slices * N * NB;
+      if (slices > 0) {
+        Wt = work + (size_t)slices * N * NB;
+        tc = (size_t)slices * N * NB + (size_t)NB * N + (size_t)M * NB <= work_elems;
+        if (!tc) {                                  // partials only: finish on the FMA pipe
+          prof_end(ctx, stream, slot, kVtx, gemm_flops);
+          slot = prof_begin(ctx, stream);
+          launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
+          prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
+          slot = prof_begin(ctx, stream);
+          gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads,
+                                   (size_t)NB * (kBM + kBN) * sizeof(T), stream>>>(
+              A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+          prof_end(ctx, stream, slot, kUpd, gemm_flops);
+          return check_launch(ctx, "trailing update");
+        }
+      }
     }
   }
   if (slices == 0) {
@@ -706,21 +741,24 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   }
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
-  launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
+  if (tc) launch_tw<T, NB, TRANS, true>(Wp, slices, N, wy_panel, nbw, Wt, stream);
+  else launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
   size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
+  bool done = false;
   if constexpr (std::is_same<T, float>::value) {
-    if (ctx->use_tc && TRANS) {
-      launch_upd_tc(NB, A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt, ctx->d_status, stream);
-    } else {
-      gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
-          A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+    if (tc) {
+      const int xcol0 = (int)((X - A) / lda);
+      done = launch_upd_tc((const float *)A, lda, Vtop, k0, M, xcol0, N, (const float *)Wt,
+                           (float *)(Wt + (size_t)NB * N), ctx->d_status, stream);
+      if (!done)                                    // no tensor map: W' again in FMA layout
+        launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
     }
-  } else {
+  }
+  if (!done)
     gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
         A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
-  }
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
   return check_launch(ctx, "trailing update");
 }
@@ -815,7 +853,9 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   const size_t gpart_doubles = (size_t)Pmax * NB * (NB - 1) / 2;
   const size_t prow_doubles = 2 * (size_t)NB;
   const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
-  const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms);
+  // (the FP32 path also keeps a row-major copy of V for the tensor-core update)
+  const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms) +
+                              (std::is_same<T, float>::value ? (size_t)m * NB : 0);
   const size_t bytes = 256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles) * 8 +
                        work_doubles * sizeof(T) + 256;
   slqr_status st = ensure_workspace(ctx, bytes);
@@ -826,7 +866,8 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   double *gpart = rec + rec_doubles;
   double *prow = gpart + gpart_doubles;
   double *wy_store = wy ? wy : prow + prow_doubles;
-  T *work = (T *)(prow + prow_doubles + wy_doubles);
+  // 256-byte aligned (vector stores and TMA maps of the trailing update)
+  T *work = (T *)align_up((size_t)(prow + prow_doubles + wy_doubles), 256);
 
   cudaError_t e = cudaMemsetAsync(bar, 0, 256, stream);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));

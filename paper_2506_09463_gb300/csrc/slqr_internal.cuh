@@ -102,10 +102,13 @@ slqr_status init_kernel_attrs(slqr_ctx *ctx);
 slqr_status init_batch_attrs(slqr_ctx *ctx);
 slqr_status init_tc_attrs(slqr_ctx *ctx);
 
-// X -= V W' on a 128 x 128 tile grid with tcgen05 (TF32 operands, FP32
-// accumulation in tensor memory); see tc_update.cu.
-void launch_upd_tc(int nb, const float *A, int lda, const double *Vtop, int k0, int nbw, int M,
-                   float *X, int ldx, int N, const float *Wt, int *status, cudaStream_t stream);
+// X -= V W' for a full 64-wide panel on a 128 x 64 tile grid with tcgen05
+// (TF32 operands, FP32 accumulation in tensor memory), X = columns
+// [xcol0, xcol0 + N) of A from row k0; Wt = W'^T ([column][64]); Vr: scratch
+// of M x 64 floats for the row-major V.  Returns false (nothing launched) when
+// a tensor map cannot be encoded; see tc_update.cu.
+bool launch_upd_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,
+                   const float *Wt, float *Vr, int *status, cudaStream_t stream);
 // W = V^T X partials with TMA + tcgen05 for a full 64-wide panel; returns the
 // number of partial slices written to Wp (0: not applicable).
 int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,

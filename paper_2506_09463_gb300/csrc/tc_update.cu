@@ -1,20 +1,16 @@
 // tc_update.cu -- the two products of the compact-WY trailing update on the
 // 5th-generation tensor cores (tcgen05, kind::tf32), for the FP32
 // factorization of the mixed-precision path:
-//   upd_tc_kernel  X -= V W'   (K = NB: operands staged by the threads)
-//   vtx_tc_kernel  W = V^T X   (K = rows: operands streamed by TMA)
+//   vtx_tc_kernel  W = V^T X   (K = rows, a 4-stage TMA ring)
+//   upd_tc_kernel  X -= V W'   (K = 64 reflectors, one TMA batch per tile)
 //
-// One CTA (128 threads) owns a 128 x 128 tile of X.  The two operands are
-// staged in shared memory in the K-major, 128-byte-swizzled layout the MMA
-// reads (8-row x 128-byte atoms, 16-byte chunks XOR-ed with the row):
-//   A = V   (128 rows of the tile x NB reflectors),
-//   B = W'^T (128 columns of the tile x NB reflectors),
-// one elected thread issues NB/8 MMAs (M = 128, N = 128, K = 8 each) into a
-// 128 x 128 FP32 accumulator in tensor memory, commits them to an mbarrier,
-// and after a bounded wait the four warps read the accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile) and
-// subtract it from X.  TF32 keeps 10 mantissa bits of each operand; the
-// products accumulate in FP32.
+// Operands reach shared memory by TMA (cp.async.bulk.tensor) in the K-major,
+// 128-byte-swizzled layout the MMA reads (8-row x 128-byte atoms, 16-byte
+// chunks XOR-ed with the row), one elected thread issues the MMAs into an FP32
+// accumulator in tensor memory and commits them to an mbarrier, and after a
+// bounded wait the four warps read the accumulator back with tcgen05.ld (warp
+// w owns TMEM lanes 32w..32w+31).  TF32 keeps 10 mantissa bits of each
+// operand; the products accumulate in FP32.
 #include "slqr_internal.cuh"
 
 #include <cuda.h>   // CUtensorMap and its enums (types only: the encoder is fetched at run time)
@@ -41,119 +37,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                    // descriptor version
   d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
   return d;
-}
-
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = N = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) |
-                                ((uint32_t)(kTcTile >> 3) << 17) |
-                                ((uint32_t)(kTcTile >> 4) << 24);
-
-// byte offset of element (row, k) of a K-major SW128 operand tile of 128 rows
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-  const int kb = k >> 5, kk = k & 31;
-  return (uint32_t)(kb * (kTcTile * 128) + (row >> 3) * 1024 + (row & 7) * 128 +
-                    ((((kk >> 2) ^ (row & 7)) & 7) << 4) + (kk & 3) * 4);
-}
-
-template <int NB>
-__global__ void __launch_bounds__(kTcThreads)
-upd_tc_kernel(const float *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
-              int nbw, int M, float *__restrict__ X, int ldx, int N,
-              const float *__restrict__ Wt, int *status) {
-  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-  // 1024-byte aligned operand tiles
-  unsigned char *base = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = base;
-  unsigned char *sB = base + kTcTile * NB * 4;
-  __shared__ uint32_t s_taddr;
-  __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ int s_done;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i0 = blockIdx.x * kTcTile, c0 = blockIdx.y * kTcTile;
-
-  // stage A = V rows [i0, i0+128) and B = W'^T columns [c0, c0+128)
-  for (int idx = tid; idx < kTcTile * NB; idx += kTcThreads) {
-    const int r = idx & (kTcTile - 1), a = idx >> 7;
-    const int i = i0 + r;
-    float v = 0.f;
-    if (i < M && a < nbw) v = (i < nbw) ? (float)Vtop[i + a * NB] : A[SLQR_IDX(k0 + i, k0 + a, lda)];
-    *(float *)(sA + sw128_offset(r, a)) = v;
-    const int c = c0 + r;
-    float w = 0.f;
-    if (c < N && a < nbw) w = Wt[(size_t)a * N + c];
-    *(float *)(sB + sw128_offset(r, a)) = w;
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&s_taddr)), "r"(kTcTile));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  // the generic-proxy smem writes must be visible to the tensor core
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = s_taddr;
-
-  if (tid == 0) {
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-#pragma unroll
-    for (int s = 0; s < NB / 8; ++s) {
-      const uint32_t koff = (uint32_t)((s >> 2) * (kTcTile * 128) + (s & 3) * 32);
-      const uint64_t ad = sw128_desc(a0 + koff), bd = sw128_desc(b0 + koff);
-      const uint32_t accum = (s > 0) ? 1u : 0u;
-      asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                   " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                   :: "r"(taddr), "l"(ad), "l"(bd), "r"(kIdescTf32), "r"(accum) : "memory");
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(smem_u32(&s_mbar)) : "memory");
-  }
-  // bounded wait for the MMAs
-  if (tid == 0) {
-    uint32_t done = 0;
-    for (unsigned it = 0; it < kSpinLimit && !done; ++it) {
-      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                   " selp.b32 %0, 1, 0, p;\n}"
-                   : "=r"(done) : "r"(smem_u32(&s_mbar)), "r"(0) : "memory");
-      if (!done && it > 64) __nanosleep(32);
-    }
-    s_done = (int)done;
-    if (!done) atomicCAS(status, 0, SLQR_ETIMEOUT);
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (s_done) {
-    const int row = warp * 32 + lane;
-    const int i = i0 + row;
-#pragma unroll 1
-    for (int cc = 0; cc < kTcTile; cc += 16) {
-      uint32_t r[16];
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                   "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                     "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                     "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                   : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (i < M) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int c = c0 + cc + q;
-          if (c < N) X[SLQR_IDX(k0 + i, c, ldx)] -= __uint_as_float(r[q]);
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                 :: "r"(taddr), "r"(kTcTile));
 }
 
 // --------------------------------------------------------------------------
@@ -310,6 +193,141 @@ vtx_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ 
 
 constexpr size_t kVxSmem = (size_t)kVxStages * (kVxBytesA + kVxBytesB) + 1024;
 
+// --------------------------------------------------------------------------
+// X -= V W' on the tensor cores, one 128 x 64 tile of X per CTA:
+// D[i][c] = sum_a V[i][a] W'[a][c] with M = 128 rows, N = 64 columns and
+// K = 64 reflectors.  The MMA wants both operands K-major (the 64 reflector
+// values of a row of V, or of a column of W', contiguous), so V is first
+// copied row-major (vrow_kernel) and the forward substitution writes W' as
+// [column][reflector].  One elected thread loads the two K-halves of each
+// operand (128-byte swizzle) and the X tile (no swizzle, [column][row]) on one
+// mbarrier, issues 8 MMAs of K = 8, and the four warps subtract the
+// accumulator from the X tile in shared memory, which one TMA store writes
+// back (rows beyond the matrix are clipped by the tensor map).
+// --------------------------------------------------------------------------
+constexpr int kUpN = 64;                              // columns of X per CTA
+constexpr int kUpBytesA = kTcTile * 64 * 4;           // V tile: 32 KB
+constexpr int kUpBytesB = kUpN * 64 * 4;              // W' tile: 16 KB
+constexpr int kUpBytesX = kTcTile * kUpN * 4;         // X tile: 32 KB
+constexpr size_t kUpSmem = (size_t)kUpBytesA + kUpBytesB + kUpBytesX + 1024;
+
+// Vr[i][a] = V(i, a) of the panel at row offset k0 (64 floats per row): rows
+// i < 64 from Vtop (up on the diagonal, zeros above), the rest the reflector
+// tails in A.  32 rows per CTA, transposed through shared memory.
+__global__ void __launch_bounds__(256)
+vrow_kernel(const float *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0, int M,
+            float *__restrict__ Vr) {
+  __shared__ float t[64][33];
+  const int tid = threadIdx.x, i0 = blockIdx.x * 32;
+  const int r = tid & 31;
+  for (int a = tid >> 5; a < 64; a += 8) {
+    const int i = i0 + r;
+    float v = 0.f;
+    if (i < M) v = (i < 64) ? (float)Vtop[i + a * 64] : A[SLQR_IDX(k0 + i, k0 + a, lda)];
+    t[a][r] = v;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 32 * 64; idx += 256) {
+    const int rr = idx >> 6, a = idx & 63;
+    if (i0 + rr < M) Vr[(size_t)(i0 + rr) * 64 + a] = t[a][rr];
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads)
+upd_tc_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapW,
+              const __grid_constant__ CUtensorMap mapX, int k0, int xcol0, int *status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = base;
+  unsigned char *sB = base + kUpBytesA;
+  float *sX = (float *)(base + kUpBytesA + kUpBytesB);
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_full, s_mma;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * kTcTile, c0 = blockIdx.y * kUpN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&s_taddr)), "r"(kUpN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mma)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = s_taddr;
+
+  if (tid == 0) {
+    const uint32_t full = smem_u32(&s_full);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(full), "r"(kUpBytesA + kUpBytesB + kUpBytesX) : "memory");
+    tma_load_2d(smem_u32(sA), &mapV, 0, i0, full);
+    tma_load_2d(smem_u32(sA + kUpBytesA / 2), &mapV, 32, i0, full);
+    tma_load_2d(smem_u32(sB), &mapW, 0, c0, full);
+    tma_load_2d(smem_u32(sB + kUpBytesB / 2), &mapW, 32, c0, full);
+    tma_load_2d(smem_u32(sX), &mapX, k0 + i0, xcol0 + c0, full);
+    bool ok = mbar_wait(full, 0);
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint64_t ad = sw128_desc(a0 + (k >> 2) * (kUpBytesA / 2) + (k & 3) * 32);
+        const uint64_t bd = sw128_desc(b0 + (k >> 2) * (kUpBytesB / 2) + (k & 3) * 32);
+        const uint32_t accum = (k > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                     :: "r"(taddr), "l"(ad), "l"(bd), "r"(kIdescTf32N64), "r"(accum) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&s_mma)) : "memory");
+      ok = mbar_wait(smem_u32(&s_mma), 0);
+    } else {
+      mbar_wait(full, 0);                 // let the copies in flight land before leaving
+    }
+    if (!ok) atomicCAS(status, 0, SLQR_ETIMEOUT);
+    s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool ok = s_ok != 0;
+  if (ok) {
+    const int row = warp * 32 + lane;                 // TMEM lane = row of the tile
+#pragma unroll 1
+    for (int cc = 0; cc < kUpN; cc += 16) {
+      uint32_t r[16];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                   "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                     "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                     "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                   : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sX[(cc + q) * kTcTile + row] -= __uint_as_float(r[q]);
+    }
+    // the generic-proxy writes must be visible to the TMA store
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0 && ok) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 :: "l"((uint64_t)&mapX), "r"(k0 + i0), "r"(xcol0 + c0), "r"(smem_u32(sX))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kUpN));
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -330,18 +348,19 @@ static EncodeTiledFn tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map of a column-major FP32 matrix (rows contiguous), 128-byte swizzle,
-// zero fill outside the matrix.
-static bool make_map(CUtensorMap *map, const float *base, int rows, int cols, int ld, int box_rows,
-                     int box_cols) {
+// 2-D map of an FP32 matrix whose dim0 is contiguous (a column-major matrix:
+// dim0 = rows; a row-major one: dim0 = columns), zero fill outside it.
+static bool make_map(CUtensorMap *map, const float *base, int dim0, int dim1, int ld, int box0,
+                     int box1, bool swizzle = true) {
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  const cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -372,17 +391,9 @@ int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, in
   return S + 1;
 }
 
-template <int NB>
-static size_t upd_tc_smem() {
-  return (size_t)2 * kTcTile * NB * 4 + 1024;
-}
-
 slqr_status init_tc_attrs(slqr_ctx *ctx) {
-  cudaError_t e = cudaFuncSetAttribute(upd_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)upd_tc_smem<64>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(upd_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)upd_tc_smem<32>());
+  cudaError_t e = cudaFuncSetAttribute(upd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kUpSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(vtx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kVxSmem);
@@ -391,15 +402,23 @@ slqr_status init_tc_attrs(slqr_ctx *ctx) {
   return SLQR_OK;
 }
 
-void launch_upd_tc(int nb, const float *A, int lda, const double *Vtop, int k0, int nbw, int M,
-                   float *X, int ldx, int N, const float *Wt, int *status, cudaStream_t stream) {
-  dim3 grid((M + kTcTile - 1) / kTcTile, (N + kTcTile - 1) / kTcTile);
-  if (nb == 32)
-    upd_tc_kernel<32><<<grid, kTcThreads, upd_tc_smem<32>(), stream>>>(A, lda, Vtop, k0, nbw, M, X,
-                                                                       ldx, N, Wt, status);
-  else
-    upd_tc_kernel<64><<<grid, kTcThreads, upd_tc_smem<64>(), stream>>>(A, lda, Vtop, k0, nbw, M, X,
-                                                                       ldx, N, Wt, status);
+// X -= V W' for a full 64-reflector panel: V in row-major form (Vr), then the
+// tensor-core tiles.  Returns false (nothing launched) when a tensor map
+// cannot be encoded.
+bool launch_upd_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,
+                   const float *Wt, float *Vr, int *status, cudaStream_t stream) {
+  if (lda % 4 != 0 || ((uintptr_t)A & 15) != 0 || ((uintptr_t)Wt & 15) != 0 ||
+      ((uintptr_t)Vr & 15) != 0 || M <= 0 || N <= 0)
+    return false;
+  CUtensorMap mapV, mapW, mapX;
+  if (!make_map(&mapV, Vr, 64, M, 64, 32, kTcTile) ||
+      !make_map(&mapW, Wt, 64, N, 64, 32, kUpN) ||
+      !make_map(&mapX, A, k0 + M, xcol0 + N, lda, kTcTile, kUpN, false))
+    return false;
+  vrow_kernel<<<(M + 31) / 32, 256, 0, stream>>>(A, lda, Vtop, k0, M, Vr);
+  dim3 grid((M + kTcTile - 1) / kTcTile, (N + kUpN - 1) / kUpN);
+  upd_tc_kernel<<<grid, kTcThreads, kUpSmem, stream>>>(mapV, mapW, mapX, k0, xcol0, status);
+  return true;
 }
 
 }  // namespace slqr
