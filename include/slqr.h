@@ -162,6 +162,36 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
                          double *B, int ldb, void *stream);
 
 /*
+ * Structure-aware factorization of a stacked SLSQP least-squares matrix
+ * A = [L^T; C]: an n x n upper-triangular block on top of an m_eq x n block C
+ * (m = n + m_eq rows).  In Alg. 2 the reflector of column k is then zero in
+ * rows k+1 .. n-1, and no reflector changes those rows of any column, so each
+ * panel works on its own diagonal rows and the rows of C only: about
+ * 2 m_eq n^2 flops instead of 2 m n^2 - 2 n^3 / 3.  The result is the H12
+ * factorization slqr_factor computes for the same A (in exact arithmetic the
+ * same reflectors; rounding differs only by the order of the sums), so
+ * slqr_apply_qt, slqr_apply_qt_stacked and slqr_solve_r apply to it.
+ *   n, m_eq  n >= 0, m_eq >= 0, n + m_eq <= slqr_max_rows()
+ *   A      device, (n + m_eq) x n column-major, lda >= n + m_eq; the strictly
+ *          lower part of the top n x n block must be zero: it is neither read
+ *          nor written (it is the zero part of the reflector tails)
+ *   up, wy as for slqr_factor with m = n + m_eq
+ * Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA.
+ */
+slqr_status slqr_factor_stacked(slqr_ctx *ctx, int n, int m_eq, double *A, int lda,
+                                double *up, double *wy, void *stream);
+
+/*
+ * B <- Q^T B for a factorization made by slqr_factor_stacked, skipping the
+ * rows where the reflectors are zero (4 (m_eq + 1) n flops per right-hand side
+ * instead of 4 m n - 2 n^2).  Arguments as for slqr_apply_qt with
+ * m = n + m_eq; B is (n + m_eq) x nrhs, ldb >= n + m_eq.
+ */
+slqr_status slqr_apply_qt_stacked(slqr_ctx *ctx, int n, int m_eq, const double *A, int lda,
+                                  const double *up, const double *wy, int nrhs, double *B,
+                                  int ldb, void *stream);
+
+/*
  * slqr_batch_factor -- `count` independent least-squares problems in one
  * persistent launch.  Each problem is the factorization of slqr_factor
  * (Alg. 2, Task 1 skip rule) and, when its b is given, Q^T b and the
@@ -198,14 +228,29 @@ slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrh
  */
 #define SLQR_FP64 0   /* FP64 throughout (DFMA)                                   */
 #define SLQR_FP32 1   /* FP32 factorization + FP64-residual refinement            */
-#define SLQR_TF32 2   /* as SLQR_FP32, the rank-NB trailing update on the tensor
-                         cores (tcgen05, TF32 operands, FP32 accumulation)
+#define SLQR_TF32 2   /* as SLQR_FP32, the two products of the rank-NB trailing
+                         update (W = V^T X and X -= V W') on the tensor cores
+                         (tcgen05, TF32 operands, FP32 accumulation)
                          (slqr_lstsq_mixed only)                                  */
 slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
                               double *const *A, const int *lda, double *const *up,
                               double *const *b, int prec, int *status, double *err,
                               void *stream);
 int slqr_batch_max_rows(void);
+
+/*
+ * slqr_batch_factor for stacked SLSQP matrices A_i = [L_i^T; C_i]: problem i
+ * is (n[i] + m_eq[i]) x n[i] with an upper-triangular top n[i] x n[i] block,
+ * factored with the structure of slqr_factor_stacked.  The strictly lower part
+ * of the top block must be zero; SLQR_FP64 neither reads nor writes it
+ * (SLQR_FP32 reads all of A for its FP64 residuals).  Other arguments and
+ * outputs as for slqr_batch_factor with m[i] = n[i] + m_eq[i] <=
+ * slqr_batch_max_rows().
+ */
+slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const int *n, const int *m_eq,
+                                      double *const *A, const int *lda, double *const *up,
+                                      double *const *b, int prec, int *status, double *err,
+                                      void *stream);
 
 /*
  * slqr_lstsq_mixed -- least squares min ||A x - b|| for one large problem in
@@ -218,8 +263,8 @@ int slqr_batch_max_rows(void);
  *   A      device, m x n column-major FP64, lda >= m, m >= n >= 1 (read only)
  *   b      device, m doubles (read only);  x  device, n doubles (output)
  *   prec   SLQR_FP32 (trailing-update products on the FP32 FMA pipe) or
- *          SLQR_TF32 (the X -= V W' products on the tensor cores, TF32
- *          operands: refinement then converges for kappa * 2^-11 < 1)
+ *          SLQR_TF32 (W = V^T X and X -= V W' on the tensor cores, TF32
+ *          operands: refinement then converges for kappa well below 2^11)
  *   max_iter  refinement sweeps (<= 0: 30);  tol  stop at ||dx||_inf <=
  *          tol ||x||_inf (<= 0: 1e-14)
  *   iters, err  HOST ints/doubles or NULL: sweeps done and the last
@@ -278,7 +323,13 @@ typedef struct {
   double *x;            /* host, n doubles, written at completion */
   uint64_t handle;      /* SOLVE, RELEASE */
   int prec;             /* SLQR_FP64 or SLQR_FP32 */
+  int structure;        /* SLQR_DENSE, or SLQR_STACKED: A = [L^T; C] with an
+                           upper-triangular top n x n block whose strictly lower
+                           part is zero (factored as slqr_factor_stacked) */
 } slqr_request;
+
+#define SLQR_DENSE   0
+#define SLQR_STACKED 1
 
 typedef struct {
   int status;           /* SLQR_OK, SLQR_ERANK, SLQR_ENOCONV, SLQR_EBUSY, SLQR_ENOTFOUND, ... */

@@ -42,7 +42,8 @@ SLQR_REQ_FACTOR, SLQR_REQ_SOLVE, SLQR_REQ_FACTOR_SOLVE, SLQR_REQ_RELEASE = 1, 2,
 class SlqrRequest(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
                 ("lda", ctypes.c_int), ("A", ctypes.c_void_p), ("b", ctypes.c_void_p),
-                ("x", ctypes.c_void_p), ("handle", ctypes.c_uint64), ("prec", ctypes.c_int)]
+                ("x", ctypes.c_void_p), ("handle", ctypes.c_uint64), ("prec", ctypes.c_int),
+                ("structure", ctypes.c_int)]
 
 
 class SlqrResult(ctypes.Structure):
@@ -65,6 +66,9 @@ SIGNATURES = [
     ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     ("slqr_apply_qt", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _vp, _c_int, _vp]),
     ("slqr_solve_r", _c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int, _vp]),
+    ("slqr_factor_stacked", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    ("slqr_apply_qt_stacked", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _vp,
+                                       _c_int, _vp]),
     ("slqr_profile", _c_int, [_vp, _c_int]),
     ("slqr_profile_read", _c_int, [_vp, _c_int, ctypes.POINTER(_dbl),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_dbl)]),
@@ -75,6 +79,10 @@ SIGNATURES = [
                                    ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, _vp, _vp,
                                    _vp]),
     ("slqr_batch_max_rows", _c_int, []),
+    ("slqr_batch_factor_stacked", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int),
+                                           ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_vp), _c_int, _vp, _vp, _vp]),
     ("slqr_submit", _c_int, [_vp, ctypes.POINTER(SlqrRequest), ctypes.POINTER(ctypes.c_uint64)]),
     ("slqr_poll", _c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(SlqrResult)]),
     ("slqr_server_bytes_in_use", _c_size, [_vp]),
@@ -90,6 +98,8 @@ KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm", "batch"]
 SLQR_FP64 = 0
 SLQR_FP32 = 1
 SLQR_TF32 = 2
+SLQR_DENSE = 0
+SLQR_STACKED = 1
 
 
 def _load() -> ctypes.CDLL:
@@ -162,6 +172,14 @@ def slqr_solve_r(ctx, n, A, lda, nrhs, B, ldb, stream) -> int:
     return _lib.slqr_solve_r(ctx, n, A, lda, nrhs, B, ldb, stream)
 
 
+def slqr_factor_stacked(ctx, n, m_eq, A, lda, up, wy, stream) -> int:
+    return _lib.slqr_factor_stacked(ctx, n, m_eq, A, lda, up, wy, stream)
+
+
+def slqr_apply_qt_stacked(ctx, n, m_eq, A, lda, up, wy, nrhs, B, ldb, stream) -> int:
+    return _lib.slqr_apply_qt_stacked(ctx, n, m_eq, A, lda, up, wy, nrhs, B, ldb, stream)
+
+
 def slqr_profile(ctx: int, enable: bool) -> int:
     return _lib.slqr_profile(ctx, 1 if enable else 0)
 
@@ -198,6 +216,16 @@ def slqr_batch_factor(ctx, m_list, n_list, A_ptrs, lda_list, up_ptrs, b_ptrs, pr
 
 def slqr_batch_max_rows() -> int:
     return _lib.slqr_batch_max_rows()
+
+
+def slqr_batch_factor_stacked(ctx, n_list, meq_list, A_ptrs, lda_list, up_ptrs, b_ptrs, prec,
+                              status, err, stream) -> int:
+    """As slqr_batch_factor for stacked [L^T; C] problems of n + m_eq rows."""
+    count = len(n_list)
+    return _lib.slqr_batch_factor_stacked(
+        ctx, count, _int_array(n_list), _int_array(meq_list), _ptr_array(A_ptrs),
+        _int_array(lda_list), _ptr_array(up_ptrs) if up_ptrs is not None else None,
+        _ptr_array(b_ptrs) if b_ptrs is not None else None, prec, status, err, stream)
 
 
 def slqr_submit(ctx, req: SlqrRequest):

@@ -78,6 +78,31 @@ class Context:
         abi.check(self.ctx, st, "slqr_factor")
         return A, up, wy
 
+    def factor_stacked(self, A: torch.Tensor, up: torch.Tensor | None = None,
+                       wy: torch.Tensor | None = None, stream=None):
+        """Structure-aware H12 QR of A = [L^T; C] ((n + m_eq) x n, column-major,
+        upper-triangular top n x n block).  Returns (A, up, wy)."""
+        _check(A, "A")
+        m, n = A.shape
+        if up is None:
+            up = torch.empty(n, dtype=torch.float64, device=A.device)
+        st = abi.slqr_factor_stacked(self.ctx, n, m - n, A.data_ptr(), _ld(A), up.data_ptr(),
+                                     wy.data_ptr() if wy is not None else None, _stream(stream))
+        abi.check(self.ctx, st, "slqr_factor_stacked")
+        return A, up, wy
+
+    def apply_qt_stacked(self, A: torch.Tensor, up: torch.Tensor, B: torch.Tensor,
+                         wy: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """B <- Q^T B for a factorization made by factor_stacked."""
+        _check(A, "A"); _check(B, "B")
+        m, n = A.shape
+        nrhs = 1 if B.dim() == 1 else B.shape[1]
+        st = abi.slqr_apply_qt_stacked(self.ctx, n, m - n, A.data_ptr(), _ld(A), up.data_ptr(),
+                                       wy.data_ptr() if wy is not None else None, nrhs,
+                                       B.data_ptr(), _ld(B), _stream(stream))
+        abi.check(self.ctx, st, "slqr_apply_qt_stacked")
+        return B
+
     def wy_buffer(self, m: int, n: int, device=None) -> torch.Tensor:
         """Device buffer for the compact-WY store of an m x n factorization."""
         nbytes = abi.slqr_wy_size(m, n)
@@ -131,7 +156,8 @@ class Server:
         self.ctx = ctx
         self._live = {}
 
-    def submit(self, kind, A=None, b=None, handle=0, prec=abi.SLQR_FP64, m=None, n=None):
+    def submit(self, kind, A=None, b=None, handle=0, prec=abi.SLQR_FP64, m=None, n=None,
+               structure=abi.SLQR_DENSE):
         import numpy as np
         req = abi.SlqrRequest()
         req.kind = kind
@@ -154,6 +180,7 @@ class Server:
             x = None
         req.handle = handle
         req.prec = prec
+        req.structure = structure
         st, t = abi.slqr_submit(self.ctx.ctx, req)
         abi.check(self.ctx.ctx, st, "slqr_submit")
         self._live[t] = (keep, x)

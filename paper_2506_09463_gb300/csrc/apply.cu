@@ -120,10 +120,13 @@ __global__ void gram_reduce_kernel(const double *__restrict__ Gp, int S, int K,
   }
 }
 
+// ntop > 0: A holds the factorization of a stacked [L^T; C] (upper-triangular
+// top block of ntop = n rows), whose reflectors are zero between each panel's
+// diagonal block and C: those rows are skipped.
 template <int NB>
 static slqr_status apply_qt_impl(slqr_ctx *ctx, int m, int n, const double *A, int lda,
                                  const double *up, const double *wy, int nrhs, double *B,
-                                 int ldb, cudaStream_t stream) {
+                                 int ldb, cudaStream_t stream, int ntop = 0) {
   const int K = num_reflectors(m, n);
   const int np = num_panels(K, NB);
   if (np == 0) return SLQR_OK;
@@ -157,8 +160,9 @@ static slqr_status apply_qt_impl(slqr_ctx *ctx, int m, int n, const double *A, i
   for (int pnl = 0; pnl < np; ++pnl) {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
+    const int skip = ntop > 0 ? ntop - (k0 + nbw) : 0;
     st = apply_panel_update(ctx, m, k0, nbw, NB, A, lda, wys + (size_t)pnl * wy_panel_doubles(NB),
-                            B, ldb, nrhs, work, work_doubles, stream);
+                            B, ldb, nrhs, work, work_doubles, stream, skip);
     if (st != SLQR_OK) return st;
   }
   return SLQR_OK;
@@ -184,4 +188,24 @@ extern "C" slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *
   cudaStream_t s = (cudaStream_t)stream;
   if (panel_width(m, n) == 32) return apply_qt_impl<32>(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, s);
   return apply_qt_impl<64>(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, s);
+}
+
+extern "C" slqr_status slqr_apply_qt_stacked(slqr_ctx *ctx, int n, int m_eq, const double *A,
+                                             int lda, const double *up, const double *wy,
+                                             int nrhs, double *B, int ldb, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);
+  if (nrhs < 0) return fail(ctx, SLQR_EINVAL, "nrhs=%d < 0", nrhs);
+  const int m = n + m_eq;
+  if (n == 0 || nrhs == 0) return SLQR_OK;
+  if (lda < m) return fail(ctx, SLQR_EINVAL, "lda=%d < n + m_eq=%d", lda, m);
+  if (ldb < m) return fail(ctx, SLQR_EINVAL, "ldb=%d < n + m_eq=%d", ldb, m);
+  if (!A || !up || !B) return fail(ctx, SLQR_EINVAL, "NULL A, up or B");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (panel_width(m, n) == 32)
+    return apply_qt_impl<32>(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, s, n);
+  return apply_qt_impl<64>(ctx, m, n, A, lda, up, wy, nrhs, B, ldb, s, n);
 }

@@ -39,7 +39,8 @@ struct BatchProblem {
   double *A;
   double *up;
   double *b;
-  int m, n, lda, pad;
+  int m, n, lda;
+  int ntop;          // > 0: stacked [L^T; C] with an upper-triangular top block of ntop rows
 };
 
 struct BatchParams {
@@ -98,9 +99,15 @@ struct BatchSmem {
 // striu(V^T V) and tau are kept there (the mixed path reuses them to apply Q).
 // Bcol (T == double only) is an extra right-hand-side column updated with the
 // trailing columns, giving Q^T b.
+//
+// ntop > 0: A = [L^T; C] with an upper-triangular top block of ntop rows.  A
+// panel at k0 then uses its own nbw diagonal rows and the rows of C only (row
+// r of the panel is matrix row k0 + r for r < nbw, k0 + skip + r below, with
+// skip = ntop - k0 - nbw): the rows between are zero in every reflector and
+// untouched by the update.
 template <typename T>
 __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, double *Bcol,
-                                  double *G_out, double *tau_out, char *smraw) {
+                                  double *G_out, double *tau_out, char *smraw, int ntop) {
   using SM = BatchSmem<T>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T *Ps = (T *)smraw;
@@ -116,10 +123,15 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
 
   for (int k0 = 0; k0 < K; k0 += kBNB) {
     const int nbw = min(kBNB, K - k0);
-    const int M = m - k0;
+    const int skip = ntop > 0 ? ntop - k0 - nbw : 0;
+    const int M = m - k0 - skip;
+    // matrix row (relative to k0) of panel row r
+    auto prow = [&](int r) { return r + (r >= nbw ? skip : 0); };
+    // (stacked: the strictly lower part of the diagonal block is zero, not read)
     for (int idx = tid; idx < kBNB * M; idx += kThreads) {
       int c = idx / M, r = idx - c * M;
-      Ps[c * kBMaxRows + r] = (c < nbw) ? A[SLQR_IDX(k0 + r, k0 + c, lda)] : T(0);
+      const bool zero = c >= nbw || (ntop > 0 && r < nbw && r > c);
+      Ps[c * kBMaxRows + r] = zero ? T(0) : A[SLQR_IDX(k0 + prow(r), k0 + c, lda)];
     }
     __syncthreads();
     for (int j = 0; j < nbw; ++j) {
@@ -192,7 +204,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     // V (zero above the diagonal, up on it) for the trailing update
     for (int idx = tid; idx < nbw * M; idx += kThreads) {
       int c = idx / M, r = idx - c * M;
-      A[SLQR_IDX(k0 + r, k0 + c, lda)] = Ps[c * kBMaxRows + r];
+      if (!(ntop > 0 && r < nbw && r > c)) A[SLQR_IDX(k0 + prow(r), k0 + c, lda)] = Ps[c * kBMaxRows + r];
     }
     if (tid < nbw) up_out[k0 + tid] = ups[tid];
     if (G_out) {
@@ -223,7 +235,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
 #pragma unroll
         for (int a = 0; a < kBNB; ++a) acc[a] = T(0);
         for (int r = lane; r < M; r += 32) {
-          const T cv = C[r];
+          const T cv = C[prow(r)];
 #pragma unroll
           for (int a = 0; a < kBNB; ++a)
             if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
@@ -261,11 +273,12 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
 #pragma unroll
         for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
         for (int r = lane; r < M; r += 32) {
-          T cv = C[r];
+          const int pr = prow(r);
+          T cv = C[pr];
 #pragma unroll
           for (int a = 0; a < kBNB; ++a)
             if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
-          C[r] = cv;
+          C[pr] = cv;
         }
       }
       __syncthreads();
@@ -310,7 +323,8 @@ batch_factor_fp64_kernel(BatchParams bp) {
     const int p = bp.order[item];
     const BatchProblem pr = bp.probs[p];
     if (pr.n > 0) {
-      batch_factor_core<double>(pr.A, pr.lda, pr.m, pr.n, pr.up, pr.b, nullptr, nullptr, smraw);
+      batch_factor_core<double>(pr.A, pr.lda, pr.m, pr.n, pr.up, pr.b, nullptr, nullptr, smraw,
+                                pr.ntop);
       if (pr.b) {
         batch_solve_fp64(pr.A, pr.lda, pr.n, pr.b, (double *)smraw, &s_status);
       } else if (threadIdx.x == 0) {
@@ -475,7 +489,7 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
       Af[idx] = (float)pr.A[SLQR_IDX(r, c, pr.lda)];
     }
     __syncthreads();
-    batch_factor_core<float>(Af, m, m, n, up, nullptr, G, tau, smraw);
+    batch_factor_core<float>(Af, m, m, n, up, nullptr, G, tau, smraw, pr.ntop);
     __syncthreads();
     // refinement vectors in shared memory (the panel area is free now)
     double *x = (double *)smraw;          // n
@@ -565,12 +579,14 @@ using namespace slqr;
 
 extern "C" int slqr_batch_max_rows(void) { return kBMaxRows; }
 
-extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
-                                         double *const *A, const int *lda, double *const *up,
-                                         double *const *b, int prec, int *status, double *err,
-                                         void *stream) {
-  if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+namespace slqr {
+
+// The launch behind slqr_batch_factor and slqr_batch_factor_stacked (ntop:
+// NULL, or per problem the rows of its upper-triangular top block, 0 for a
+// dense problem).  The context mutex is held by the caller.
+slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, const int *ntop,
+                         double *const *A, const int *lda, double *const *up, double *const *b,
+                         int prec, int *status, double *err, void *stream) {
   if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
   if (count == 0) return SLQR_OK;
   if (!m || !n || !A || !lda) return fail(ctx, SLQR_EINVAL, "NULL size or pointer array");
@@ -587,8 +603,12 @@ extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m,
     if (n[i] > 0 && (lda[i] < std::max(1, m[i]) || !A[i] ||
                      (prec == SLQR_FP64 && !up[i]) || (prec == SLQR_FP32 && !b[i])))
       return fail(ctx, SLQR_EINVAL, "problem %d: bad lda or NULL pointer", i);
-    probs[i] = BatchProblem{A[i], up ? up[i] : nullptr, b ? b[i] : nullptr, m[i], n[i], lda[i], 0};
-    cost[i] = 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0 +
+    const int nt = ntop ? ntop[i] : 0;
+    probs[i] = BatchProblem{A[i], up ? up[i] : nullptr, b ? b[i] : nullptr, m[i], n[i], lda[i], nt};
+    // flops of the factorization as this launch performs it (the stacked form
+    // touches the m - n rows of C and one diagonal row per reflector)
+    cost[i] = (nt > 0 ? 2.0 * (m[i] - n[i] + 1) * (double)n[i] * n[i]
+                      : 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0) +
               (b && b[i] ? 6.0 * m[i] * (double)n[i] : 0.0);
   }
   std::vector<int> order(count);
@@ -642,4 +662,43 @@ extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m,
   }
   prof_end(ctx, s, slot, kBatch, flops);
   return check_launch(ctx, "batch_factor");
+}
+
+slqr_status batch_factor_locked(slqr_ctx *ctx, int count, const int *m, const int *n,
+                                const int *ntop, double *const *A, const int *lda,
+                                double *const *up, double *const *b, int prec, int *status,
+                                double *err, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return batch_launch(ctx, count, m, n, ntop, A, lda, up, b, prec, status, err, stream);
+}
+
+}  // namespace slqr
+
+extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
+                                         double *const *A, const int *lda, double *const *up,
+                                         double *const *b, int prec, int *status, double *err,
+                                         void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return batch_launch(ctx, count, m, n, nullptr, A, lda, up, b, prec, status, err, stream);
+}
+
+extern "C" slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const int *n,
+                                                 const int *m_eq, double *const *A,
+                                                 const int *lda, double *const *up,
+                                                 double *const *b, int prec, int *status,
+                                                 double *err, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
+  if (count > 0 && (!n || !m_eq)) return fail(ctx, SLQR_EINVAL, "NULL size array");
+  std::vector<int> m(std::max(count, 0));
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 0 || m_eq[i] < 0)
+      return fail(ctx, SLQR_EINVAL, "problem %d: need n, m_eq >= 0 (n=%d m_eq=%d)", i, n[i],
+                  m_eq[i]);
+    m[i] = n[i] + m_eq[i];
+  }
+  return batch_launch(ctx, count, m.data(), n, n, A, lda, up, b, prec, status, err, stream);
 }

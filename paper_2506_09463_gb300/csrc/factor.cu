@@ -74,9 +74,20 @@ struct PanelParams {
   unsigned *bar;       // monotonic arrival counter
   int *status;
   int m, lda, k0, nbw;
+  int skip;            // rows skipped after the panel's top nbw rows (stacked [L^T; C])
+  int stacked;         // stacked [L^T; C]: the diagonal block's strict lower part is zero
   int P, R;            // CTAs, rows per CTA
   unsigned bar_base;   // counter value when this panel starts
 };
+
+// Row map of a panel: row i of the panel (0 <= i < m - k0 - skip) is matrix
+// row k0 + i for i < nbw and k0 + skip + i below.  skip = 0 for a dense
+// matrix; for a stacked [L^T; C] (upper-triangular top block of n rows) the
+// rows between the panel's diagonal block and C are zero in every reflector
+// and untouched by the update, so they are left out.
+__host__ __device__ __forceinline__ int panel_row(int k0, int nbw, int skip, int i) {
+  return k0 + i + (i >= nbw ? skip : 0);
+}
 
 // Arrive at the grid barrier and wait (bounded) until `target` arrivals.
 // Returns false after recording SLQR_ETIMEOUT.
@@ -167,15 +178,18 @@ panel_kernel(PanelParams p) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cta = blockIdx.x;
   const int R = p.R;
-  const int row0 = p.k0 + cta * R;                 // first global row of this slice
-  const int RO = min(R, p.m - row0);               // rows owned
+  const int row0 = cta * R;                        // first panel row of this slice
+  const int RO = min(R, p.m - p.k0 - p.skip - row0);   // rows owned
   const int nbw = p.nbw;
   T *A = (T *)p.A;
   const int lda = p.lda;
 
   for (int idx = tid; idx < nbw * R; idx += kThreads) {
     int c = idx / R, r = idx - c * R;
-    Ps[c * R + r] = (r < RO) ? A[SLQR_IDX(row0 + r, p.k0 + c, lda)] : T(0);
+    // (stacked: the strictly lower part of the diagonal block is zero, not read)
+    const bool zero = r >= RO || (p.stacked && row0 + r < nbw && row0 + r > c);
+    Ps[c * R + r] =
+        zero ? T(0) : A[SLQR_IDX(panel_row(p.k0, nbw, p.skip, row0 + r), p.k0 + c, lda)];
   }
   for (int idx = tid; idx < NB * NB; idx += kThreads) Gloc[idx] = 0.0;
   double *G = p.wy + (size_t)NB * NB;
@@ -372,7 +386,8 @@ panel_kernel(PanelParams p) {
   // write the slice back
   for (int idx = tid; idx < nbw * R; idx += kThreads) {
     int c = idx / R, r = idx - c * R;
-    if (r < RO) A[SLQR_IDX(row0 + r, p.k0 + c, lda)] = Ps[c * R + r];
+    if (r < RO && !(p.stacked && row0 + r < nbw && row0 + r > c))
+      A[SLQR_IDX(panel_row(p.k0, nbw, p.skip, row0 + r), p.k0 + c, lda)] = Ps[c * R + r];
   }
   // publish the local Gram terms and reduce them: CTA q owns entries q, q+P, ..
   constexpr int NT = NB * (NB - 1) / 2;       // strict upper triangle, packed by column
@@ -418,10 +433,10 @@ panel_kernel(PanelParams p) {
 // straight from the reflector tails in A.  Columns a >= nbw read as 0.
 template <typename T>
 __device__ __forceinline__ T v_at(const T *A, int lda, const double *Vtop, int NB, int k0,
-                                  int nbw, int i, int a) {
+                                  int nbw, int i, int a, int skip) {
   if (a >= nbw) return T(0);
   if (i < nbw) return (T)Vtop[i + a * NB];
-  return A[SLQR_IDX(k0 + i, k0 + a, lda)];
+  return A[SLQR_IDX(k0 + skip + i, k0 + a, lda)];
 }
 
 constexpr int kBK = 32;   // rows per chunk of the V^T X reduction
@@ -434,7 +449,7 @@ template <typename T, int NB, bool X_IS_V>
 __global__ void __launch_bounds__(kThreads)
 gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
                 int nbw, int M, const T *__restrict__ X, int ldx, int N, int RS,
-                T *__restrict__ Wp) {
+                T *__restrict__ Wp, int skip = 0) {
   __shared__ T Vs[NB][kBK + 1];
   __shared__ T Xs[kBN][kBK + 1];
   constexpr int TP = NB / 16;
@@ -452,15 +467,15 @@ gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
     for (int idx = tid; idx < NB * kBK; idx += kThreads) {
       int a = idx / kBK, ii = idx - a * kBK;
       int i = i0 + ii;
-      Vs[a][ii] = (i < i_end) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a) : T(0);
+      Vs[a][ii] = (i < i_end) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a, skip) : T(0);
     }
     for (int idx = tid; idx < kBN * kBK; idx += kThreads) {
       int c = idx / kBK, ii = idx - c * kBK;
       int i = i0 + ii, cc = c0 + c;
       T v = T(0);
       if (i < i_end && cc < N) {
-        if (X_IS_V) v = v_at<T>(A, lda, Vtop, NB, k0, nbw, i, cc);
-        else v = X[SLQR_IDX(k0 + i, cc, ldx)];
+        if (X_IS_V) v = v_at<T>(A, lda, Vtop, NB, k0, nbw, i, cc, skip);
+        else v = X[SLQR_IDX(panel_row(k0, nbw, skip, i), cc, ldx)];
       }
       Xs[c][ii] = v;
     }
@@ -601,7 +616,8 @@ static void launch_tw(const T *Wp, int S, int N, const double *wy, int nbw, T *W
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads)
 gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vtop, int k0,
-                int nbw, int M, T *__restrict__ X, int ldx, int N, const T *__restrict__ Wt) {
+                int nbw, int M, T *__restrict__ X, int ldx, int N, const T *__restrict__ Wt,
+                int skip = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Vs = (T *)smem_raw;             // [NB][kBM]
   T *Ws = Vs + NB * kBM;             // [NB][kBN]
@@ -610,7 +626,7 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
   for (int idx = tid; idx < NB * kBM; idx += kThreads) {
     int a = idx / kBM, ii = idx - a * kBM;
     int i = i0 + ii;
-    Vs[idx] = (i < M) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a) : T(0);
+    Vs[idx] = (i < M) ? v_at<T>(A, lda, Vtop, NB, k0, nbw, i, a, skip) : T(0);
   }
   for (int idx = tid; idx < NB * kBN; idx += kThreads) {
     int a = idx / kBN, cc = idx - a * kBN;
@@ -642,7 +658,7 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
     for (int pp = 0; pp < 4; ++pp) {
       int i = i0 + tx + 16 * pp;
       if (i < M) {
-        T *dst = X + SLQR_IDX(k0 + i, cc, ldx);
+        T *dst = X + SLQR_IDX(panel_row(k0, nbw, skip, i), cc, ldx);
         *dst -= acc[pp][q];
       }
     }
@@ -692,9 +708,9 @@ static void vtop_part_f32(const float *A, int lda, const double *Vtop, int k0, i
 template <typename T, int NB, bool TRANS = true>
 static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const T *A, int lda,
                                      const double *wy_panel, T *X, int ldx, int N, T *work,
-                                     size_t work_elems, cudaStream_t stream) {
+                                     size_t work_elems, cudaStream_t stream, int skip = 0) {
   if (N <= 0) return SLQR_OK;
-  const int M = m - k0;
+  const int M = m - k0 - skip;                     // rows of the panel (row map: panel_row)
   const int ntiles = (N + kBN - 1) / kBN;
   const int S = split_count(M, ntiles, ctx->num_sms);
   int RS = (M + S - 1) / S;
@@ -712,7 +728,8 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   if constexpr (std::is_same<T, float>::value && NB == 64) {
     // TF32 path: both products on the tensor cores for a full panel whose X
     // lies in A (the factorization); W'^T and a row-major V follow the partials
-    if (ctx->use_tc && TRANS && nbw == 64 && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
+    if (ctx->use_tc && TRANS && skip == 0 && nbw == 64 && ldx == lda &&
+        X >= A + (size_t)lda * (k0 + nbw)) {
       const int xcol0 = (int)((X - A) / lda);
       slices = launch_vtx_tc(A, lda, Vtop, k0, M, xcol0, N, Wp, work_elems, ctx->num_sms,
                              ctx->d_status, stream, &vtop_part_f32);
@@ -737,7 +754,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   if (slices == 0) {
     slices = Seff;
     gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
-        A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp);
+        A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp, skip);
   }
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
@@ -758,19 +775,19 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   }
   if (!done)
     gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
-        A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+        A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt, skip);
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
   return check_launch(ctx, "trailing update");
 }
 
 slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const double *A,
                                int lda, const double *wy_panel, double *X, int ldx, int N,
-                               double *work, size_t work_doubles, cudaStream_t stream) {
+                               double *work, size_t work_doubles, cudaStream_t stream, int skip) {
   if (nb == 32)
     return panel_update_impl<double, 32>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
-                                         work_doubles, stream);
+                                         work_doubles, stream, skip);
   return panel_update_impl<double, 64>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N, work,
-                                       work_doubles, stream);
+                                       work_doubles, stream, skip);
 }
 
 // Opt the kernels that use more than 48 KB of dynamic shared memory in; run
@@ -842,10 +859,14 @@ static size_t panel_smem_bytes(int nb, int R, size_t elem) {
   return ((size_t)nb * R * elem + 15) / 16 * 16 + (size_t)nb * nb * sizeof(double);
 }
 
+// ntop > 0: A = [L^T; C] with an upper-triangular top block of ntop = n rows
+// (the structure-aware factorization: each panel skips the zero rows between
+// its diagonal block and C).
 template <typename T, int NB>
 static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, double *up,
-                               double *wy, cudaStream_t stream) {
+                               double *wy, cudaStream_t stream, int ntop = 0) {
   const int K = num_reflectors(m, n);
+  auto skip_of = [&](int k0, int nbw) { return ntop > 0 ? ntop - (k0 + nbw) : 0; };
   const int np = num_panels(K, NB);
   // workspace: [bar (256 B)] [records] [prow] [wy if none given] [trailing work]
   const int Pmax = ctx->num_sms;
@@ -877,6 +898,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     if (e != cudaSuccess)
       return fail(ctx, SLQR_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
+  if (np == 0) return SLQR_OK;
 
   // Look-ahead: after panel p, the columns of panel p+1 are updated first;
   // panel p+1 is then factored on the auxiliary stream while the rest of the
@@ -887,7 +909,8 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   auto launch_panel = [&](int pnl, cudaStream_t s) -> slqr_status {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
-    const int M = m - k0;
+    const int skip = skip_of(k0, nbw);
+    const int M = m - k0 - skip;
     const int R = panel_rows_per_cta(M, nbw, Pmax, max_rows_per_cta(NB, sizeof(T)));
     if (R > max_rows_per_cta(NB, sizeof(T)))
       return fail(ctx, SLQR_EINVAL, "m = %d is too large for the shared-memory panel", m);
@@ -897,7 +920,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
     pp.bar = bar;
     pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
-    pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    pp.skip = skip; pp.stacked = ntop > 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(T));
     // algorithmic flops of the panel: per column j a norm over M-j entries and,
@@ -921,7 +944,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     return panel_update_impl<T, NB>(ctx, m, k0, nbw, A, lda,
                                  wy_store + (size_t)pnl * wy_panel_doubles(NB),
                                  A + (size_t)c_begin * lda, lda, c_end - c_begin, work,
-                                 work_doubles, stream);
+                                 work_doubles, stream, skip_of(k0, nbw));
   };
   // order the auxiliary stream after everything already on the caller's stream
   e = cudaEventRecord(ctx->ev_start, stream);
@@ -1011,6 +1034,23 @@ extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int l
   cudaStream_t s = (cudaStream_t)stream;
   if (panel_width(m, n) == 32) return factor_impl<double, 32>(ctx, m, n, A, lda, up, wy, s);
   return factor_impl<double, 64>(ctx, m, n, A, lda, up, wy, s);
+}
+
+extern "C" slqr_status slqr_factor_stacked(slqr_ctx *ctx, int n, int m_eq, double *A, int lda,
+                                           double *up, double *wy, void *stream) {
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);
+  if (n == 0) return SLQR_OK;
+  const int m = n + m_eq;
+  if (lda < m) return fail(ctx, SLQR_EINVAL, "lda=%d < n + m_eq=%d", lda, m);
+  if (!A || !up) return fail(ctx, SLQR_EINVAL, "NULL A or up");
+  if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (panel_width(m, n) == 32) return factor_impl<double, 32>(ctx, m, n, A, lda, up, wy, s, n);
+  return factor_impl<double, 64>(ctx, m, n, A, lda, up, wy, s, n);
 }
 
 // ==========================================================================
@@ -1163,7 +1203,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
     pp.bar = bar;
     pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
-    pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    pp.skip = 0; pp.stacked = 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(double));
     e = cudaLaunchCooperativeKernel(panel_kernel_for<double, NB>(P), dim3(P), dim3(kThreads), args,

@@ -41,6 +41,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Resident {
   int m = 0, n = 0;
+  bool stacked = false;          // [L^T; C] factorization (slqr_factor_stacked)
   double *dA = nullptr, *dup = nullptr, *dwy = nullptr;
   size_t bytes = 0;
   cudaEvent_t ready = nullptr;   // the factorization is complete after this
@@ -195,7 +196,11 @@ static void admit(Server *S) {
       cudaMemcpyAsync(q.db, r.b, sizeof(double) * h->m, cudaMemcpyHostToDevice, s);
       cudaStreamWaitEvent(s, h->ready, 0);
       slqr_ctx *c = S->sub[si];
-      slqr_status st = slqr_apply_qt(c, h->m, h->n, h->dA, h->m, h->dup, h->dwy, 1, q.db, h->m, s);
+      slqr_status st =
+          h->stacked
+              ? slqr_apply_qt_stacked(c, h->n, h->m - h->n, h->dA, h->m, h->dup, h->dwy, 1, q.db,
+                                      h->m, s)
+              : slqr_apply_qt(c, h->m, h->n, h->dA, h->m, h->dup, h->dwy, 1, q.db, h->m, s);
       if (st == SLQR_OK) st = slqr_solve_r(c, h->n, h->dA, h->m, 1, q.db, h->m, s);
       Unit u;
       u.reqs.push_back(&q);
@@ -247,9 +252,13 @@ static void admit(Server *S) {
       S->small_ready[pi].push_back(&q);
     } else {
       slqr_ctx *c = S->sub[si];
-      st = slqr_factor(c, r.m, r.n, q.dA, r.m, q.dup, q.dwy, s);
+      const bool stacked = (r.structure == SLQR_STACKED);
+      st = stacked ? slqr_factor_stacked(c, r.n, r.m - r.n, q.dA, r.m, q.dup, q.dwy, s)
+                   : slqr_factor(c, r.m, r.n, q.dA, r.m, q.dup, q.dwy, s);
       if (st == SLQR_OK && q.db) {
-        st = slqr_apply_qt(c, r.m, r.n, q.dA, r.m, q.dup, q.dwy, 1, q.db, r.m, s);
+        st = stacked ? slqr_apply_qt_stacked(c, r.n, r.m - r.n, q.dA, r.m, q.dup, q.dwy, 1, q.db,
+                                             r.m, s)
+                     : slqr_apply_qt(c, r.m, r.n, q.dA, r.m, q.dup, q.dwy, 1, q.db, r.m, s);
         if (st == SLQR_OK) st = slqr_solve_r(c, r.n, q.dA, r.m, 1, q.db, r.m, s);
       }
       Unit u;
@@ -274,13 +283,14 @@ static void launch_batches(Server *S) {
     auto &ready = S->small_ready[pi];
     if (ready.empty()) continue;
     const int cnt = (int)ready.size();
-    std::vector<int> m(cnt), n(cnt), lda(cnt);
+    std::vector<int> m(cnt), n(cnt), ntop(cnt), lda(cnt);
     std::vector<double *> A(cnt), up(cnt), b(cnt);
     bool any_b = false;
     for (int i = 0; i < cnt; ++i) {
       const Req &q = *ready[i];
       m[i] = q.r.m;
       n[i] = q.r.n;
+      ntop[i] = (q.r.structure == SLQR_STACKED) ? q.r.n : 0;
       lda[i] = q.r.m;
       A[i] = q.dA;
       up[i] = q.dup;
@@ -292,9 +302,10 @@ static void launch_batches(Server *S) {
     u.stream = s;
     u.d_status = (int *)pool_alloc(S, sizeof(int) * cnt, s);
     u.d_err = pool_alloc(S, sizeof(double) * cnt, s);
-    slqr_status st = slqr_batch_factor(S->bctx[pi], cnt, m.data(), n.data(), A.data(), lda.data(),
-                                       up.data(), any_b ? b.data() : nullptr,
-                                       pi ? SLQR_FP32 : SLQR_FP64, u.d_status, u.d_err, s);
+    slqr_status st = batch_factor_locked(S->bctx[pi], cnt, m.data(), n.data(), ntop.data(),
+                                         A.data(), lda.data(), up.data(),
+                                         any_b ? b.data() : nullptr, pi ? SLQR_FP32 : SLQR_FP64,
+                                         u.d_status, u.d_err, s);
     u.reqs = ready;
     cudaEventCreateWithFlags(&u.done, cudaEventDisableTiming);
     cudaEventRecord(u.done, s);
@@ -348,6 +359,7 @@ static void retire(Server *S) {
           Resident h;
           h.m = r.m;
           h.n = r.n;
+          h.stacked = (r.structure == SLQR_STACKED);
           h.dA = q.dA;
           h.dup = q.dup;
           h.dwy = q.small ? nullptr : q.dwy;   // the batched kernel keeps no WY store
@@ -497,6 +509,8 @@ extern "C" slqr_status slqr_submit(slqr_ctx *ctx, const slqr_request *req, uint6
         return fail(ctx, SLQR_EINVAL,
                     "request: SLQR_FP32 serves FACTOR_SOLVE with m <= %d", slqr_batch_max_rows());
       if (r.m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "request: m above slqr_max_rows()");
+      if (r.structure != SLQR_DENSE && r.structure != SLQR_STACKED)
+        return fail(ctx, SLQR_EINVAL, "request: unknown structure %d", r.structure);
       break;
     case SLQR_REQ_SOLVE:
       if (!r.b || !r.x) return fail(ctx, SLQR_EINVAL, "request: SOLVE needs b and x");

@@ -116,6 +116,13 @@ int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, in
                   void (*vtop_part)(const float *, int, const double *, int, int, const float *, int,
                                     int, float *, cudaStream_t));
 
+// slqr_batch_factor with a per-problem stacked top block (ntop[i] rows, 0 for a
+// dense problem; ntop may be NULL); takes the context mutex.
+slqr_status batch_factor_locked(slqr_ctx *ctx, int count, const int *m, const int *n,
+                                const int *ntop, double *const *A, const int *lda,
+                                double *const *up, double *const *b, int prec, int *status,
+                                double *err, void *stream);
+
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);
 
@@ -140,10 +147,12 @@ __host__ __device__ inline int num_reflectors(int m, int n) {
 // --- launchers (defined in factor.cu / apply.cu / solve.cu) -------------
 // Trailing update of columns [c0, c0+N) of the matrix X (rows [k0, m), leading
 // dimension ldx) by the panel (V from A/Vtop, G, tau) at offset k0 of width nbw.
+// skip: rows left out after the panel's top nbw rows (stacked [L^T; C], see
+// panel_row in factor.cu); 0 for a dense matrix.
 slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
                                const double *A, int lda, const double *wy_panel,
                                double *X, int ldx, int N, double *work, size_t work_doubles,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int skip = 0);
 size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
 
 // FP32 factorization (FP64 reflector constants) and FP32 compact-WY panel

@@ -267,6 +267,22 @@ def test_upper_triangular_tall_gives_minus_a():
     assert np.all(np.tril(F, -1) == 0)
 
 
+@pytest.mark.parametrize("n,m_eq", [(1, 0), (6, 0), (6, 3), (40, 25), (120, 7)])
+def test_stacked_top_block_stays_exactly_zero(n, m_eq):
+    """For A = [L^T; C] the reflector of column k has zeros in rows k+1..n-1 and
+    no reflector changes those rows: after the factorization the strictly
+    lower part of the top n x n block is still exactly zero (the fact the
+    structure-aware factorization rests on), and R^T R = A^T A."""
+    A, _ = workloads.slsqp_stack(n, m_eq, seed=n + 13 * m_eq)
+    assert np.all(np.tril(A[:n], -1) == 0.0)
+    F, up, skipped = oracle.h12_factor(A)
+    assert skipped == 0
+    assert np.all(np.tril(F[:n], -1) == 0.0)
+    R = np.triu(F[:n])
+    G = A.T @ A
+    np.testing.assert_allclose(R.T @ R, G, rtol=0, atol=1e-12 * np.abs(G).max())
+
+
 def test_orthogonal_input_gives_unit_r():
     rng = np.random.default_rng(11)
     Q, _ = np.linalg.qr(rng.standard_normal((20, 20)))
