@@ -441,7 +441,9 @@ def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):
     """Poisson request streams of SLSQP-shaped LS subproblems [L^T; C]
     (n ~ log-U[50, 2000], m_eq ~ U{0..n/2}), FACTOR_SOLVE each, through
     slqr_submit / slqr_poll; reports solves/s and p50/p99 latency per rate, in
-    FP64 and mixed (FP32 + refinement for m <= 512, FP64 above)."""
+    FP64 and mixed (FP32 + refinement for m <= 512, FP64 above), each as a
+    dense request and as a stacked one (SLQR_STACKED: the structure-aware
+    factorization of [L^T; C])."""
     import time
     import workloads
     from paper_2506_09463_gb300 import abi, api
@@ -450,7 +452,9 @@ def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):
     gflop = sum(2.0 * (n + me) * n * n - 2.0 * n ** 3 / 3.0 for n, me in zip(ns, meqs)) / 1e9
     out = {"requests": count, "mean_gflop_per_request": gflop / count,
            "shapes": "[L^T; C], n ~ log-U[50,2000], m_eq ~ U{0..n/2}, Poisson arrivals"}
-    for mode in ("fp64", "mixed"):
+    modes = (("fp64", abi.SLQR_DENSE), ("mixed", abi.SLQR_DENSE),
+             ("fp64_stacked", abi.SLQR_STACKED), ("mixed_stacked", abi.SLQR_STACKED))
+    for mode, structure in modes:
         res_mode = {}
         for rate in rates:
             with api.Context(ctx_device) as sctx:
@@ -466,8 +470,10 @@ def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):
                     while time.perf_counter() - t0 < arrivals[i]:
                         pass
                     A, b = problems[i]
-                    prec = abi.SLQR_FP32 if (mode == "mixed" and A.shape[0] <= 512) else abi.SLQR_FP64
-                    tickets.append(srv.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b, prec=prec))
+                    mixed = mode.startswith("mixed") and A.shape[0] <= 512
+                    prec = abi.SLQR_FP32 if mixed else abi.SLQR_FP64
+                    tickets.append(srv.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b, prec=prec,
+                                              structure=structure))
                 lat, bad = [], 0
                 for t in tickets:
                     r, _ = srv.wait(t, timeout_s=600)
