@@ -51,25 +51,54 @@ struct BatchParams {
   int *status;
 };
 
-constexpr int kNoExpB = -4000;
-
-__device__ __forceinline__ void b_ssq_add(int &E, double &S, double x) {
-  if (x != 0.0) {
-    int ex = ilogb(x);
-    if (ex > E) {
-      S = ldexp(S, 2 * (E - ex));
-      E = ex;
-    }
-    double y = ldexp(x, -E);
-    S = fma(y, y, S);
-  }
+// Exponent bits of |x| (as a double): the integer order of these bit patterns
+// is the numeric order, so a max over them finds the largest magnitude.
+template <typename T>
+__device__ __forceinline__ unsigned b_abs_hi(T x) {
+  return (unsigned)((unsigned long long)__double_as_longlong((double)x) >> 32) & 0x7fffffffu;
 }
 
-__device__ __forceinline__ void b_ssq_merge(int &E, double &S, int E2, double S2) {
-  if (S2 == 0.0) return;
-  if (S == 0.0) { E = E2; S = S2; return; }
-  if (E2 > E) { S = ldexp(S, 2 * (E - E2)) + S2; E = E2; }
-  else S = S + ldexp(S2, 2 * (E2 - E));
+// 2^e as a double for e in [-1022, 1023] (exact; built from the exponent bits)
+__device__ __forceinline__ double b_pow2(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Sum over a warp of 16 per-lane values acc[0..15] (each lane its own
+// partials): a halving exchange -- at each of four levels a lane keeps half of
+// its values and adds the other half received from its partner -- then one
+// last exchange.  16 shuffles and 16 adds per lane instead of 80 of each for
+// 16 separate butterflies.  Lanes 2a and 2a+1 end with the total of value a.
+template <typename T>
+__device__ __forceinline__ T b_warp_sum16(T (&acc)[kBNB], int lane) {
+  static_assert(kBNB == 16, "four halving levels");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = (lane & 16) != 0;
+    const T send = hi ? acc[i] : acc[i + 8];
+    const T keep = hi ? acc[i + 8] : acc[i];
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = (lane & 8) != 0;
+    const T send = hi ? acc[i] : acc[i + 4];
+    const T keep = hi ? acc[i + 4] : acc[i];
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = (lane & 4) != 0;
+    const T send = hi ? acc[i] : acc[i + 2];
+    const T keep = hi ? acc[i + 2] : acc[i];
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = (lane & 2) != 0;
+    const T send = hi ? acc[0] : acc[1];
+    const T keep = hi ? acc[1] : acc[0];
+    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
 }
 
 __device__ __forceinline__ double b_warp_sum(double v) {
@@ -89,7 +118,7 @@ struct BatchSmem {
   static constexpr int kW = kBNB * (kBCols + 1);        // Wt[a][col]
   static constexpr size_t kBytesT = (size_t)(kPanel + kW) * sizeof(T);
   static constexpr int kG = kBNB * kBNB;                // G[q][j] (ld kBNB)
-  static constexpr int kMisc = 4 * kBNB + 8;            // dots, sigma, tau, up, norm
+  static constexpr int kMisc = 5 * kBNB + 8;            // dots, sigma, tau, up, scale, norm
   static constexpr size_t kBytes = align_up_c(kBytesT, 16) + (size_t)(kG + kMisc) * sizeof(double);
 };
 
@@ -117,7 +146,8 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
   double *sig = dots + kBNB;
   double *tau = sig + kBNB;
   double *ups = tau + kBNB;
-  double *misc = ups + kBNB;        // [0] = norm
+  double *scl = ups + kBNB;         // per-column scale 2^-E of the panel
+  double *misc = scl + kBNB;        // [0] = norm
   const int K = num_reflectors(m, n);
   for (int k = K + tid; k < n; k += kThreads) up_out[k] = 0.0;
 
@@ -134,6 +164,25 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
       Ps[c * kBMaxRows + r] = zero ? T(0) : A[SLQR_IDX(k0 + prow(r), k0 + c, lda)];
     }
     __syncthreads();
+    // Per-column scale of the panel for the overflow-safe norm: 2^-E with E the
+    // exponent of the column's largest |entry| from its diagonal down (an exact
+    // power of two; entries that earlier reflectors of the panel add stay
+    // within a factor sqrt(M) of it).
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int c = warp + kBWarps * t;
+      if (c < nbw) {
+        unsigned mx = 0;
+        for (int r = c + lane; r < M; r += 32) mx = max(mx, b_abs_hi(Ps[c * kBMaxRows + r]));
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) {
+          int E = (int)((mx >> 20) & 0x7ff) - 1023;
+          E = min(max(E, -1000), 1022);
+          scl[c] = b_pow2(-E);
+        }
+      }
+    }
+    __syncthreads();
     for (int j = 0; j < nbw; ++j) {
       const T *x = Ps + j * kBMaxRows;
       // phase 1: warp w takes panel columns w and w + 8
@@ -142,16 +191,14 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         const int c = warp + kBWarps * t;
         if (c >= nbw) continue;
         if (c == j) {
-          int E = kNoExpB;
+          const double sc = scl[j];
           double S = 0.0;
-          for (int r = j + lane; r < M; r += 32) b_ssq_add(E, S, (double)x[r]);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            int E2 = __shfl_xor_sync(0xffffffffu, E, o);
-            double S2 = __shfl_xor_sync(0xffffffffu, S, o);
-            b_ssq_merge(E, S, E2, S2);
+          for (int r = j + lane; r < M; r += 32) {
+            const double xs = (double)x[r] * sc;
+            S = fma(xs, xs, S);
           }
-          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : ldexp(sqrt(S), E);
+          S = b_warp_sum(S);
+          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : sqrt(S) / sc;
         } else {
           const T *col = Ps + c * kBMaxRows;
           T acc = T(0);
@@ -240,13 +287,8 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
           for (int a = 0; a < kBNB; ++a)
             if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
         }
-#pragma unroll
-        for (int a = 0; a < kBNB; ++a) {
-          T v = acc[a];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) Wt[a * (kBCols + 1) + cc] = v;
-        }
+        const T v = b_warp_sum16(acc, lane);        // lanes 2a, 2a+1 hold W[a]
+        if ((lane & 1) == 0) Wt[(lane >> 1) * (kBCols + 1) + cc] = v;
       }
       __syncthreads();
       // phase B: W' = T^T W, one lane per column (FP64 arithmetic)
