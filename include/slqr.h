@@ -121,8 +121,9 @@ slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double 
  * Process-wide tuning knobs of the blocked factorization (no counterpart in the
  * paper; its alpha/beta task sizes play this role on the CPU):
  *   panel_width     32 or 64 forces the panel width (0: 32 for n <= 256, else 64)
- *   panel_rows_min  smallest slice of rows one panel CTA holds (0: 192); larger
- *                   values put fewer CTAs on each panel
+ *   panel_rows_min  smallest slice of rows one panel CTA holds (0: by panel
+ *                   height, 64 below 1536 rows, 128 below 6144, else 192);
+ *                   larger values put fewer CTAs on each panel
  * Changing the panel width changes slqr_panel_width and slqr_wy_size: set it
  * before allocating compact-WY stores, and not while calls are in flight.
  */

@@ -40,20 +40,10 @@ namespace slqr {
 // --------------------------------------------------------------------------
 // small device helpers
 // --------------------------------------------------------------------------
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-__device__ __forceinline__ void record_status(int *status, int code) {
-  atomicCAS(status, kStatusOk, code);
 }
 
 // --------------------------------------------------------------------------
@@ -87,31 +77,6 @@ struct PanelParams {
 // and untouched by the update, so they are left out.
 __host__ __device__ __forceinline__ int panel_row(int k0, int nbw, int skip, int i) {
   return k0 + i + (i >= nbw ? skip : 0);
-}
-
-// Arrive at the grid barrier and wait (bounded) until `target` arrivals.
-// Returns false after recording SLQR_ETIMEOUT.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
-                                             int *s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    unsigned it = 0;
-    int ok = 1;
-    while (ld_acquire_u32(bar) < target) {
-      if (++it > kSpinLimit) { ok = 0; break; }
-      if (it > 256) __nanosleep(64);
-    }
-    __threadfence();
-    *s_ok = ok;
-  }
-  __syncthreads();
-  if (!*s_ok) {
-    if (threadIdx.x == 0) record_status(status, SLQR_ETIMEOUT);
-    return false;
-  }
-  return true;
 }
 
 // Bits of |x| as an unsigned 64-bit integer: for non-negative doubles the
@@ -671,8 +636,14 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 // Tuning knobs (slqr_set_tuning): panel width override and the smallest
 // slice of rows a panel CTA holds (which sets how many CTAs share a panel).
 static int g_tune_nb = 0;
-constexpr int kDefaultRowsMin = 192;   // measured best on GB300 for 2048..8192 columns
-static int g_tune_rows_min = kDefaultRowsMin;
+static int g_tune_rows_min = 0;        // 0: chosen from the panel height (rows_min_auto)
+
+// Smallest row slice per panel CTA when not set: small panels get more CTAs
+// (each column step then does less FP64 work per SM), tall ones fewer (they
+// share the SMs with the concurrent trailing update).  Measured on GB300:
+// 600 x 500 and 1200 x 1000 are 20-25% faster with 64 rows than with 192,
+// 2500..5000 rows best with 128, 8192 rows and up with 192.
+static int rows_min_auto(int M) { return M < 1536 ? 64 : (M < 6144 ? 128 : 192); }
 
 int panel_width(int m, int n) {
   (void)m;
@@ -837,7 +808,7 @@ static int panel_rows_per_cta(int M, int nbw, int num_sms, int max_rows) {
   const int ctas = std::min(num_sms, kMaxPanelCtas);
   int R = (M + ctas - 1) / ctas;
   R = std::max(R, nbw);
-  R = std::max(R, g_tune_rows_min);
+  R = std::max(R, g_tune_rows_min > 0 ? g_tune_rows_min : rows_min_auto(M));
   const int r_small = (M + kSmallPanelCtas - 1) / kSmallPanelCtas;
   if (r_small <= max_rows) R = std::max(R, r_small);
   return R;
@@ -985,20 +956,6 @@ slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *u
   return factor_impl<float, 64>(ctx, m, n, A, lda, up, wy, stream);
 }
 
-slqr_status apply_panel_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const float *A,
-                                   int lda, const double *wy_panel, float *X, int ldx, int N,
-                                   float *work, size_t work_elems, cudaStream_t stream,
-                                   bool trans) {
-  if (nb == 32)
-    return trans ? panel_update_impl<float, 32, true>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx,
-                                                      N, work, work_elems, stream)
-                 : panel_update_impl<float, 32, false>(ctx, m, k0, nbw, A, lda, wy_panel, X,
-                                                       ldx, N, work, work_elems, stream);
-  return trans ? panel_update_impl<float, 64, true>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx, N,
-                                                    work, work_elems, stream)
-               : panel_update_impl<float, 64, false>(ctx, m, k0, nbw, A, lda, wy_panel, X, ldx,
-                                                     N, work, work_elems, stream);
-}
 
 }  // namespace slqr
 
@@ -1008,7 +965,7 @@ extern "C" int slqr_panel_width(int m, int n) { return panel_width(m, n); }
 
 extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
   g_tune_nb = (panel_width == 32 || panel_width == 64) ? panel_width : 0;
-  g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : kDefaultRowsMin;
+  g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : 0;
 }
 
 extern "C" size_t slqr_wy_size(int m, int n) {

@@ -206,6 +206,140 @@ trsv_f32_step_kernel(const float *__restrict__ R, int lda, int n, float *__restr
   }
 }
 
+// --------------------------------------------------------------------------
+// Q^T f and Q f for one FP32 vector in a single cooperative launch.
+//
+// Each panel's block reflector is applied as f <- f - V (T^T (V^T f)) (Q^T)
+// or f - V (T (V^T f)) (Q), with the panels taken in order (Q^T) or in
+// reverse (Q).  T is formed once per factorization (tmat_kernel) from
+// T^-1 = striu(V^T V) + diag(1/tau).  A CTA owns a fixed slice of R rows of f:
+// per panel it stages its slice of V in shared memory, publishes its 64
+// partial dot products, and after one grid barrier every CTA sums the
+// partials of all CTAs in the same fixed order, forms W' = T^T W (or T W) and
+// updates its own rows.  One barrier per panel instead of three launches.
+// --------------------------------------------------------------------------
+constexpr int kQvRows = 256;     // rows of f per CTA (at most)
+
+// T of panel p (float, ld nb + 1): column j solves U y = e_j by back
+// substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and
+// y_i = -tau_i sum_{k=i+1..j} G[i,k] y_k (tau = 0: a zero row and column).
+__global__ void __launch_bounds__(64)
+tmat_kernel(const double *__restrict__ wy, int nb, int K, float *__restrict__ Tm) {
+  __shared__ double ys[64][65];
+  const int pnl = blockIdx.x, j = threadIdx.x;
+  const int nbw = min(nb, K - pnl * nb);
+  const double *G = wy + (size_t)pnl * wy_panel_doubles(nb) + (size_t)nb * nb;
+  const double *tau = G + (size_t)nb * nb;
+  float *T = Tm + (size_t)pnl * nb * (nb + 1);
+  if (j < nb) {
+    for (int i = 0; i < nb; ++i) ys[i][j] = 0.0;
+    if (j < nbw) {
+      ys[j][j] = tau[j];
+      for (int i = j - 1; i >= 0; --i) {
+        double t = 0.0;
+        for (int k = i + 1; k <= j; ++k) t = fma(G[i + (size_t)k * nb], ys[k][j], t);
+        ys[i][j] = -tau[i] * t;
+      }
+    }
+    for (int i = 0; i < nb; ++i) T[i + (size_t)j * (nb + 1)] = (float)ys[i][j];
+  }
+}
+
+struct QvecParams {
+  const float *A;        // FP32 factorization (H12 form), ld lda
+  const double *wy;      // compact-WY store (Vtop of each panel)
+  const float *Tm;       // explicit T of each panel, nb x nb, ld nb + 1
+  float *f;              // the vector, m entries, updated in place
+  float *part;           // 2 buffers x P CTAs x nb partial sums
+  unsigned *bar;         // monotonic arrival counter
+  int *status;
+  int lda, m, K, nb, np;
+  int trans;             // 1: Q^T f, 0: Q f
+  int R, P;
+  unsigned bar_base;
+};
+
+__global__ void __launch_bounds__(kThreads)
+qvec_kernel(QvecParams p) {
+  extern __shared__ __align__(16) float qv_smem[];
+  const int nb = p.nb, R = p.R;
+  float *Vs = qv_smem;                          // [nb][R + 1]
+  float *fs = Vs + (size_t)nb * (R + 1);        // [R]
+  float *Ts = fs + R;                           // [nb][nb + 1]
+  float *red = Ts + (size_t)nb * (nb + 1);      // [kThreads / nb][nb]
+  float *ws = red + kThreads;                   // [nb]
+  float *wt = ws + nb;                          // [nb]
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, cta = blockIdx.x;
+  const int r0 = cta * R, r1 = min(p.m, r0 + R);
+  for (int step = 0; step < p.np; ++step) {
+    const int pnl = p.trans ? step : p.np - 1 - step;
+    const int k0 = pnl * nb, nbw = min(nb, p.K - k0);
+    const double *Vtop = p.wy + (size_t)pnl * wy_panel_doubles(nb);
+    const int lo = max(r0, k0), rows = max(0, r1 - lo);
+    float *mypart = p.part + ((size_t)(step & 1) * p.P + cta) * nb;
+    // phase A: stage V and f of the slice, partial dots V^T f
+    for (int idx = tid; idx < nbw * rows; idx += kThreads) {
+      const int a = idx / rows, rr = idx - a * rows;
+      const int i = lo + rr, ii = i - k0;
+      Vs[a * (R + 1) + rr] = (ii < nbw) ? (float)Vtop[ii + a * nb] : p.A[SLQR_IDX(i, k0 + a, p.lda)];
+    }
+    for (int rr = tid; rr < rows; rr += kThreads) fs[rr] = p.f[lo + rr];
+    __syncthreads();
+    {
+      const int a = tid % nb, g = tid / nb, G = kThreads / nb;
+      float acc = 0.f;
+      if (a < nbw)
+        for (int rr = g; rr < rows; rr += G) acc = fmaf(Vs[a * (R + 1) + rr], fs[rr], acc);
+      red[g * nb + a] = acc;
+      __syncthreads();
+      if (tid < nb) {
+        float v = 0.f;
+        for (int q = 0; q < G; ++q) v += red[q * nb + tid];
+        mypart[tid] = v;
+      }
+    }
+    for (int idx = tid; idx < nb * nb; idx += kThreads) {
+      const int i = idx % nb, j = idx / nb;
+      Ts[i + j * (nb + 1)] = p.Tm[(size_t)pnl * nb * (nb + 1) + i + j * (nb + 1)];
+    }
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
+      return;
+    // phase B: W (all CTAs, fixed order), then W' = T^T W or T W
+    if (tid < nb) {
+      const float *src = p.part + (size_t)(step & 1) * p.P * nb + tid;
+      float v = 0.f;
+      for (int q = 0; q < p.P; ++q) v += __ldcg(src + (size_t)q * nb);
+      ws[tid] = v;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      const int j = tid;
+      float v = 0.f;
+      if (j < nbw) {
+        if (p.trans) {
+          for (int q = 0; q <= j; ++q) v = fmaf(Ts[q + j * (nb + 1)], ws[q], v);
+        } else {
+          for (int q = j; q < nbw; ++q) v = fmaf(Ts[j + q * (nb + 1)], ws[q], v);
+        }
+      }
+      wt[j] = v;
+    }
+    __syncthreads();
+    // phase C: f -= V W' on the slice
+    for (int rr = tid; rr < rows; rr += kThreads) {
+      float v = fs[rr];
+      for (int a = 0; a < nbw; ++a) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
+      p.f[lo + rr] = v;
+    }
+    __syncthreads();
+  }
+}
+
+static size_t qvec_smem_bytes(int nb, int R) {
+  return sizeof(float) * ((size_t)nb * (R + 1) + R + (size_t)nb * (nb + 1) + kThreads + 2 * nb);
+}
+
 }  // namespace slqr
 
 namespace slqr {
@@ -250,7 +384,6 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   const int np = num_panels(K, nb);
   const int chunks = (n + kColChunk - 1) / kColChunk;
   const int ublocks = (n + 255) / 256;
-  const size_t work_elems = panel_update_work_doubles(m, 1, nb, ctx->num_sms);
   // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -265,7 +398,12 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   const size_t o_part = take((size_t)chunks * m * sizeof(double));
   const size_t o_max = take((size_t)2 * ublocks * sizeof(double));
   const size_t o_flag = take(sizeof(int));
-  const size_t o_work = take(work_elems * sizeof(float));
+  // fused Q application: rows per CTA, explicit T per panel, partials, barrier
+  const int qv_R = std::max(kQvRows, (m + ctx->num_sms - 1) / ctx->num_sms);
+  const int qv_P = (m + qv_R - 1) / qv_R;
+  const size_t o_tm = take((size_t)std::max(np, 1) * nb * (nb + 1) * sizeof(float));
+  const size_t o_qpart = take((size_t)2 * qv_P * nb * sizeof(float));
+  const size_t o_bar = take(256);
   slqr_status st = ensure_workspace2(ctx, off);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws2.ptr;
@@ -279,13 +417,36 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   double *part = (double *)(base + o_part);
   double *maxima = (double *)(base + o_max);
   int *zero_flag = (int *)(base + o_flag);
-  float *work = (float *)(base + o_work);
+  float *Tm = (float *)(base + o_tm);
+  float *qpart = (float *)(base + o_qpart);
+  unsigned *qbar = (unsigned *)(base + o_bar);
+  const size_t qv_smem = qvec_smem_bytes(nb, qv_R);
+  e = cudaFuncSetAttribute(qvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qv_smem);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
+  unsigned qbar_base = 0;
+  // f <- Q^T f (trans) or Q f with one cooperative launch
+  auto apply_q = [&](bool trans) -> slqr_status {
+    if (np == 0) return SLQR_OK;
+    QvecParams qp;
+    qp.A = A32; qp.wy = wy; qp.Tm = Tm; qp.f = f32; qp.part = qpart; qp.bar = qbar;
+    qp.status = ctx->d_status; qp.lda = lda32; qp.m = m; qp.K = K; qp.nb = nb; qp.np = np;
+    qp.trans = trans ? 1 : 0; qp.R = qv_R; qp.P = qv_P; qp.bar_base = qbar_base;
+    void *args[] = {&qp};
+    cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel, dim3(qv_P),
+                                                 dim3(kThreads), args, qv_smem, s);
+    if (le != cudaSuccess)
+      return fail(ctx, SLQR_ECUDA, "Q application: %s", cudaGetErrorString(le));
+    qbar_base += (unsigned)np * (unsigned)qv_P;
+    return SLQR_OK;
+  };
 
   to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32, lda32);
   ctx->use_tc = (prec == SLQR_TF32);
   st = factor_f32(ctx, m, n, A32, lda32, up, wy, s);
   ctx->use_tc = false;
   if (st != SLQR_OK) return st;
+  if (np > 0) tmat_kernel<<<np, 64, 0, s>>>(wy, nb, K, Tm);
+  cudaMemsetAsync(qbar, 0, 256, s);
   init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, m, x, n);
   cudaMemsetAsync(zero_flag, 0, sizeof(int), s);
   std::vector<double> hmax(2 * ublocks);
@@ -297,21 +458,13 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
     resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(b, r, part, chunks, m, f32);
     resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, r, g32);
     trsv_f32<false>(A32, lda32, n, g32, zero_flag, s);                   // h = R^-T g
-    for (int p = 0; p < np; ++p) {                                      // d = Q^T f
-      const int k0 = p * nb, nbw = std::min(nb, K - k0);
-      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, lda32, wy + (size_t)p * wy_panel_doubles(nb),
-                                  f32, m, 1, work, work_elems, s, true);
-      if (st != SLQR_OK) return st;
-    }
+    st = apply_q(true);                                                 // d = Q^T f
+    if (st != SLQR_OK) return st;
     form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(f32, g32, m, n, e32);
     trsv_f32<true>(A32, lda32, n, e32, zero_flag, s);                    // dx = R^-1 (d1 - h)
     update_kernel<<<ublocks, 256, 0, s>>>(f32, g32, e32, x, n, maxima);  // d = [h; d2], x += dx
-    for (int q = np - 1; q >= 0; --q) {                                 // dr = Q [h; d2]
-      const int k0 = q * nb, nbw = std::min(nb, K - k0);
-      st = apply_panel_update_f32(ctx, m, k0, nbw, nb, A32, lda32, wy + (size_t)q * wy_panel_doubles(nb),
-                                  f32, m, 1, work, work_elems, s, false);
-      if (st != SLQR_OK) return st;
-    }
+    st = apply_q(false);                                                // dr = Q [h; d2]
+    if (st != SLQR_OK) return st;
     add_r_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, f32, m);
     int zflag = 0;
     e = cudaMemcpyAsync(hmax.data(), maxima, sizeof(double) * 2 * ublocks, cudaMemcpyDeviceToHost, s);

@@ -123,6 +123,45 @@ slqr_status batch_factor_locked(slqr_ctx *ctx, int count, const int *m, const in
                                 double *const *up, double *const *b, int prec, int *status,
                                 double *err, void *stream);
 
+// --------------------------------------------------------------------------
+// device helpers shared by the cooperative kernels
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void record_status(int *status, int code) {
+  atomicCAS(status, kStatusOk, code);
+}
+
+// Arrive at a grid barrier (a monotonic arrival counter) and wait, bounded,
+// until it reaches `target`.  Returns false after recording SLQR_ETIMEOUT.
+// Cooperative launches only (every CTA resident).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
+                                             int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    unsigned it = 0;
+    int ok = 1;
+    while (ld_acquire_u32(bar) < target) {
+      if (++it > kSpinLimit) { ok = 0; break; }
+      if (it > 256) __nanosleep(64);
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  if (!*s_ok) {
+    if (threadIdx.x == 0) record_status(status, SLQR_ETIMEOUT);
+    return false;
+  }
+  return true;
+}
+
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);
 
@@ -155,13 +194,9 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
                                cudaStream_t stream, int skip = 0);
 size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
 
-// FP32 factorization (FP64 reflector constants) and FP32 compact-WY panel
-// application (trans: Q^T, else Q) used by the mixed-precision driver.
+// FP32 factorization (FP64 reflector constants) used by the mixed-precision
+// driver.
 slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
                        cudaStream_t stream);
-slqr_status apply_panel_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, int nb, const float *A,
-                                   int lda, const double *wy_panel, float *X, int ldx, int N,
-                                   float *work, size_t work_elems, cudaStream_t stream,
-                                   bool trans);
 
 }  // namespace slqr
