@@ -129,6 +129,19 @@ slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double 
  */
 void slqr_set_tuning(int panel_width, int panel_rows_min);
 
+/*
+ * Autotuner of those knobs for one problem shape: times slqr_factor of a
+ * generic m x n scratch matrix (allocated and freed here) under panel width
+ * 32 and 64 and rows-per-CTA minimum 0 (by panel height), 64, 96, 128, 192 and
+ * 256, keeps the fastest with slqr_set_tuning (process-wide) and reports it.
+ * Synchronous; takes about 24 factorizations of that shape.
+ *   best_ms, best_panel_width, best_rows_min  HOST outputs, each may be NULL
+ * Errors: SLQR_EINVAL (sizes), SLQR_ENOMEM (scratch), SLQR_ECUDA; on error
+ * the previous tuning is kept.
+ */
+slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_ms, int *best_panel_width,
+                          int *best_rows_min);
+
 /* Largest m that slqr_factor accepts (the panel is held in shared memory). */
 int slqr_max_rows(void);
 

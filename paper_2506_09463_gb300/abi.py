@@ -63,6 +63,8 @@ SIGNATURES = [
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
     ("slqr_set_tuning", None, [_c_int, _c_int]),
+    ("slqr_autotune", _c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_dbl), ctypes.POINTER(_c_int),
+                               ctypes.POINTER(_c_int)]),
     ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     ("slqr_apply_qt", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _vp, _c_int, _vp]),
     ("slqr_solve_r", _c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int, _vp]),
@@ -158,6 +160,13 @@ def slqr_max_rows() -> int:
 
 def slqr_set_tuning(panel_width: int = 0, panel_rows_min: int = 0) -> None:
     _lib.slqr_set_tuning(panel_width, panel_rows_min)
+
+
+def slqr_autotune(ctx, m, n):
+    """Returns (status, best_ms, panel_width, rows_min) and keeps that tuning."""
+    ms, w, r = _dbl(), _c_int(), _c_int()
+    st = _lib.slqr_autotune(ctx, m, n, ctypes.byref(ms), ctypes.byref(w), ctypes.byref(r))
+    return st, ms.value, w.value, r.value
 
 
 def slqr_factor(ctx, m, n, A, lda, up, wy, stream) -> int:

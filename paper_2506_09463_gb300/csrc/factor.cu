@@ -968,6 +968,103 @@ extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
   g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : 0;
 }
 
+namespace slqr {
+
+// Deterministic scratch matrix for the autotuner: entries in (-1, 1) from a
+// hash of the index (the timing does not depend on the values, only on their
+// being generic).
+__global__ void tune_fill_kernel(double *A, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long h = (i + 1) * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 27;
+    A[i] = (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+}  // namespace slqr
+
+extern "C" slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_ms,
+                                     int *best_panel_width, int *best_rows_min) {
+  if (!ctx) return SLQR_EINVAL;
+  if (m < 1 || n < 1 || m < n || m > slqr_max_rows())
+    return fail(ctx, SLQR_EINVAL, "autotune: need 1 <= n <= m <= %d (m=%d n=%d)", slqr_max_rows(),
+                m, n);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  const size_t count = (size_t)m * n;
+  double *A0 = nullptr, *A = nullptr, *up = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMalloc(&A0, count * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&A, count * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&up, (size_t)n * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(A0);
+    cudaFree(A);
+    cudaFree(up);
+  };
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, SLQR_ENOMEM, "autotune scratch: %s", cudaGetErrorString(e));
+  }
+  tune_fill_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A0, count);
+  const int saved_nb = g_tune_nb, saved_rows = g_tune_rows_min;
+  const int widths[2] = {32, 64};
+  const int rows[6] = {0, 64, 96, 128, 192, 256};
+  double best = 1e300;
+  int bw = 0, br = 0;
+  slqr_status st = SLQR_OK;
+  for (int wi = 0; wi < 2 && st == SLQR_OK; ++wi) {
+    if (widths[wi] == 64 && n <= 32) continue;      // one panel either way
+    for (int ri = 0; ri < 6 && st == SLQR_OK; ++ri) {
+      g_tune_nb = widths[wi];
+      g_tune_rows_min = rows[ri];
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 2 && st == SLQR_OK; ++rep) {
+        cudaMemcpyAsync(A, A0, count * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaEventRecord(e0, s);
+        st = slqr_factor(ctx, m, n, A, m, up, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = SLQR_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (st == SLQR_EINVAL) {                      // setting outside the kernel limits
+        st = SLQR_OK;
+        continue;
+      }
+      if (st == SLQR_OK && ms_min < best) {
+        best = ms_min;
+        bw = widths[wi];
+        br = rows[ri];
+      }
+    }
+  }
+  cleanup();
+  if (st != SLQR_OK || best >= 1e300) {
+    g_tune_nb = saved_nb;
+    g_tune_rows_min = saved_rows;
+    return st != SLQR_OK ? st : fail(ctx, SLQR_ECUDA, "autotune: no setting ran");
+  }
+  g_tune_nb = bw;
+  g_tune_rows_min = br;
+  if (best_ms) *best_ms = best;
+  if (best_panel_width) *best_panel_width = bw;
+  if (best_rows_min) *best_rows_min = br;
+  return SLQR_OK;
+}
+
 extern "C" size_t slqr_wy_size(int m, int n) {
   if (m <= 0 || n <= 0) return 0;
   int nb = panel_width(m, n);
