@@ -44,6 +44,14 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12
 CPU_SAMPLE_COLS = 512   # oracle sample: leading m x 512 block of each matrix
 # factorization-only timings reported beside the step (N(0,1), seeds 2, 3, 4)
 FACTOR_ONLY_SHAPES = [(16384, 2048, 2), (8192, 8192, 3), (8192, 4096, 4)]
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the two
+# trailing-update kernels, averaged over every launch of
+#   python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-mixed --no-serving
+# under ncu (one pass), beside the algorithmic bytes of the same launches
+# (vtx: 8 M (N + 64) read; upd: X read and written, V and W' read).  Reset to
+# None whenever either kernel changes.
+TRAFFIC_PER_LAUNCH = {"vtx": {"dram": 58.52e6, "algorithmic": 52.23e6},
+                      "upd": {"dram": 85.63e6, "algorithmic": 101.72e6}}
 
 
 def step_flops(shapes=SHAPES, nrhs=NRHS):
@@ -335,8 +343,12 @@ def run_ours(args, rank, world, local_rank):
     dom = max(("vtx", "upd"), key=lambda k: prof[k][0])
     dms, dn, dfl = prof[dom]
     achieved = (dfl / dn) / (dms / dn / 1e3) / 1e12 if dn else 0.0
+    tr = TRAFFIC_PER_LAUNCH.get(dom)
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": tr["dram"] if tr else None,
+                "traffic_algorithmic": tr["algorithmic"] if tr else None,
+                "traffic_unit": "bytes per launch (ncu, average over the launches of the FP64 bench command)",
                 "peak_source": "derived: FP64 FMA pipe 4 flop/clk/SM x 152 SMs x 2070 MHz"}
     kernels = {k: {"ms": v[0], "launches": v[1], "share_of_step_time": v[0] / max(1e-9, ms),
                    "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0}
