@@ -128,84 +128,6 @@ __global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ 
   if (i < n) x[i] = 0.0;
 }
 
-// One 64-row block step of an FP32 triangular solve with R = triu(A32[0:n,0:n])
-// (ld = lda).  UPPER: R y = c, blocks from the bottom; else R^T y = c, blocks
-// from the top.  CTA t updates row block t with the solution of block b_src,
-// and CTA t == b_diag then solves its diagonal block (one warp).
-template <bool UPPER>
-__global__ void __launch_bounds__(kThreads)
-trsv_f32_step_kernel(const float *__restrict__ R, int lda, int n, float *__restrict__ y,
-                     int t_first, int b_src, int b_diag, int *zero_flag) {
-  __shared__ float xs[64];
-  __shared__ float ys[64];
-  __shared__ float Rs[64][65];
-  const int t = t_first + blockIdx.x;
-  const int tid = threadIdx.x;
-  const int row_begin = t * 64;
-  const int rows = min(64, n - row_begin);
-  if (b_src >= 0) {
-    const int col_begin = b_src * 64;
-    const int cols = min(64, n - col_begin);
-    if (tid < 64) xs[tid] = (tid < cols) ? y[col_begin + tid] : 0.f;
-    __syncthreads();
-    // y[rows of t] -= M * xs with M = R[t rows, b_src cols] (UPPER) or
-    // R^T[t rows, b_src cols] = R[b_src rows, t cols]^T
-    const int r = tid & 63, part = tid >> 6;     // 4 threads per row
-    float acc = 0.f;
-    if (r < rows) {
-      for (int c = part; c < cols; c += 4) {
-        const float mv = UPPER ? R[SLQR_IDX(row_begin + r, col_begin + c, lda)]
-                               : R[SLQR_IDX(col_begin + c, row_begin + r, lda)];
-        acc = fmaf(mv, xs[c], acc);
-      }
-    }
-    __shared__ float red[4][64];
-    red[part][r] = acc;
-    __syncthreads();
-    if (tid < rows) y[row_begin + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-    __syncthreads();
-  }
-  if (t != b_diag) return;
-  for (int idx = tid; idx < 64 * 64; idx += kThreads) {
-    const int c = idx >> 6, r = idx & 63;
-    float v = 0.f;
-    if (r < rows && c < rows) {
-      // UPPER: Rs[r][c] = R[r, c] (r <= c); transposed: Rs[r][c] = R[c, r] (r >= c)
-      if (UPPER && r <= c) v = R[SLQR_IDX(row_begin + r, row_begin + c, lda)];
-      if (!UPPER && r >= c) v = R[SLQR_IDX(row_begin + c, row_begin + r, lda)];
-    }
-    Rs[r][c] = v;
-  }
-  if (tid < 64) ys[tid] = (tid < rows) ? y[row_begin + tid] : 0.f;
-  __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
-    float c0 = ys[lane], c1 = ys[lane + 32];
-    bool zero = false;
-    for (int s = 0; s < rows; ++s) {
-      const int i = UPPER ? rows - 1 - s : s;
-      const float ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
-      const float d = Rs[i][i];
-      float xi = 0.f;
-      if (d != 0.f) xi = ci / d;
-      else zero = true;
-      if (lane == (i & 31)) {
-        if (i < 32) c0 = xi; else c1 = xi;
-      }
-      if (UPPER) {
-        if (lane < i) c0 = fmaf(-Rs[lane][i], xi, c0);
-        if (lane + 32 < i) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
-      } else {
-        if (lane > i) c0 = fmaf(-Rs[lane][i], xi, c0);
-        if (lane + 32 > i && lane + 32 < rows) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
-      }
-    }
-    if (lane < rows) y[row_begin + lane] = c0;
-    if (lane + 32 < rows) y[row_begin + lane + 32] = c1;
-    if (zero && lane == 0) atomicExch(zero_flag, 1);
-  }
-}
-
 // --------------------------------------------------------------------------
 // Q^T f and Q f for one FP32 vector in a single cooperative launch.
 //
@@ -340,24 +262,125 @@ static size_t qvec_smem_bytes(int nb, int R) {
   return sizeof(float) * ((size_t)nb * (R + 1) + R + (size_t)nb * (nb + 1) + kThreads + 2 * nb);
 }
 
+// FP32 triangular solve with R = triu(A32[0:n, 0:n]) (ld lda) in one
+// cooperative launch.  UPPER: R y = c, 64-row blocks from the bottom; else
+// R^T y = c, blocks from the top.  CTA q owns the row blocks t = q (mod P).
+// Step b: the owner of block b solves its diagonal block (one warp, the
+// updates of every earlier step already applied to it), one grid barrier
+// publishes x_b, and every CTA subtracts R_tb x_b (or R_bt^T x_b) from each of
+// its blocks t still to be solved.  An exact zero on the diagonal sets that
+// entry of y to 0 and raises *zero_flag.
+struct TrsvParams {
+  const float *R;
+  float *y;
+  int *zero_flag;
+  unsigned *bar;
+  int *status;
+  int lda, n, nblk, P;
+  unsigned bar_base;
+};
+
+template <bool UPPER>
+__global__ void __launch_bounds__(kThreads)
+trsv_coop_kernel(TrsvParams p) {
+  __shared__ float Rs[64][65];
+  __shared__ float xs[64];
+  __shared__ float red[4][64];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, cta = blockIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int step = 0; step < p.nblk; ++step) {
+    const int b = UPPER ? p.nblk - 1 - step : step;
+    const int b0 = b * 64, rows = min(64, p.n - b0);
+    if (b % p.P == cta) {
+      // diagonal block: UPPER Rs[r][c] = R[r, c] (r <= c); else Rs[r][c] = R[c, r] (r >= c)
+      for (int idx = tid; idx < 64 * 64; idx += kThreads) {
+        const int c = idx >> 6, r = idx & 63;
+        float v = 0.f;
+        if (r < rows && c < rows) {
+          if (UPPER && r <= c) v = p.R[SLQR_IDX(b0 + r, b0 + c, p.lda)];
+          if (!UPPER && r >= c) v = p.R[SLQR_IDX(b0 + c, b0 + r, p.lda)];
+        }
+        Rs[r][c] = v;
+      }
+      if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : 0.f;
+      __syncthreads();
+      if (tid < 32) {
+        float c0 = xs[lane], c1 = xs[lane + 32];
+        bool zero = false;
+        for (int s = 0; s < rows; ++s) {
+          const int i = UPPER ? rows - 1 - s : s;
+          const float ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
+          const float d = Rs[i][i];
+          float xi = 0.f;
+          if (d != 0.f) xi = ci / d;
+          else zero = true;
+          if (lane == (i & 31)) {
+            if (i < 32) c0 = xi; else c1 = xi;
+          }
+          if (UPPER) {
+            if (lane < i) c0 = fmaf(-Rs[lane][i], xi, c0);
+            if (lane + 32 < i) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+          } else {
+            if (lane > i) c0 = fmaf(-Rs[lane][i], xi, c0);
+            if (lane + 32 > i && lane + 32 < rows) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+          }
+        }
+        if (lane < rows) p.y[b0 + lane] = c0;
+        if (lane + 32 < rows) p.y[b0 + lane + 32] = c1;
+        if (zero && lane == 0) atomicExch(p.zero_flag, 1);
+      }
+    }
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
+      return;
+    // x_b from the owner, then the updates of this CTA's remaining blocks
+    if (tid < 64) xs[tid] = (tid < rows) ? __ldcg(p.y + b0 + tid) : 0.f;
+    __syncthreads();
+    for (int t = cta; t < p.nblk; t += p.P) {
+      if (UPPER ? t >= b : t <= b) continue;
+      const int t0 = t * 64, trows = min(64, p.n - t0);
+      if (UPPER) {
+        // y_t -= R[t rows, b cols] x_b: thread (row r, quarter q) over columns c = q (mod 4)
+        const int r = tid & 63, q = tid >> 6;
+        float acc = 0.f;
+        if (r < trows)
+          for (int c = q; c < rows; c += 4) acc = fmaf(p.R[SLQR_IDX(t0 + r, b0 + c, p.lda)], xs[c], acc);
+        red[q][r] = acc;
+        __syncthreads();
+        if (tid < trows) p.y[t0 + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+        __syncthreads();
+      } else {
+        // y_t -= R[b rows, t cols]^T x_b: warp per output row, lanes over c (contiguous in R)
+        for (int r = warp; r < trows; r += kThreads / 32) {
+          float acc = 0.f;
+          for (int c = lane; c < rows; c += 32) acc = fmaf(p.R[SLQR_IDX(b0 + c, t0 + r, p.lda)], xs[c], acc);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) p.y[t0 + r] -= acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace slqr
 
 namespace slqr {
 
 template <bool UPPER>
-static void trsv_f32(const float *R, int lda, int n, float *y, int *zero_flag, cudaStream_t s) {
-  const int nblk = (n + 63) / 64;
-  if (UPPER) {
-    trsv_f32_step_kernel<true><<<1, kThreads, 0, s>>>(R, lda, n, y, nblk - 1, -1, nblk - 1,
-                                                      zero_flag);
-    for (int b = nblk - 1; b >= 1; --b)
-      trsv_f32_step_kernel<true><<<b, kThreads, 0, s>>>(R, lda, n, y, 0, b, b - 1, zero_flag);
-  } else {
-    trsv_f32_step_kernel<false><<<1, kThreads, 0, s>>>(R, lda, n, y, 0, -1, 0, zero_flag);
-    for (int b = 0; b + 1 < nblk; ++b)
-      trsv_f32_step_kernel<false><<<nblk - 1 - b, kThreads, 0, s>>>(R, lda, n, y, b + 1, b,
-                                                                    b + 1, zero_flag);
-  }
+static slqr_status trsv_f32(slqr_ctx *ctx, const float *R, int lda, int n, float *y, int *zero_flag,
+                            unsigned *bar, unsigned &bar_base, cudaStream_t s) {
+  TrsvParams tp;
+  tp.R = R; tp.y = y; tp.zero_flag = zero_flag; tp.bar = bar; tp.status = ctx->d_status;
+  tp.lda = lda; tp.n = n; tp.nblk = (n + 63) / 64;
+  tp.P = std::min(tp.nblk, ctx->num_sms);
+  tp.bar_base = bar_base;
+  void *args[] = {&tp};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)trsv_coop_kernel<UPPER>, dim3(tp.P),
+                                              dim3(kThreads), args, 0, s);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "triangular solve: %s", cudaGetErrorString(e));
+  bar_base += (unsigned)tp.nblk * (unsigned)tp.P;
+  return SLQR_OK;
 }
 
 }  // namespace slqr
@@ -457,11 +480,13 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
         A, lda, m, n, x, part);
     resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(b, r, part, chunks, m, f32);
     resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, r, g32);
-    trsv_f32<false>(A32, lda32, n, g32, zero_flag, s);                   // h = R^-T g
+    st = trsv_f32<false>(ctx, A32, lda32, n, g32, zero_flag, qbar, qbar_base, s);  // h = R^-T g
+    if (st != SLQR_OK) return st;
     st = apply_q(true);                                                 // d = Q^T f
     if (st != SLQR_OK) return st;
     form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(f32, g32, m, n, e32);
-    trsv_f32<true>(A32, lda32, n, e32, zero_flag, s);                    // dx = R^-1 (d1 - h)
+    st = trsv_f32<true>(ctx, A32, lda32, n, e32, zero_flag, qbar, qbar_base, s);   // dx = R^-1 (d1 - h)
+    if (st != SLQR_OK) return st;
     update_kernel<<<ublocks, 256, 0, s>>>(f32, g32, e32, x, n, maxima);  // d = [h; d2], x += dx
     st = apply_q(false);                                                // dr = Q [h; d2]
     if (st != SLQR_OK) return st;
