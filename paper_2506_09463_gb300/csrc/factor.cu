@@ -129,7 +129,11 @@ panel_kernel(PanelParams p) {
   T *Ps = (T *)smem_raw;                      // [NB][R] column-major panel slice
   double *Gloc = (double *)(smem_raw + ((size_t)NB * p.R * sizeof(T) + 15) / 16 * 16);
                                               // [NB][NB] local Gram terms
-  __shared__ double s_lane[NB][33];           // lane partials of phase 1
+  // lane partials of phase 1: the dots in the storage precision (an FP32
+  // factorization adds them on the FP32 pipe), the norm in FP64
+  using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+  __shared__ Acc s_lane[NB][33];
+  __shared__ double s_nlane[32];
   __shared__ double s_part[GROUPS][NB];
   __shared__ double s_sig[NB];                // sigma per column
   __shared__ double s_up[NB];
@@ -239,8 +243,9 @@ panel_kernel(PanelParams p) {
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
         const int c = warp + t * NW;
-        if (c < NB) s_lane[c][lane] = (c == j) ? nacc : (double)acc[t];
+        if (c < NB && c != j) s_lane[c][lane] = (Acc)acc[t];
       }
+      if (norm_warp) s_nlane[lane] = nacc;
       if (cta == 0 && tid < nbw) prow[tid] = (double)Ps[tid * R + j];
     }
     __syncthreads();
@@ -248,10 +253,17 @@ panel_kernel(PanelParams p) {
       // thread (c, quarter) sums 32 / LQ lane partials; then one thread per c
       const int c = tid / LQ, qq = tid - c * LQ;
       constexpr int LPQ = 32 / LQ;
-      double v = 0.0;
+      if (c == j) {
+        double v = 0.0;
 #pragma unroll
-      for (int l = 0; l < LPQ; ++l) v += s_lane[c][qq * LPQ + l];
-      s_part[qq][c] = v;
+        for (int l = 0; l < LPQ; ++l) v += s_nlane[qq * LPQ + l];
+        s_part[qq][c] = v;
+      } else {
+        Acc v = Acc(0);
+#pragma unroll
+        for (int l = 0; l < LPQ; ++l) v += s_lane[c][qq * LPQ + l];
+        s_part[qq][c] = (double)v;
+      }
     }
     __syncthreads();
     if (tid < nbw) {

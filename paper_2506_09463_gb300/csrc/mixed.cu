@@ -200,13 +200,46 @@ qvec_kernel(QvecParams p) {
     const double *Vtop = p.wy + (size_t)pnl * wy_panel_doubles(nb);
     const int lo = max(r0, k0), rows = max(0, r1 - lo);
     float *mypart = p.part + ((size_t)(step & 1) * p.P + cta) * nb;
-    // phase A: stage V and f of the slice, partial dots V^T f
-    for (int idx = tid; idx < nbw * rows; idx += kThreads) {
-      const int a = idx / rows, rr = idx - a * rows;
-      const int i = lo + rr, ii = i - k0;
-      Vs[a * (R + 1) + rr] = (ii < nbw) ? (float)Vtop[ii + a * nb] : p.A[SLQR_IDX(i, k0 + a, p.lda)];
+    // phase A: stage V and f of the slice, partial dots V^T f.  The slice
+    // starts on a multiple of 64 rows and the columns of A are 128-byte
+    // aligned, so whole rows of four go in one 16-byte load (8 in flight per
+    // thread); the panel's top rows are then taken from Vtop.
+    {
+      const int rows4 = rows >> 2, n4 = nbw * rows4;
+      for (int base = tid; base < n4; base += 8 * kThreads) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * kThreads;
+          if (idx < n4) {
+            const int a = idx / rows4, q = idx - a * rows4;
+            v[u] = __ldcs((const float4 *)(p.A + SLQR_IDX(lo + 4 * q, k0 + a, p.lda)));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * kThreads;
+          if (idx < n4) {
+            const int a = idx / rows4, q = idx - a * rows4;
+            float *dst = Vs + a * (R + 1) + 4 * q;
+            dst[0] = v[u].x; dst[1] = v[u].y; dst[2] = v[u].z; dst[3] = v[u].w;
+          }
+        }
+      }
+      for (int idx = tid; idx < nbw * (rows - 4 * rows4); idx += kThreads) {   // ragged rows
+        const int tail = rows - 4 * rows4, a = idx / tail, rr = 4 * rows4 + idx - a * tail;
+        Vs[a * (R + 1) + rr] = p.A[SLQR_IDX(lo + rr, k0 + a, p.lda)];
+      }
     }
     for (int rr = tid; rr < rows; rr += kThreads) fs[rr] = p.f[lo + rr];
+    __syncthreads();
+    if (lo < k0 + nbw) {                         // the panel's top rows: Vtop
+      const int top = min(k0 + nbw, r1) - lo;
+      for (int idx = tid; idx < nbw * top; idx += kThreads) {
+        const int a = idx / top, rr = idx - a * top;
+        Vs[a * (R + 1) + rr] = (float)Vtop[(lo + rr - k0) + a * nb];
+      }
+    }
     __syncthreads();
     {
       const int a = tid % nb, g = tid / nb, G = kThreads / nb;
@@ -422,7 +455,8 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   const size_t o_max = take((size_t)2 * ublocks * sizeof(double));
   const size_t o_flag = take(sizeof(int));
   // fused Q application: rows per CTA, explicit T per panel, partials, barrier
-  const int qv_R = std::max(kQvRows, (m + ctx->num_sms - 1) / ctx->num_sms);
+  // (a multiple of 64 rows: every slice starts 16-byte aligned for the vector loads)
+  const int qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
   const int qv_P = (m + qv_R - 1) / qv_R;
   const size_t o_tm = take((size_t)std::max(np, 1) * nb * (nb + 1) * sizeof(float));
   const size_t o_qpart = take((size_t)2 * qv_P * nb * sizeof(float));
