@@ -140,7 +140,7 @@ __global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ 
 // partials of all CTAs in the same fixed order, forms W' = T^T W (or T W) and
 // updates its own rows.  One barrier per panel instead of three launches.
 // --------------------------------------------------------------------------
-constexpr int kQvRows = 256;     // rows of f per CTA (at most)
+constexpr int kQvRows = 128;     // rows of f per CTA (at least; more CTAs when m is large)
 
 // T of panel p (float, ld nb + 1): column j solves U y = e_j by back
 // substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and
@@ -169,7 +169,7 @@ tmat_kernel(const double *__restrict__ wy, int nb, int K, float *__restrict__ Tm
 
 struct QvecParams {
   const float *A;        // FP32 factorization (H12 form), ld lda
-  const double *wy;      // compact-WY store (Vtop of each panel)
+  const double *up;      // pivot entries of the reflectors
   const float *Tm;       // explicit T of each panel, nb x nb, ld nb + 1
   float *f;              // the vector, m entries, updated in place
   float *part;           // 2 buffers x P CTAs x nb partial sums
@@ -185,25 +185,38 @@ __global__ void __launch_bounds__(kThreads)
 qvec_kernel(QvecParams p) {
   extern __shared__ __align__(16) float qv_smem[];
   const int nb = p.nb, R = p.R;
-  float *Vs = qv_smem;                          // [nb][R + 1]
+  const int tsz = nb * (nb + 1);                // one T (multiple of 4 floats)
+  float *Ts2 = qv_smem;                         // [2][nb][nb + 1], 16-byte aligned
+  float *Vs = Ts2 + 2 * tsz;                    // [nb][R + 1]
   float *fs = Vs + (size_t)nb * (R + 1);        // [R]
-  float *Ts = fs + R;                           // [nb][nb + 1]
-  float *red = Ts + (size_t)nb * (nb + 1);      // [kThreads / nb][nb]
+  float *red = fs + R;                          // [kThreads / nb][nb]
   float *ws = red + kThreads;                   // [nb]
   float *wt = ws + nb;                          // [nb]
   __shared__ int s_ok;
   const int tid = threadIdx.x, cta = blockIdx.x;
   const int r0 = cta * R, r1 = min(p.m, r0 + R);
+  // T of a panel into buffer `buf` with asynchronous 16-byte copies
+  auto fetch_t = [&](int step, int buf) {
+    if (step >= p.np) return;
+    const int pnl = p.trans ? step : p.np - 1 - step;
+    const float *src = p.Tm + (size_t)pnl * tsz;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ts2 + buf * tsz);
+    for (int c = tid; c < tsz / 4; c += kThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst + 16 * c), "l"(src + 4 * c)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  fetch_t(0, 0);
   for (int step = 0; step < p.np; ++step) {
     const int pnl = p.trans ? step : p.np - 1 - step;
+    float *Ts = Ts2 + (step & 1) * tsz;
     const int k0 = pnl * nb, nbw = min(nb, p.K - k0);
-    const double *Vtop = p.wy + (size_t)pnl * wy_panel_doubles(nb);
     const int lo = max(r0, k0), rows = max(0, r1 - lo);
     float *mypart = p.part + ((size_t)(step & 1) * p.P + cta) * nb;
     // phase A: stage V and f of the slice, partial dots V^T f.  The slice
     // starts on a multiple of 64 rows and the columns of A are 128-byte
     // aligned, so whole rows of four go in one 16-byte load (8 in flight per
-    // thread); the panel's top rows are then taken from Vtop.
+    // thread); the panel's top rows are then fixed up (0 above the diagonal, up on it).
     {
       const int rows4 = rows >> 2, n4 = nbw * rows4;
       for (int base = tid; base < n4; base += 8 * kThreads) {
@@ -233,11 +246,14 @@ qvec_kernel(QvecParams p) {
     }
     for (int rr = tid; rr < rows; rr += kThreads) fs[rr] = p.f[lo + rr];
     __syncthreads();
-    if (lo < k0 + nbw) {                         // the panel's top rows: Vtop
+    if (lo < k0 + nbw) {
+      // the panel's top rows: V is 0 above the diagonal and up on it (the
+      // tails below are the staged entries of A)
       const int top = min(k0 + nbw, r1) - lo;
       for (int idx = tid; idx < nbw * top; idx += kThreads) {
-        const int a = idx / top, rr = idx - a * top;
-        Vs[a * (R + 1) + rr] = (float)Vtop[(lo + rr - k0) + a * nb];
+        const int a = idx / top, rr = idx - a * top, ii = lo + rr - k0;
+        if (ii < a) Vs[a * (R + 1) + rr] = 0.f;
+        else if (ii == a) Vs[a * (R + 1) + rr] = (float)p.up[k0 + a];
       }
     }
     __syncthreads();
@@ -254,45 +270,71 @@ qvec_kernel(QvecParams p) {
         mypart[tid] = v;
       }
     }
-    for (int idx = tid; idx < nb * nb; idx += kThreads) {
-      const int i = idx % nb, j = idx / nb;
-      Ts[i + j * (nb + 1)] = p.Tm[(size_t)pnl * nb * (nb + 1) + i + j * (nb + 1)];
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");      // this panel's T has landed
     if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
       return;
-    // phase B: W (all CTAs, fixed order), then W' = T^T W or T W
-    if (tid < nb) {
-      const float *src = p.part + (size_t)(step & 1) * p.P * nb + tid;
-      float v = 0.f;
-      for (int q = 0; q < p.P; ++q) v += __ldcg(src + (size_t)q * nb);
-      ws[tid] = v;
+    fetch_t(step + 1, (step + 1) & 1);                   // the next panel's T, in flight
+    // phase B: W (all CTAs, fixed order: thread (a, g) sums the partials of
+    // CTAs g, g + G, .. with four loads in flight, then the G sums are added),
+    // then W' = T^T W or T W
+    {
+      const int a = tid % nb, g = tid / nb, G = kThreads / nb;
+      const float *src = p.part + (size_t)(step & 1) * p.P * nb + a;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+      int q = g;
+      for (; q + 3 * G < p.P; q += 4 * G) {
+        v0 += __ldcg(src + (size_t)q * nb);
+        v1 += __ldcg(src + (size_t)(q + G) * nb);
+        v2 += __ldcg(src + (size_t)(q + 2 * G) * nb);
+        v3 += __ldcg(src + (size_t)(q + 3 * G) * nb);
+      }
+      for (; q < p.P; q += G) v0 += __ldcg(src + (size_t)q * nb);
+      red[g * nb + a] = (v0 + v1) + (v2 + v3);
+      __syncthreads();
+      if (tid < nb) {
+        float v = 0.f;
+        for (int gg = 0; gg < G; ++gg) v += red[gg * nb + tid];
+        ws[tid] = v;
+      }
     }
     __syncthreads();
-    if (tid < nb) {
-      const int j = tid;
+    {
+      // W' entry j: four threads take every fourth term of its dot product
+      const int j = tid >> 2, part = tid & 3;
       float v = 0.f;
       if (j < nbw) {
         if (p.trans) {
-          for (int q = 0; q <= j; ++q) v = fmaf(Ts[q + j * (nb + 1)], ws[q], v);
+          for (int q = part; q <= j; q += 4) v = fmaf(Ts[q + j * (nb + 1)], ws[q], v);
         } else {
-          for (int q = j; q < nbw; ++q) v = fmaf(Ts[j + q * (nb + 1)], ws[q], v);
+          for (int q = j + part; q < nbw; q += 4) v = fmaf(Ts[j + q * (nb + 1)], ws[q], v);
         }
       }
-      wt[j] = v;
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (part == 0 && j < nb) wt[j] = v;
     }
     __syncthreads();
     // phase C: f -= V W' on the slice
-    for (int rr = tid; rr < rows; rr += kThreads) {
-      float v = fs[rr];
-      for (int a = 0; a < nbw; ++a) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
-      p.f[lo + rr] = v;
+    if (2 * rows <= kThreads) {                  // two threads per row, half the terms each
+      const int rr = tid >> 1, half = tid & 1;
+      float v = 0.f;
+      if (rr < rows)
+        for (int a = half; a < nbw; a += 2) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (rr < rows && half == 0) p.f[lo + rr] = fs[rr] + v;
+    } else {
+      for (int rr = tid; rr < rows; rr += kThreads) {
+        float v = fs[rr];
+        for (int a = 0; a < nbw; ++a) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
+        p.f[lo + rr] = v;
+      }
     }
     __syncthreads();
   }
 }
 
 static size_t qvec_smem_bytes(int nb, int R) {
-  return sizeof(float) * ((size_t)nb * (R + 1) + R + (size_t)nb * (nb + 1) + kThreads + 2 * nb);
+  return sizeof(float) * (2 * (size_t)nb * (nb + 1) + (size_t)nb * (R + 1) + R + kThreads + 2 * nb);
 }
 
 // FP32 triangular solve with R = triu(A32[0:n, 0:n]) (ld lda) in one
@@ -316,25 +358,48 @@ struct TrsvParams {
 template <bool UPPER>
 __global__ void __launch_bounds__(kThreads)
 trsv_coop_kernel(TrsvParams p) {
-  __shared__ float Rs[64][65];
+  __shared__ float Rs[64][65];      // diagonal block being solved
+  __shared__ float Tu[64][65];      // update tile, [c][r]: R[t r, b c] (UPPER) or R[b c, t r]
+  __shared__ float rdiag[64];
   __shared__ float xs[64];
   __shared__ float red[4][64];
   __shared__ int s_ok;
-  const int tid = threadIdx.x, cta = blockIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, cta = blockIdx.x, lane = tid & 31;
+  // with one block per CTA the diagonal block stays in shared memory throughout
+  const bool one = (p.P == p.nblk);
+  auto load_diag = [&](int b) {
+    const int b0 = b * 64, rows = min(64, p.n - b0);
+    for (int idx = tid; idx < 64 * 64; idx += kThreads) {
+      const int c = idx >> 6, r = idx & 63;
+      float v = 0.f;
+      if (r < rows && c < rows) {
+        if (UPPER && r <= c) v = p.R[SLQR_IDX(b0 + r, b0 + c, p.lda)];
+        if (!UPPER && r >= c) v = p.R[SLQR_IDX(b0 + c, b0 + r, p.lda)];
+      }
+      Rs[r][c] = v;
+    }
+    __syncthreads();
+    if (tid < 64) rdiag[tid] = (tid < rows && Rs[tid][tid] != 0.f) ? 1.f / Rs[tid][tid] : 0.f;
+    __syncthreads();
+  };
+  auto load_update = [&](int t, int b) {
+    const int t0 = t * 64, b0 = b * 64;
+    const int trows = min(64, p.n - t0), rows = min(64, p.n - b0);
+    for (int idx = tid; idx < 64 * 64; idx += kThreads) {
+      int r, c;
+      if (UPPER) { r = idx & 63; c = idx >> 6; } else { c = idx & 63; r = idx >> 6; }
+      float v = 0.f;
+      if (r < trows && c < rows)
+        v = UPPER ? p.R[SLQR_IDX(t0 + r, b0 + c, p.lda)] : p.R[SLQR_IDX(b0 + c, t0 + r, p.lda)];
+      Tu[c][r] = v;
+    }
+  };
+  if (one) load_diag(cta);
   for (int step = 0; step < p.nblk; ++step) {
     const int b = UPPER ? p.nblk - 1 - step : step;
     const int b0 = b * 64, rows = min(64, p.n - b0);
     if (b % p.P == cta) {
-      // diagonal block: UPPER Rs[r][c] = R[r, c] (r <= c); else Rs[r][c] = R[c, r] (r >= c)
-      for (int idx = tid; idx < 64 * 64; idx += kThreads) {
-        const int c = idx >> 6, r = idx & 63;
-        float v = 0.f;
-        if (r < rows && c < rows) {
-          if (UPPER && r <= c) v = p.R[SLQR_IDX(b0 + r, b0 + c, p.lda)];
-          if (!UPPER && r >= c) v = p.R[SLQR_IDX(b0 + c, b0 + r, p.lda)];
-        }
-        Rs[r][c] = v;
-      }
+      if (!one) load_diag(b);
       if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : 0.f;
       __syncthreads();
       if (tid < 32) {
@@ -343,10 +408,9 @@ trsv_coop_kernel(TrsvParams p) {
         for (int s = 0; s < rows; ++s) {
           const int i = UPPER ? rows - 1 - s : s;
           const float ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
-          const float d = Rs[i][i];
-          float xi = 0.f;
-          if (d != 0.f) xi = ci / d;
-          else zero = true;
+          const float rd = rdiag[i];
+          const float xi = ci * rd;
+          zero |= (rd == 0.f);
           if (lane == (i & 31)) {
             if (i < 32) c0 = xi; else c1 = xi;
           }
@@ -363,36 +427,29 @@ trsv_coop_kernel(TrsvParams p) {
         if (zero && lane == 0) atomicExch(p.zero_flag, 1);
       }
     }
+    // one block per CTA: its update tile does not depend on x_b, so it is
+    // loaded while the owner of block b solves
+    const bool upd_one = one && (UPPER ? cta < b : cta > b);
+    if (upd_one) load_update(cta, b);
     if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
       return;
-    // x_b from the owner, then the updates of this CTA's remaining blocks
     if (tid < 64) xs[tid] = (tid < rows) ? __ldcg(p.y + b0 + tid) : 0.f;
     __syncthreads();
     for (int t = cta; t < p.nblk; t += p.P) {
       if (UPPER ? t >= b : t <= b) continue;
-      const int t0 = t * 64, trows = min(64, p.n - t0);
-      if (UPPER) {
-        // y_t -= R[t rows, b cols] x_b: thread (row r, quarter q) over columns c = q (mod 4)
-        const int r = tid & 63, q = tid >> 6;
-        float acc = 0.f;
-        if (r < trows)
-          for (int c = q; c < rows; c += 4) acc = fmaf(p.R[SLQR_IDX(t0 + r, b0 + c, p.lda)], xs[c], acc);
-        red[q][r] = acc;
+      if (!one) {
+        load_update(t, b);
         __syncthreads();
-        if (tid < trows) p.y[t0 + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-        __syncthreads();
-      } else {
-        // y_t -= R[b rows, t cols]^T x_b: warp per output row, lanes over c (contiguous in R)
-        for (int r = warp; r < trows; r += kThreads / 32) {
-          float acc = 0.f;
-          for (int c = lane; c < rows; c += 32) acc = fmaf(p.R[SLQR_IDX(b0 + c, t0 + r, p.lda)], xs[c], acc);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) p.y[t0 + r] -= acc;
-        }
       }
+      const int t0 = t * 64, trows = min(64, p.n - t0);
+      const int r = tid & 63, q = tid >> 6;
+      float acc = 0.f;
+      for (int c = q; c < rows; c += 4) acc = fmaf(Tu[c][r], xs[c], acc);
+      red[q][r] = acc;
+      __syncthreads();
+      if (tid < trows) p.y[t0 + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -485,7 +542,7 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   auto apply_q = [&](bool trans) -> slqr_status {
     if (np == 0) return SLQR_OK;
     QvecParams qp;
-    qp.A = A32; qp.wy = wy; qp.Tm = Tm; qp.f = f32; qp.part = qpart; qp.bar = qbar;
+    qp.A = A32; qp.up = up; qp.Tm = Tm; qp.f = f32; qp.part = qpart; qp.bar = qbar;
     qp.status = ctx->d_status; qp.lda = lda32; qp.m = m; qp.K = K; qp.nb = nb; qp.np = np;
     qp.trans = trans ? 1 : 0; qp.R = qv_R; qp.P = qv_P; qp.bar_base = qbar_base;
     void *args[] = {&qp};
