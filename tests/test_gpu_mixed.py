@@ -52,6 +52,22 @@ def test_mixed_against_oracle(ctx, m, n, kappa):
     assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * kappa * EPS
 
 
+@pytest.mark.parametrize("m,n,prec", [(1001, 250, "fp32"), (1001, 250, "tf32"), (4099, 1030, "fp32"),
+                                      (4099, 1030, "tf32"), (130, 129, "fp32")])
+def test_mixed_ragged_shapes(ctx, m, n, prec):
+    """Panel width 32 (n <= 256), rows not a multiple of 4 or 64 (the vector
+    staging's ragged tail, a partial last slice), a partial last panel."""
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, 1e3, seed=m + 3 * n)
+    p = abi.SLQR_FP32 if prec == "fp32" else abi.SLQR_TF32
+    for b in (b_cons, b_rand):
+        st, its, err, x = mixed(ctx, A, b, p)
+        assert st == 0, (st, its, err)
+        x_o = oracle.lstsq(A.cpu().numpy(), b.cpu().numpy())[0]
+        rel = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= 1e-10, (rel, its, err)
+
+
 def test_mixed_reports_no_convergence_when_kappa_too_large(ctx):
     from paper_2506_09463_gb300 import abi
     A, b_cons, x_true, b_rand = workloads.conditioned_device(1000, 600, 1e10, seed=3)
