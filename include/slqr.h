@@ -126,6 +126,8 @@ slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double 
  *                   larger values put fewer CTAs on each panel
  * Changing the panel width changes slqr_panel_width and slqr_wy_size: set it
  * before allocating compact-WY stores, and not while calls are in flight.
+ * These overrides take precedence over the per-shape settings of
+ * slqr_autotune; slqr_set_tuning(0, 0) also forgets those.
  */
 void slqr_set_tuning(int panel_width, int panel_rows_min);
 
@@ -133,8 +135,12 @@ void slqr_set_tuning(int panel_width, int panel_rows_min);
  * Autotuner of those knobs for one problem shape: times slqr_factor of a
  * generic m x n scratch matrix (allocated and freed here) under panel width
  * 32 and 64 and rows-per-CTA minimum 0 (by panel height), 64, 96, 128, 192 and
- * 256, keeps the fastest with slqr_set_tuning (process-wide) and reports it.
- * Synchronous; takes about 24 factorizations of that shape.
+ * 256, and keeps the fastest in a process-wide table keyed by (m, n): later
+ * factorizations of exactly that shape (slqr_factor, slqr_factor_stacked,
+ * slqr_factor_noalloc, the FP32 factorization of slqr_lstsq_mixed) use it,
+ * other shapes keep the defaults.  Run it before allocating compact-WY stores
+ * for that shape (the panel width sets slqr_wy_size) and not while other calls
+ * are in flight.  Synchronous; takes about 24 factorizations of that shape.
  *   best_ms, best_panel_width, best_rows_min  HOST outputs, each may be NULL
  * Errors: SLQR_EINVAL (sizes), SLQR_ENOMEM (scratch), SLQR_ECUDA; on error
  * the previous tuning is kept.

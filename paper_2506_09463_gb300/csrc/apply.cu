@@ -175,6 +175,7 @@ using namespace slqr;
 extern "C" slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *A, int lda,
                                      const double *up, const double *wy, int nrhs, double *B,
                                      int ldb, void *stream) {
+  NvtxRange nvtx_range("slqr_apply_qt");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (m < 0 || n < 0 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 0 (m=%d n=%d)", m, n);
@@ -193,6 +194,7 @@ extern "C" slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *
 extern "C" slqr_status slqr_apply_qt_stacked(slqr_ctx *ctx, int n, int m_eq, const double *A,
                                              int lda, const double *up, const double *wy,
                                              int nrhs, double *B, int ldb, void *stream) {
+  NvtxRange nvtx_range("slqr_apply_qt_stacked");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);

@@ -721,6 +721,7 @@ extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m,
                                          double *const *A, const int *lda, double *const *up,
                                          double *const *b, int prec, int *status, double *err,
                                          void *stream) {
+  NvtxRange nvtx_range("slqr_batch_factor");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   return batch_launch(ctx, count, m, n, nullptr, A, lda, up, b, prec, status, err, stream);
@@ -731,6 +732,7 @@ extern "C" slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const
                                                  const int *lda, double *const *up,
                                                  double *const *b, int prec, int *status,
                                                  double *err, void *stream) {
+  NvtxRange nvtx_range("slqr_batch_factor_stacked");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);

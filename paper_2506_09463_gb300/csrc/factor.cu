@@ -33,6 +33,8 @@
 #include <cstdio>
 #include <cstdarg>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 namespace slqr {
@@ -650,6 +652,27 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 static int g_tune_nb = 0;
 static int g_tune_rows_min = 0;        // 0: chosen from the panel height (rows_min_auto)
 
+// Per-shape settings found by slqr_autotune, keyed by (m, n); the global
+// overrides of slqr_set_tuning take precedence.
+struct TuneEntry { int nb, rows_min; };
+static std::map<std::pair<int, int>, TuneEntry> g_tune_cache;
+static std::mutex g_tune_mu;
+
+static bool tune_lookup(int m, int n, TuneEntry *e) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find({m, n});
+  if (it == g_tune_cache.end()) return false;
+  *e = it->second;
+  return true;
+}
+
+// The rows-per-CTA minimum for an m x n factorization (0: by panel height).
+static int rows_min_for(int m, int n) {
+  if (g_tune_rows_min > 0) return g_tune_rows_min;
+  TuneEntry e;
+  return tune_lookup(m, n, &e) ? e.rows_min : 0;
+}
+
 // Smallest row slice per panel CTA when not set: small panels get more CTAs
 // (each column step then does less FP64 work per SM), tall ones fewer (they
 // share the SMs with the concurrent trailing update).  Measured on GB300:
@@ -658,8 +681,9 @@ static int g_tune_rows_min = 0;        // 0: chosen from the panel height (rows_
 static int rows_min_auto(int M) { return M < 1536 ? 64 : (M < 6144 ? 128 : 192); }
 
 int panel_width(int m, int n) {
-  (void)m;
   if (g_tune_nb == 32 || g_tune_nb == 64) return g_tune_nb;
+  TuneEntry e;
+  if (tune_lookup(m, n, &e)) return e.nb;
   return n <= 256 ? 32 : 64;
 }
 
@@ -816,11 +840,11 @@ slqr_status init_kernel_attrs(slqr_ctx *ctx) {
 // Rows per panel CTA: at least the tuning minimum, and enough that the panel
 // fits the small-grid kernel (at most 64 CTAs, fewer registers) whenever the
 // slice still fits shared memory (max_rows).
-static int panel_rows_per_cta(int M, int nbw, int num_sms, int max_rows) {
+static int panel_rows_per_cta(int M, int nbw, int num_sms, int max_rows, int rows_min) {
   const int ctas = std::min(num_sms, kMaxPanelCtas);
   int R = (M + ctas - 1) / ctas;
   R = std::max(R, nbw);
-  R = std::max(R, g_tune_rows_min > 0 ? g_tune_rows_min : rows_min_auto(M));
+  R = std::max(R, rows_min > 0 ? rows_min : rows_min_auto(M));
   const int r_small = (M + kSmallPanelCtas - 1) / kSmallPanelCtas;
   if (r_small <= max_rows) R = std::max(R, r_small);
   return R;
@@ -851,6 +875,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   const int K = num_reflectors(m, n);
   auto skip_of = [&](int k0, int nbw) { return ntop > 0 ? ntop - (k0 + nbw) : 0; };
   const int np = num_panels(K, NB);
+  const int rmin = rows_min_for(m, n);
   // workspace: [bar (256 B)] [records] [prow] [wy if none given] [trailing work]
   const int Pmax = ctx->num_sms;
   const size_t rec_doubles = 2 * (size_t)(NB + 2) * Pmax;
@@ -894,7 +919,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     const int nbw = std::min(NB, K - k0);
     const int skip = skip_of(k0, nbw);
     const int M = m - k0 - skip;
-    const int R = panel_rows_per_cta(M, nbw, Pmax, max_rows_per_cta(NB, sizeof(T)));
+    const int R = panel_rows_per_cta(M, nbw, Pmax, max_rows_per_cta(NB, sizeof(T)), rmin);
     if (R > max_rows_per_cta(NB, sizeof(T)))
       return fail(ctx, SLQR_EINVAL, "m = %d is too large for the shared-memory panel", m);
     const int P = (M + R - 1) / R;
@@ -978,6 +1003,10 @@ extern "C" int slqr_panel_width(int m, int n) { return panel_width(m, n); }
 extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
   g_tune_nb = (panel_width == 32 || panel_width == 64) ? panel_width : 0;
   g_tune_rows_min = panel_rows_min > 0 ? std::min(panel_rows_min, 1024) : 0;
+  if (g_tune_nb == 0 && g_tune_rows_min == 0) {      // back to the defaults
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+  }
 }
 
 namespace slqr {
@@ -1000,12 +1029,25 @@ __global__ void tune_fill_kernel(double *A, size_t count) {
 
 extern "C" slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_ms,
                                      int *best_panel_width, int *best_rows_min) {
+  NvtxRange nvtx_range("slqr_autotune");
   if (!ctx) return SLQR_EINVAL;
   if (m < 1 || n < 1 || m < n || m > slqr_max_rows())
     return fail(ctx, SLQR_EINVAL, "autotune: need 1 <= n <= m <= %d (m=%d n=%d)", slqr_max_rows(),
                 m, n);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  // measure without a previous entry for this shape (candidate 0 is "by panel height")
+  TuneEntry old_entry;
+  bool had_entry = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find({m, n});
+    if (it != g_tune_cache.end()) {
+      old_entry = it->second;
+      had_entry = true;
+      g_tune_cache.erase(it);
+    }
+  }
   const size_t count = (size_t)m * n;
   double *A0 = nullptr, *A = nullptr, *up = nullptr;
   cudaStream_t s = nullptr;
@@ -1027,6 +1069,10 @@ extern "C" slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_m
   if (e != cudaSuccess) {
     cudaGetLastError();
     cleanup();
+    if (had_entry) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[{m, n}] = old_entry;
+    }
     return fail(ctx, SLQR_ENOMEM, "autotune scratch: %s", cudaGetErrorString(e));
   }
   tune_fill_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A0, count);
@@ -1064,13 +1110,19 @@ extern "C" slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_m
     }
   }
   cleanup();
+  g_tune_nb = saved_nb;
+  g_tune_rows_min = saved_rows;
   if (st != SLQR_OK || best >= 1e300) {
-    g_tune_nb = saved_nb;
-    g_tune_rows_min = saved_rows;
+    if (had_entry) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[{m, n}] = old_entry;
+    }
     return st != SLQR_OK ? st : fail(ctx, SLQR_ECUDA, "autotune: no setting ran");
   }
-  g_tune_nb = bw;
-  g_tune_rows_min = br;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[{m, n}] = TuneEntry{bw, br};
+  }
   if (best_ms) *best_ms = best;
   if (best_panel_width) *best_panel_width = bw;
   if (best_rows_min) *best_rows_min = br;
@@ -1088,6 +1140,7 @@ extern "C" int slqr_max_rows(void) { return 49152; }
 
 extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double *up,
                                    double *wy, void *stream) {
+  NvtxRange nvtx_range("slqr_factor");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (m < 0 || n < 0 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 0 (m=%d n=%d)", m, n);
@@ -1104,6 +1157,7 @@ extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int l
 
 extern "C" slqr_status slqr_factor_stacked(slqr_ctx *ctx, int n, int m_eq, double *A, int lda,
                                            double *up, double *wy, void *stream) {
+  NvtxRange nvtx_range("slqr_factor_stacked");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);
@@ -1245,6 +1299,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
                                        cudaStream_t stream) {
   const int K = num_reflectors(m, n);
   const int np = num_panels(K, NB);
+  const int rmin = rows_min_for(m, n);
   unsigned *bar = (unsigned *)scratch;
   if (!status) status = (int *)(scratch + 16);
   double *rec = scratch + kNoAllocHeadDoubles;
@@ -1261,7 +1316,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     const int M = m - k0;
-    const int R = panel_rows_per_cta(M, nbw, num_sms, max_rows_per_cta(NB));
+    const int R = panel_rows_per_cta(M, nbw, num_sms, max_rows_per_cta(NB), rmin);
     if (R > max_rows_per_cta(NB)) return SLQR_EINVAL;
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
@@ -1294,6 +1349,7 @@ extern "C" int slqr_noalloc_max_cols(void) { return kNoAllocMaxCols; }
 
 extern "C" slqr_status slqr_factor_noalloc(int m, int n, double *A, int lda, double *up,
                                            double *wy, int *status, void *stream) {
+  NvtxRange nvtx_range("slqr_factor_noalloc");
   if (m < 0 || n < 0 || m < n) return SLQR_EINVAL;
   if (n == 0) return SLQR_OK;
   if (m > kNoAllocMaxRows || n > kNoAllocMaxCols) return SLQR_EINVAL;

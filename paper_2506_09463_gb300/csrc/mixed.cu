@@ -480,6 +480,7 @@ using namespace slqr;
 extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int lda,
                                         const double *b, double *x, int prec, int max_iter,
                                         double tol, int *iters, double *err, void *stream) {
+  NvtxRange nvtx_range("slqr_lstsq_mixed");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);

@@ -12,6 +12,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/slqr.h"
 
 #define SLQR_IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
@@ -77,6 +79,15 @@ struct slqr_ctx {
 };
 
 namespace slqr {
+
+// NVTX range over one entry point (visible in Nsight timelines; free when no
+// tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Record an error message in the context and return the status.
 slqr_status fail(slqr_ctx *ctx, slqr_status st, const char *fmt, ...);

@@ -146,6 +146,7 @@ using namespace slqr;
 
 extern "C" slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int lda, int nrhs,
                                     double *B, int ldb, void *stream) {
+  NvtxRange nvtx_range("slqr_solve_r");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (n < 0 || nrhs < 0) return fail(ctx, SLQR_EINVAL, "n=%d nrhs=%d must be >= 0", n, nrhs);

@@ -47,8 +47,12 @@ def test_autotune(ctx):
     st, ms, width, rows = abi.slqr_autotune(ctx.ctx, 1500, 1000)
     assert st == 0, abi.slqr_last_error(ctx.ctx)
     assert ms > 0 and width in (32, 64) and rows in (0, 64, 96, 128, 192, 256)
-    assert abi.slqr_panel_width(1500, 1000) == width          # the setting is kept
+    assert abi.slqr_panel_width(1500, 1000) == width          # kept for this shape
+    assert abi.slqr_panel_width(1500, 999) == 64              # other shapes: defaults
+    assert abi.slqr_panel_width(1500, 200) == 32
     factor_matches_oracle(ctx, 1500, 1000, seed=77)
+    abi.slqr_set_tuning(0, 0)                                  # forgets the table
+    assert abi.slqr_panel_width(1500, 1000) == 64
     assert abi.slqr_autotune(ctx.ctx, 10, 20)[0] == abi.SLQR_EINVAL
 
 
