@@ -89,6 +89,17 @@ const char *slqr_last_error(slqr_ctx *ctx);
 slqr_status slqr_sync(slqr_ctx *ctx, void *stream);
 
 /*
+ * Diagnostic of the failure path every device-side wait of the library takes
+ * (the panel's grid barrier, the tensor-core kernels' mbarrier waits): one
+ * thread polls a device word that nothing sets, gives up after `polls` polls
+ * (1 .. 2^20; about 0.3 us each), records SLQR_ETIMEOUT in the status word and
+ * returns.  Synchronous; returns the status word it read (SLQR_ETIMEOUT when
+ * the path works) and clears it, so the context stays usable.
+ * Errors: SLQR_EINVAL (polls out of range), SLQR_ECUDA.
+ */
+slqr_status slqr_check_bounded_wait(slqr_ctx *ctx, unsigned polls, void *stream);
+
+/*
  * Panel width the factorization uses for an m x n problem (columns per
  * compact-WY block).  It depends only on (m, n).
  */

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("slqr_destroy", None, [_vp]),
     ("slqr_last_error", ctypes.c_char_p, [_vp]),
     ("slqr_sync", _c_int, [_vp, _vp]),
+    ("slqr_check_bounded_wait", _c_int, [_vp, ctypes.c_uint, _vp]),
     ("slqr_panel_width", _c_int, [_c_int, _c_int]),
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
@@ -167,6 +168,10 @@ def slqr_autotune(ctx, m, n):
     ms, w, r = _dbl(), _c_int(), _c_int()
     st = _lib.slqr_autotune(ctx, m, n, ctypes.byref(ms), ctypes.byref(w), ctypes.byref(r))
     return st, ms.value, w.value, r.value
+
+
+def slqr_check_bounded_wait(ctx, polls, stream=None) -> int:
+    return _lib.slqr_check_bounded_wait(ctx, polls, stream)
 
 
 def slqr_factor(ctx, m, n, A, lda, up, wy, stream) -> int:

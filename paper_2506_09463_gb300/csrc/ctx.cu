@@ -178,6 +178,10 @@ extern "C" slqr_status slqr_create(slqr_ctx **out, int device, size_t hbm_budget
   ctx->smem_optin = (size_t)optin;
   if (init_kernel_attrs(ctx) != SLQR_OK || init_batch_attrs(ctx) != SLQR_OK ||
       init_tc_attrs(ctx) != SLQR_OK) {
+    cudaEventDestroy(ctx->ev_start);
+    cudaEventDestroy(ctx->ev_ready);
+    cudaEventDestroy(ctx->ev_panel);
+    cudaStreamDestroy(ctx->aux_stream);
     cudaFree(ctx->d_status);
     delete ctx;
     return SLQR_ECUDA;
@@ -203,6 +207,46 @@ extern "C" void slqr_destroy(slqr_ctx *ctx) {
   delete ctx;
 }
 
+namespace slqr {
+
+// A wait on a word that nothing sets, bounded by `polls`: the same give-up
+// path as the kernels' barrier and mbarrier waits (record SLQR_ETIMEOUT in
+// the status word, return).
+__global__ void wait_probe_kernel(const unsigned *word, unsigned polls, int *status) {
+  if (threadIdx.x != 0) return;
+  for (unsigned it = 0; ld_acquire_u32(word) == 0u; ++it) {
+    if (it >= polls) {
+      record_status(status, SLQR_ETIMEOUT);
+      return;
+    }
+    if (it > 64) __nanosleep(256);
+  }
+}
+
+}  // namespace slqr
+
+extern "C" slqr_status slqr_check_bounded_wait(slqr_ctx *ctx, unsigned polls, void *stream) {
+  if (!ctx || polls == 0 || polls > (1u << 20)) return SLQR_EINVAL;
+  NvtxRange nvtx_range("slqr_check_bounded_wait");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  unsigned *word = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&word, sizeof(unsigned));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(word, polls, ctx->d_status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (word) cudaFree(word);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "bounded-wait check: %s", cudaGetErrorString(e));
+  return st;
+}
+
 extern "C" const char *slqr_last_error(slqr_ctx *ctx) {
   if (!ctx) return "NULL context";
   return ctx->last_error.c_str();
@@ -217,10 +261,6 @@ extern "C" slqr_status slqr_sync(slqr_ctx *ctx, void *stream) {
   int st = 0;
   e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "status word: %s", cudaGetErrorString(e));
   if (st != 0) {
     if (st == SLQR_ERANK) fail(ctx, st, "R has an exact zero on its diagonal");

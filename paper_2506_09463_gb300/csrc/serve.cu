@@ -426,7 +426,7 @@ static slqr_status server_start(slqr_ctx *ctx) {
   if (!S) return SLQR_ENOMEM;
   S->owner = ctx;
   S->device = ctx->device;
-  S->nstreams = 4;
+  S->nstreams = 8;   // measured: about 8% more mid-size requests per second than 4; 16 no better
   cudaSetDevice(ctx->device);
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
