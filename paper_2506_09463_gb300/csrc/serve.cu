@@ -439,12 +439,25 @@ static slqr_status server_start(slqr_ctx *ctx) {
   }
   uint64_t keep = UINT64_MAX;
   cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  // on a failed set-up, release what was made so far
+  auto undo = [&]() {
+    for (slqr_ctx *c : S->sub) slqr_destroy(c);
+    for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+    for (int pi = 0; pi < 2; ++pi) {
+      if (S->bctx[pi]) slqr_destroy(S->bctx[pi]);
+      if (S->bstream[pi]) cudaStreamDestroy(S->bstream[pi]);
+    }
+    cudaMemPoolDestroy(S->pool);
+    delete S;
+  };
   for (int i = 0; i < S->nstreams; ++i) {
-    cudaStream_t s;
+    cudaStream_t s = nullptr;
     slqr_ctx *c = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
         slqr_create(&c, ctx->device, 0) != SLQR_OK) {
       cudaGetLastError();
+      if (s) cudaStreamDestroy(s);
+      undo();
       return fail(ctx, SLQR_ECUDA, "server stream set-up failed");
     }
     S->streams.push_back(s);
@@ -454,6 +467,7 @@ static slqr_status server_start(slqr_ctx *ctx) {
     if (cudaStreamCreateWithFlags(&S->bstream[pi], cudaStreamNonBlocking) != cudaSuccess ||
         slqr_create(&S->bctx[pi], ctx->device, 0) != SLQR_OK) {
       cudaGetLastError();
+      undo();
       return fail(ctx, SLQR_ECUDA, "server batch stream set-up failed");
     }
   }
