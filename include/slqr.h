@@ -263,6 +263,10 @@ slqr_status slqr_apply_qt_stacked(slqr_ctx *ctx, int n, int m_eq, const double *
                          update (W = V^T X and X -= V W') on the tensor cores
                          (tcgen05, TF32 operands, FP32 accumulation)
                          (slqr_lstsq_mixed only)                                  */
+#define SLQR_BF16X3 3 /* as SLQR_TF32 with BF16 operands split in two,
+                         x = hi + lo (about 16 significant bits), three MMAs per
+                         product (hi hi + hi lo + lo hi), FP32 accumulation
+                         (slqr_lstsq_mixed only)                                  */
 slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int *n,
                               double *const *A, const int *lda, double *const *up,
                               double *const *b, int prec, int *status, double *err,
@@ -293,9 +297,11 @@ slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const int *n, co
  * and corrections through the FP32 factorization.
  *   A      device, m x n column-major FP64, lda >= m, m >= n >= 1 (read only)
  *   b      device, m doubles (read only);  x  device, n doubles (output)
- *   prec   SLQR_FP32 (trailing-update products on the FP32 FMA pipe) or
+ *   prec   SLQR_FP32 (trailing-update products on the FP32 FMA pipe),
  *          SLQR_TF32 (W = V^T X and X -= V W' on the tensor cores, TF32
- *          operands: refinement then converges for kappa well below 2^11)
+ *          operands: refinement then converges for kappa well below 2^11) or
+ *          SLQR_BF16X3 (the same products with hi + lo BF16 operands, about
+ *          2^-15 per product: refinement converges for kappa well below 2^15)
  *   max_iter  refinement sweeps (<= 0: 30);  tol  stop at ||dx||_inf <=
  *          tol ||x||_inf (<= 0: 1e-14)
  *   iters, err  HOST ints/doubles or NULL: sweeps done and the last

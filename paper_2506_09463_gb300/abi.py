@@ -101,6 +101,7 @@ KERNEL_NAMES = ["panel", "vtx", "tw", "upd", "wy_rebuild", "trsm", "batch"]
 SLQR_FP64 = 0
 SLQR_FP32 = 1
 SLQR_TF32 = 2
+SLQR_BF16X3 = 3
 SLQR_DENSE = 0
 SLQR_STACKED = 1
 

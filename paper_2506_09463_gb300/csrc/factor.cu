@@ -732,17 +732,36 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   int slot = prof_begin(ctx, stream);
   int slices = 0;
   bool tc = false;
+  // tensor-core mode of an FP32 factorization (0 FMA, 1 TF32, 2 BF16 hi + lo)
+  const int mode = std::is_same<T, float>::value ? ctx->tc_mode : 0;
+  // BF16 mode: an update done on the FMA pipe refreshes the shadows it changed
+  auto refresh_shadows = [&]() {
+    if constexpr (std::is_same<T, float>::value) {
+      if (mode == 2 && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
+        const int xcol0 = (int)((X - A) / lda);
+        split_bf16_region((const float *)A, lda, k0, m, xcol0, xcol0 + N, ctx->sh_hi, ctx->sh_lo,
+                          ctx->num_sms, stream);
+      }
+    }
+  };
   if constexpr (std::is_same<T, float>::value && NB == 64) {
-    // TF32 path: both products on the tensor cores for a full panel whose X
-    // lies in A (the factorization); W'^T and a row-major V follow the partials
-    if (ctx->use_tc && TRANS && skip == 0 && nbw == 64 && ldx == lda &&
+    // tensor-core path: both products on the tensor cores for a full panel
+    // whose X lies in A (the factorization); W'^T and a row-major V follow
+    // the partials
+    if (mode != 0 && TRANS && skip == 0 && nbw == 64 && ldx == lda &&
         X >= A + (size_t)lda * (k0 + nbw)) {
       const int xcol0 = (int)((X - A) / lda);
-      slices = launch_vtx_tc(A, lda, Vtop, k0, M, xcol0, N, Wp, work_elems, ctx->num_sms,
-                             ctx->d_status, stream, &vtop_part_f32);
+      if (mode == 2)
+        slices = launch_vtx_bf16(A, lda, ctx->sh_hi, ctx->sh_lo, Vtop, k0, M, xcol0, N, Wp,
+                                 work_elems, ctx->num_sms, ctx->d_status, stream, &vtop_part_f32);
+      else
+        slices = launch_vtx_tc(A, lda, Vtop, k0, M, xcol0, N, Wp, work_elems, ctx->num_sms,
+                               ctx->d_status, stream, &vtop_part_f32);
       if (slices > 0) {
         Wt = work + (size_t)slices * N * NB;
-        tc = (size_t)slices * N * NB + (size_t)NB * N + (size_t)M * NB <= work_elems;
+        // scratch after W'^T: the row-major V (TF32), or the hi / lo pairs of V and W'
+        const size_t scratch = (mode == 2) ? (size_t)(M + N) * NB : (size_t)M * NB;
+        tc = (size_t)slices * N * NB + (size_t)NB * N + scratch <= work_elems;
         if (!tc) {                                  // partials only: finish on the FMA pipe
           prof_end(ctx, stream, slot, kVtx, gemm_flops);
           slot = prof_begin(ctx, stream);
@@ -752,6 +771,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
           gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads,
                                    (size_t)NB * (kBM + kBN) * sizeof(T), stream>>>(
               A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+          refresh_shadows();
           prof_end(ctx, stream, slot, kUpd, gemm_flops);
           return check_launch(ctx, "trailing update");
         }
@@ -774,15 +794,22 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   if constexpr (std::is_same<T, float>::value) {
     if (tc) {
       const int xcol0 = (int)((X - A) / lda);
-      done = launch_upd_tc((const float *)A, lda, Vtop, k0, M, xcol0, N, (const float *)Wt,
-                           (float *)(Wt + (size_t)NB * N), ctx->d_status, stream);
+      if (mode == 2)
+        done = launch_upd_bf16((const float *)A, lda, ctx->sh_hi, ctx->sh_lo, Vtop, k0, M, xcol0,
+                               N, (const float *)Wt, (void *)(Wt + (size_t)NB * N), ctx->num_sms,
+                               ctx->d_status, stream);
+      else
+        done = launch_upd_tc((const float *)A, lda, Vtop, k0, M, xcol0, N, (const float *)Wt,
+                             (float *)(Wt + (size_t)NB * N), ctx->d_status, stream);
       if (!done)                                    // no tensor map: W' again in FMA layout
         launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
     }
   }
-  if (!done)
+  if (!done) {
     gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
         A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt, skip);
+    refresh_shadows();
+  }
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
   return check_launch(ctx, "trailing update");
 }
@@ -883,8 +910,9 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   const size_t prow_doubles = 2 * (size_t)NB;
   const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
   // (the FP32 path also keeps a row-major copy of V for the tensor-core update)
+  // (the FP32 path also keeps a row-major V, or the BF16 pairs of V and W')
   const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms) +
-                              (std::is_same<T, float>::value ? (size_t)m * NB : 0);
+                              (std::is_same<T, float>::value ? (size_t)(m + n) * NB : 0);
   const size_t bytes = 256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles) * 8 +
                        work_doubles * sizeof(T) + 256;
   slqr_status st = ensure_workspace(ctx, bytes);
@@ -942,6 +970,12 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     if (le != cudaSuccess)
       return fail(ctx, SLQR_ECUDA, "panel launch (P=%d, smem=%zu): %s", P, smem,
                   cudaGetErrorString(le));
+    if constexpr (std::is_same<T, float>::value) {
+      // BF16 mode: the panel's columns (the reflectors) into the shadows
+      if (ctx->tc_mode == 2)
+        split_bf16_region((const float *)A, lda, k0, m, k0, k0 + nbw, ctx->sh_hi, ctx->sh_lo,
+                          ctx->num_sms, s);
+    }
     bar_base += (unsigned)P * (unsigned)(nbw + 2);
     return SLQR_OK;
   };

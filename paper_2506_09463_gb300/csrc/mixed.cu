@@ -486,7 +486,7 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);
   if (lda < m || !A || !b || !x) return fail(ctx, SLQR_EINVAL, "bad lda or NULL pointer");
   if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
-  if (prec != SLQR_FP32 && prec != SLQR_TF32)
+  if (prec != SLQR_FP32 && prec != SLQR_TF32 && prec != SLQR_BF16X3)
     return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
   if (max_iter < 1) max_iter = 30;
   if (!(tol > 0.0)) tol = 1e-14;
@@ -519,6 +519,10 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   const size_t o_tm = take((size_t)std::max(np, 1) * nb * (nb + 1) * sizeof(float));
   const size_t o_qpart = take((size_t)2 * qv_P * nb * sizeof(float));
   const size_t o_bar = take(256);
+  // BF16 hi / lo shadows of the FP32 matrix (SLQR_BF16X3)
+  const size_t sh_bytes = (prec == SLQR_BF16X3) ? (size_t)lda32 * n * 2 : 0;
+  const size_t o_shh = take(sh_bytes);
+  const size_t o_shl = take(sh_bytes);
   slqr_status st = ensure_workspace2(ctx, off);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws2.ptr;
@@ -556,9 +560,15 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
   };
 
   to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32, lda32);
-  ctx->use_tc = (prec == SLQR_TF32);
+  ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
+  if (prec == SLQR_BF16X3) {
+    ctx->sh_hi = base + o_shh;
+    ctx->sh_lo = base + o_shl;
+    split_bf16_region(A32, lda32, 0, m, 0, n, ctx->sh_hi, ctx->sh_lo, ctx->num_sms, s);
+  }
   st = factor_f32(ctx, m, n, A32, lda32, up, wy, s);
-  ctx->use_tc = false;
+  ctx->tc_mode = 0;
+  ctx->sh_hi = ctx->sh_lo = nullptr;
   if (st != SLQR_OK) return st;
   if (np > 0) tmat_kernel<<<np, 64, 0, s>>>(wy, nb, K, Tm);
   cudaMemsetAsync(qbar, 0, 256, s);

@@ -73,7 +73,10 @@ struct slqr_ctx {
   cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_panel = nullptr;
   long long launch_count = 0;          // kernels launched by this context
   slqr::Server *server = nullptr;      // request loop (slqr_submit), started lazily
-  bool use_tc = false;                 // FP32 factorization: trailing update on tcgen05 (TF32)
+  // FP32 factorization: trailing update on tcgen05 (0: FMA pipe, 1: TF32,
+  // 2: BF16 split in hi + lo, with the BF16 shadows of the matrix below)
+  int tc_mode = 0;
+  void *sh_hi = nullptr, *sh_lo = nullptr;
   std::string last_error;
   std::mutex mu;
 };
@@ -120,6 +123,19 @@ slqr_status init_tc_attrs(slqr_ctx *ctx);
 // a tensor map cannot be encoded; see tc_update.cu.
 bool launch_upd_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,
                    const float *Wt, float *Vr, int *status, cudaStream_t stream);
+// The BF16-split (hi + lo) variants (tc_bf16.cu): shadows of a region of the
+// FP32 matrix, and the two products reading / writing those shadows.
+slqr_status init_bf16_attrs(slqr_ctx *ctx);
+void split_bf16_region(const float *A, int lda, int r0, int r1, int c0, int c1, void *hi,
+                       void *lo, int num_sms, cudaStream_t stream);
+int launch_vtx_bf16(const float *A, int lda, const void *sh_hi, const void *sh_lo,
+                    const double *Vtop, int k0, int M, int xcol0, int N, float *Wp,
+                    size_t work_elems, int num_sms, int *status, cudaStream_t stream,
+                    void (*vtop_part)(const float *, int, const double *, int, int, const float *,
+                                      int, int, float *, cudaStream_t));
+bool launch_upd_bf16(const float *A, int lda, void *sh_hi, void *sh_lo, const double *Vtop,
+                     int k0, int M, int xcol0, int N, const float *Wt, void *scratch,
+                     int num_sms, int *status, cudaStream_t stream);
 // W = V^T X partials with TMA + tcgen05 for a full 64-wide panel; returns the
 // number of partial slices written to Wp (0: not applicable).
 int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, int xcol0, int N,

@@ -11,33 +11,14 @@
 // bounded wait the four warps read the accumulator back with tcgen05.ld (warp
 // w owns TMEM lanes 32w..32w+31).  TF32 keeps 10 mantissa bits of each
 // operand; the products accumulate in FP32.
-#include "slqr_internal.cuh"
+#include "tc_common.cuh"
 
-#include <cuda.h>   // CUtensorMap and its enums (types only: the encoder is fetched at run time)
 #include <algorithm>
-#include <cstdint>
-#include <mutex>
 
 namespace slqr {
 
 constexpr int kTcTile = 128;              // M = N = 128
 constexpr int kTcThreads = 128;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major operand, SWIZZLE_128B, 8-row
-// groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
-  return d;
-}
 
 // --------------------------------------------------------------------------
 // W = V^T X on the tensor cores: partial sums over row slices, TMA-fed.
@@ -58,25 +39,6 @@ constexpr int kVxBytesA = kTcTile * kVxChunk * 4;   // 16 KB
 constexpr int kVxBytesB = 64 * kVxChunk * 4;        // 8 KB
 constexpr uint32_t kIdescTf32N64 = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
                                    ((uint32_t)(kTcTile >> 4) << 24);
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t done = 0;
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.b32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-    if (done) return true;
-    if (it > 64) __nanosleep(32);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-               " [%0], [%1, {%2, %3}], [%4];"
-               :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
-}
 
 // grid: (ceil(N / 128), S); slice s covers rows [row_first + s*RS, ...) of the
 // panel (relative to k0), RS a multiple of 32; partial s+1 of Wp ([s][c][a]).
@@ -326,42 +288,6 @@ upd_tc_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ 
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kUpN));
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn tensor_map_encoder() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-    cudaGetLastError();
-  });
-  return fn;
-}
-
-// 2-D map of an FP32 matrix whose dim0 is contiguous (a column-major matrix:
-// dim0 = rows; a row-major one: dim0 = columns), zero fill outside it.
-static bool make_map(CUtensorMap *map, const float *base, int dim0, int dim1, int ld, int box0,
-                     int box1, bool swizzle = true) {
-  EncodeTiledFn enc = tensor_map_encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE,
-             swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // W = V^T X partials for a full 64-reflector panel of the FP32 matrix A

@@ -139,3 +139,46 @@ def test_tf32_full_size_8192x4096(ctx):
     st, its, err, x = mixed(ctx, A, b_cons, abi.SLQR_TF32)
     assert st == 0, (st, its, err)
     assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * 1e2 * EPS
+
+
+# --------------------------------------------------------------------------
+# BF16 hi + lo tensor-core trailing update (tcgen05 kind::f16, three MMAs per
+# product): about 2^-15 per product, so refinement converges beyond the TF32
+# range (kappa 1e4 here) in fewer sweeps, and reports SLQR_ENOCONV at 1e10.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n,kappa", [(1200, 800, 1e2), (1200, 800, 1e4), (700, 700, 1e3),
+                                       (3000, 300, 1e4), (4099, 1030, 1e3), (1001, 250, 1e3)])
+def test_bf16x3_against_oracle(ctx, m, n, kappa):
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa, seed=int(m + 5 * n))
+    for b in (b_cons, b_rand):
+        st, its, err, x = mixed(ctx, A, b, abi.SLQR_BF16X3)
+        assert st == 0, (st, its, err)
+        x_o = oracle.lstsq(A.cpu().numpy(), b.cpu().numpy())[0]
+        rel = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= max(1e-10, 1e3 * kappa * EPS), (rel, its, err)
+
+
+def test_bf16x3_fewer_sweeps_than_tf32(ctx):
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(1500, 1000, 1e2, seed=9)
+    st_t, its_t, _, _ = mixed(ctx, A, b_rand, abi.SLQR_TF32)
+    st_b, its_b, _, _ = mixed(ctx, A, b_rand, abi.SLQR_BF16X3)
+    assert st_t == 0 and st_b == 0
+    assert its_b < its_t, (its_b, its_t)
+
+
+def test_bf16x3_reports_no_convergence_when_kappa_too_large(ctx):
+    from paper_2506_09463_gb300 import abi
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(1000, 600, 1e10, seed=3)
+    st, its, err, x = mixed(ctx, A, b_rand, abi.SLQR_BF16X3)
+    assert st == abi.SLQR_ENOCONV
+
+
+def test_bf16x3_full_size_8192x4096(ctx):
+    from paper_2506_09463_gb300 import abi
+    m, n = 8192, 4096
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, 1e2)
+    st, its, err, x = mixed(ctx, A, b_cons, abi.SLQR_BF16X3)
+    assert st == 0, (st, its, err)
+    assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * 1e2 * EPS
