@@ -438,6 +438,19 @@ def run_mixed_workload(ctx, device, stream, barrier, kappas=(1e2, 1e6, 1e10), m=
             r.update({"tf32_tc_ms": tt, "tf32_status": abi.STATUS_NAMES.get(st2, st2),
                       "tf32_refine_iters": its2, "tf32_refine_last_step": err2,
                       "tf32_vs_fp64_rel": float(torch.linalg.norm(xt - x64) / torch.linalg.norm(x64))})
+            # and with BF16 operands split into hi + lo on the tensor cores
+            xb = torch.zeros(n, dtype=torch.float64, device=device)
+            barrier()
+            e0.record(stream)
+            st3, its3, err3 = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
+                                                   xb.data_ptr(), abi.SLQR_BF16X3, 0, 0.0,
+                                                   stream.cuda_stream)
+            e1.record(stream)
+            barrier()
+            tb = e0.elapsed_time(e1)
+            r.update({"bf16x3_tc_ms": tb, "bf16x3_status": abi.STATUS_NAMES.get(st3, st3),
+                      "bf16x3_refine_iters": its3, "bf16x3_refine_last_step": err3,
+                      "bf16x3_vs_fp64_rel": float(torch.linalg.norm(xb - x64) / torch.linalg.norm(x64))})
             if name == "consistent":
                 r["fp64_err_vs_x_true"] = float(torch.linalg.norm(x64 - x_true) / torch.linalg.norm(x_true))
                 r["mixed_err_vs_x_true"] = float(torch.linalg.norm(xm - x_true) / torch.linalg.norm(x_true))
@@ -640,10 +653,11 @@ def run_tune():
     return 0
 
 
-def run_ncu_mixed(m, n):
-    """Two TF32 mixed-precision LS solves of an iid N(0,1) m x n matrix: a
-    small program for ncu captures of the tensor-core kernels (no torch.linalg
-    call, which does not load under the profiler)."""
+def run_ncu_mixed(m, n, prec_name="tf32"):
+    """Two tensor-core mixed-precision LS solves (TF32 or BF16 hi + lo) of an
+    iid N(0,1) m x n matrix: a small program for ncu captures of the
+    tensor-core kernels (no torch.linalg call, which does not load under the
+    profiler)."""
     import torch
     import workloads
     from paper_2506_09463_gb300 import abi, api
@@ -654,8 +668,9 @@ def run_ncu_mixed(m, n):
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     with api.Context(0) as ctx:
         for _ in range(2):
+            prec = abi.SLQR_BF16X3 if prec_name == "bf16x3" else abi.SLQR_TF32
             st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
-                                                x.data_ptr(), abi.SLQR_TF32, 0, 0.0,
+                                                x.data_ptr(), prec, 0, 0.0,
                                                 torch.cuda.current_stream().cuda_stream)
             if st != 0:
                 raise RuntimeError(f"mixed status {st}")
@@ -727,6 +742,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream workload")
     ap.add_argument("--ncu-mixed", type=int, nargs=2, metavar=("M", "N"),
                     help="run one TF32 mixed-precision solve for profiling and exit")
+    ap.add_argument("--ncu-prec", default="tf32", choices=["tf32", "bf16x3"],
+                    help="tensor-core precision of --ncu-mixed")
     ap.add_argument("--ncu-batch", type=int, metavar="COUNT",
                     help="run one FP64 and one FP32 batch for profiling and exit")
     ap.add_argument("--tune", action="store_true",
@@ -739,7 +756,7 @@ def main():
     if args.tune:
         return run_tune()
     if args.ncu_mixed:
-        return run_ncu_mixed(*args.ncu_mixed)
+        return run_ncu_mixed(*args.ncu_mixed, prec_name=args.ncu_prec)
     if args.ncu_batch:
         return run_ncu_batch(args.ncu_batch)
     rank = int(os.environ.get("RANK", "0"))
