@@ -578,6 +578,65 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
         else:
             x64 = b_flat.clone()
         out[name] = rec
+    # the same FP64 batch as a plan (problem table uploaded once, CUDA-graph launch)
+    stp, plan = abi.slqr_batch_plan_create(ctx.ctx, list(ms), list(ns), None, A_ptrs, lda,
+                                           up_ptrs, b_ptrs, abi.SLQR_FP64, status.data_ptr(),
+                                           None)
+    abi.check(ctx.ctx, stp, "slqr_batch_plan_create")
+    times = []
+    for rep in range(reps + 1):
+        A_flat.copy_(A0)
+        b_flat.copy_(b0)
+        barrier()
+        e0.record(stream)
+        abi.check(ctx.ctx, abi.slqr_batch_plan_launch(plan, stream.cuda_stream), "plan launch")
+        e1.record(stream)
+        barrier()
+        if rep:
+            times.append(e0.elapsed_time(e1))
+    abi.slqr_batch_plan_destroy(plan)
+    out["fp64_plan"] = {"ms": min(times), "problems_per_s": count / (min(times) / 1e3),
+                        "ok": int(np.sum(status.cpu().numpy() == 0))}
+    # per-call latency of a small batch (256 problems, m ~ U{16..64}) from the
+    # host: slqr_batch_factor (table built and uploaded per call) against a plan
+    import time as _time
+    sms, sns = workloads.batch_shapes(256, seed=71, m_lo=16, m_hi=64)
+    SA, Sb, sa_off, sb_off = workloads.batch_problems_device(sms, sns, 71, device=device)
+    SA0, Sb0 = SA.clone(), Sb.clone()
+    sup = torch.zeros(int(sns.sum()) + 1, dtype=torch.float64, device=device)
+    sup_off = np.concatenate([[0], np.cumsum(sns)[:-1]])
+    sargs = ([int(m) for m in sms], [int(n) for n in sns],
+             [SA.data_ptr() + int(o) * 8 for o in sa_off], [int(m) for m in sms],
+             [sup.data_ptr() + int(o) * 8 for o in sup_off],
+             [Sb.data_ptr() + int(o) * 8 for o in sb_off])
+    sstat = torch.zeros(256, dtype=torch.int32, device=device)
+    small = {}
+    for mode in ("batch_factor", "plan"):
+        if mode == "plan":
+            stp, splan = abi.slqr_batch_plan_create(ctx.ctx, sargs[0], sargs[1], None, sargs[2],
+                                                    sargs[3], sargs[4], sargs[5], abi.SLQR_FP64,
+                                                    sstat.data_ptr(), None)
+            abi.check(ctx.ctx, stp, "slqr_batch_plan_create")
+        lat = []
+        for rep in range(21):
+            SA.copy_(SA0)
+            Sb.copy_(Sb0)
+            torch.cuda.synchronize()
+            t0 = _time.perf_counter()
+            if mode == "plan":
+                st = abi.slqr_batch_plan_launch(splan, stream.cuda_stream)
+            else:
+                st = abi.slqr_batch_factor(ctx.ctx, *sargs, abi.SLQR_FP64, sstat.data_ptr(), None,
+                                           stream.cuda_stream)
+            abi.check(ctx.ctx, st, mode)
+            torch.cuda.synchronize()
+            if rep:
+                lat.append((_time.perf_counter() - t0) * 1e3)
+        if mode == "plan":
+            abi.slqr_batch_plan_destroy(splan)
+        small[mode] = {"median_ms": float(np.median(lat)), "min_ms": float(np.min(lat))}
+    out["small_batch_256_call_latency"] = small
+    del SA, Sb, SA0, Sb0
     # plain one-at-a-time FP64 GPU path on the first `serial` problems
     A_flat.copy_(A0)
     b_flat.copy_(b0)

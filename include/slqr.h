@@ -288,6 +288,29 @@ slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const int *n, co
                                       void *stream);
 
 /*
+ * Batch plans: one batch launched many times (an SLSQP loop refactors
+ * problems of unchanged shapes at every iteration, with new values).  The
+ * arguments are those of slqr_batch_factor (ntop: NULL, or per problem the rows
+ * of its upper-triangular top block as in slqr_batch_factor_stacked, 0 for a
+ * dense problem); the problem table and the costliest-first order are copied
+ * to the device once, and each launch replays a CUDA graph of the work-counter
+ * reset and the persistent kernel.  The caller refills A[i] (and b[i]) in
+ * place between launches; the pointers, sizes, status and err arrays must
+ * stay valid for the plan's life.  The plan owns its device memory (the
+ * FP32 plan holds a scratch of up to 1 MB per resident CTA) and counts
+ * against the context's HBM budget (SLQR_EBUSY when over it).
+ * slqr_batch_plan_launch is asynchronous on `stream`; one plan must not be
+ * launched twice concurrently.
+ */
+typedef struct slqr_batch_plan slqr_batch_plan;
+slqr_status slqr_batch_plan_create(slqr_ctx *ctx, int count, const int *m, const int *n,
+                                   const int *ntop, double *const *A, const int *lda,
+                                   double *const *up, double *const *b, int prec, int *status,
+                                   double *err, slqr_batch_plan **plan);
+slqr_status slqr_batch_plan_launch(slqr_batch_plan *plan, void *stream);
+void slqr_batch_plan_destroy(slqr_batch_plan *plan);
+
+/*
  * slqr_lstsq_mixed -- least squares min ||A x - b|| for one large problem in
  * mixed precision, error stated against FP64.  The H12 factorization
  * (Alg. 2) runs on an FP32 copy of A: the reflector norm, up, b and the

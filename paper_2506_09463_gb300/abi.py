@@ -82,6 +82,13 @@ SIGNATURES = [
                                    ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, _vp, _vp,
                                    _vp]),
     ("slqr_batch_max_rows", _c_int, []),
+    ("slqr_batch_plan_create", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                        ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_vp), _c_int, _vp, _vp,
+                                        ctypes.POINTER(_vp)]),
+    ("slqr_batch_plan_launch", _c_int, [_vp, _vp]),
+    ("slqr_batch_plan_destroy", None, [_vp]),
     ("slqr_batch_factor_stacked", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int),
                                            ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
                                            ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
@@ -231,6 +238,28 @@ def slqr_batch_factor(ctx, m_list, n_list, A_ptrs, lda_list, up_ptrs, b_ptrs, pr
 
 def slqr_batch_max_rows() -> int:
     return _lib.slqr_batch_max_rows()
+
+
+def slqr_batch_plan_create(ctx, m_list, n_list, ntop_list, A_ptrs, lda_list, up_ptrs, b_ptrs,
+                           prec, status, err):
+    """Returns (status, plan handle).  ntop_list may be None (all dense)."""
+    count = len(m_list)
+    plan = _vp()
+    st = _lib.slqr_batch_plan_create(
+        ctx, count, _int_array(m_list), _int_array(n_list),
+        _int_array(ntop_list) if ntop_list is not None else None, _ptr_array(A_ptrs),
+        _int_array(lda_list), _ptr_array(up_ptrs) if up_ptrs is not None else None,
+        _ptr_array(b_ptrs) if b_ptrs is not None else None, prec, status, err,
+        ctypes.byref(plan))
+    return st, plan.value
+
+
+def slqr_batch_plan_launch(plan, stream) -> int:
+    return _lib.slqr_batch_plan_launch(plan, stream)
+
+
+def slqr_batch_plan_destroy(plan) -> None:
+    _lib.slqr_batch_plan_destroy(plan)
 
 
 def slqr_batch_factor_stacked(ctx, n_list, meq_list, A_ptrs, lda_list, up_ptrs, b_ptrs, prec,

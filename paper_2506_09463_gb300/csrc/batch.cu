@@ -626,17 +626,28 @@ namespace slqr {
 // The launch behind slqr_batch_factor and slqr_batch_factor_stacked (ntop:
 // NULL, or per problem the rows of its upper-triangular top block, 0 for a
 // dense problem).  The context mutex is held by the caller.
-slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, const int *ntop,
-                         double *const *A, const int *lda, double *const *up, double *const *b,
-                         int prec, int *status, double *err, void *stream) {
-  if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
-  if (count == 0) return SLQR_OK;
+// A batch as the kernels see it: the problem table (in the order given), the
+// longest-first order, the grid and the algorithmic flops.
+struct BatchSetup {
+  std::vector<BatchProblem> probs;
+  std::vector<int> order;
+  bool mixed = false;
+  int grid = 0;
+  double flops = 0.0;
+  size_t table_bytes = 0, head = 0, af_bytes = 0, gt_bytes = 0;   // device layout
+};
+
+// Validate the arguments and build the setup (no device work).
+static slqr_status batch_build(slqr_ctx *ctx, int count, const int *m, const int *n,
+                               const int *ntop, double *const *A, const int *lda,
+                               double *const *up, double *const *b, int prec, BatchSetup &bs) {
+  if (count <= 0) return fail(ctx, SLQR_EINVAL, "count=%d must be > 0", count);
   if (!m || !n || !A || !lda) return fail(ctx, SLQR_EINVAL, "NULL size or pointer array");
   if (prec != SLQR_FP64 && prec != SLQR_FP32)
     return fail(ctx, SLQR_EINVAL, "precision %d not available for batches", prec);
   if (prec == SLQR_FP64 && !up) return fail(ctx, SLQR_EINVAL, "SLQR_FP64 needs the up arrays");
   if (prec == SLQR_FP32 && !b) return fail(ctx, SLQR_EINVAL, "SLQR_FP32 needs the b arrays");
-  std::vector<BatchProblem> probs(count);
+  bs.probs.resize(count);
   std::vector<double> cost(count);
   for (int i = 0; i < count; ++i) {
     if (n[i] < 0 || m[i] < n[i] || m[i] > kBMaxRows)
@@ -646,22 +657,23 @@ slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, c
                      (prec == SLQR_FP64 && !up[i]) || (prec == SLQR_FP32 && !b[i])))
       return fail(ctx, SLQR_EINVAL, "problem %d: bad lda or NULL pointer", i);
     const int nt = ntop ? ntop[i] : 0;
-    probs[i] = BatchProblem{A[i], up ? up[i] : nullptr, b ? b[i] : nullptr, m[i], n[i], lda[i], nt};
+    bs.probs[i] = BatchProblem{A[i], up ? up[i] : nullptr, b ? b[i] : nullptr, m[i], n[i], lda[i], nt};
     // flops of the factorization as this launch performs it (the stacked form
     // touches the m - n rows of C and one diagonal row per reflector)
     cost[i] = (nt > 0 ? 2.0 * (m[i] - n[i] + 1) * (double)n[i] * n[i]
                       : 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0) +
               (b && b[i] ? 6.0 * m[i] * (double)n[i] : 0.0);
   }
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-
-  cudaError_t e = cudaSetDevice(ctx->device);
-  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-  const bool mixed = (prec == SLQR_FP32);
+  bs.order.resize(count);
+  std::iota(bs.order.begin(), bs.order.end(), 0);
+  std::stable_sort(bs.order.begin(), bs.order.end(),
+                   [&](int a, int c) { return cost[a] > cost[c]; });
+  bs.flops = 0.0;
+  for (int i = 0; i < count; ++i) bs.flops += cost[i];
+  bs.mixed = (prec == SLQR_FP32);
   int per_sm = 0;
-  if (mixed)
+  cudaError_t e;
+  if (bs.mixed)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_factor_mixed_kernel, kThreads,
                                                       kBMixedSmemBytes);
   else
@@ -669,40 +681,61 @@ slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, c
                                                       kBSmemBytes);
   if (e != cudaSuccess || per_sm < 1)
     return fail(ctx, SLQR_ECUDA, "batch occupancy: %s", cudaGetErrorString(e));
-  const int grid = std::min(count, per_sm * ctx->num_sms);
-  // workspace: [counter 256 B][problem table][order][per-CTA scratch (mixed)]
-  const size_t table_bytes = align_up(sizeof(BatchProblem) * count, 256);
-  const size_t head = align_up(256 + table_bytes + sizeof(int) * count, 256);
-  const size_t af_bytes = mixed ? (size_t)grid * kBMaxRows * kBMaxRows * sizeof(float) : 0;
-  const size_t gt_bytes = mixed ? (size_t)grid * kBGtDoubles * sizeof(double) : 0;
-  slqr_status st = ensure_workspace(ctx, head + af_bytes + gt_bytes);
-  if (st != SLQR_OK) return st;
-  char *base = (char *)ctx->ws.ptr;
+  bs.grid = std::min(count, per_sm * ctx->num_sms);
+  // device layout: [counter 256 B][problem table][order][per-CTA scratch (mixed)]
+  bs.table_bytes = align_up(sizeof(BatchProblem) * count, 256);
+  bs.head = align_up(256 + bs.table_bytes + sizeof(int) * count, 256);
+  bs.af_bytes = bs.mixed ? (size_t)bs.grid * kBMaxRows * kBMaxRows * sizeof(float) : 0;
+  bs.gt_bytes = bs.mixed ? (size_t)bs.grid * kBGtDoubles * sizeof(double) : 0;
+  return SLQR_OK;
+}
+
+// The kernel launch of a batch whose table and order are already at `base`.
+static void batch_kernel_launch(const BatchSetup &bs, char *base, int count, int *status,
+                                double *err, cudaStream_t s) {
   unsigned *counter = (unsigned *)base;
   BatchProblem *d_probs = (BatchProblem *)(base + 256);
-  int *d_order = (int *)(base + 256 + table_bytes);
-  cudaStream_t s = (cudaStream_t)stream;
-  e = cudaMemsetAsync(counter, 0, 256, s);
-  // (copies from pageable host memory return once the source has been staged)
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_probs, probs.data(), sizeof(BatchProblem) * count,
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
-  double flops = 0.0;
-  for (int i = 0; i < count; ++i) flops += cost[i];
-  int slot = prof_begin(ctx, s);
-  if (!mixed) {
+  int *d_order = (int *)(base + 256 + bs.table_bytes);
+  if (!bs.mixed) {
     BatchParams bp{d_probs, d_order, count, counter, status};
-    batch_factor_fp64_kernel<<<grid, kThreads, kBSmemBytes, s>>>(bp);
+    batch_factor_fp64_kernel<<<bs.grid, kThreads, kBSmemBytes, s>>>(bp);
   } else {
     BatchMixedParams mp{d_probs, d_order, count, counter, status, err,
-                        (float *)(base + head), (double *)(base + head + af_bytes),
+                        (float *)(base + bs.head), (double *)(base + bs.head + bs.af_bytes),
                         kBMaxRefine, kBRefineTol};
-    batch_factor_mixed_kernel<<<grid, kThreads, kBMixedSmemBytes, s>>>(mp);
+    batch_factor_mixed_kernel<<<bs.grid, kThreads, kBMixedSmemBytes, s>>>(mp);
   }
-  prof_end(ctx, s, slot, kBatch, flops);
+}
+
+// The launch behind slqr_batch_factor and slqr_batch_factor_stacked (ntop:
+// NULL, or per problem the rows of its upper-triangular top block, 0 for a
+// dense problem).  The context mutex is held by the caller.
+slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, const int *ntop,
+                         double *const *A, const int *lda, double *const *up, double *const *b,
+                         int prec, int *status, double *err, void *stream) {
+  if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
+  if (count == 0) return SLQR_OK;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  BatchSetup bs;
+  slqr_status st = batch_build(ctx, count, m, n, ntop, A, lda, up, b, prec, bs);
+  if (st != SLQR_OK) return st;
+  st = ensure_workspace(ctx, bs.head + bs.af_bytes + bs.gt_bytes);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws.ptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaMemsetAsync(base, 0, 256, s);
+  // (copies from pageable host memory return once the source has been staged)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + 256, bs.probs.data(), sizeof(BatchProblem) * count,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + 256 + bs.table_bytes, bs.order.data(), sizeof(int) * count,
+                        cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
+  int slot = prof_begin(ctx, s);
+  batch_kernel_launch(bs, base, count, status, err, s);
+  prof_end(ctx, s, slot, kBatch, bs.flops);
   return check_launch(ctx, "batch_factor");
 }
 
@@ -745,4 +778,93 @@ extern "C" slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const
     m[i] = n[i] + m_eq[i];
   }
   return batch_launch(ctx, count, m.data(), n, n, A, lda, up, b, prec, status, err, stream);
+}
+
+// --------------------------------------------------------------------------
+// Batch plans: the same batch launched many times (an SLSQP loop refactors
+// problems of unchanged shapes at every iteration).  The problem table and
+// the order go to the device once; the launch (reset of the work counter and
+// the persistent kernel) is captured into a CUDA graph and replayed.
+// --------------------------------------------------------------------------
+struct slqr_batch_plan {
+  slqr_ctx *ctx = nullptr;
+  slqr::BatchSetup bs;
+  int count = 0;
+  char *dev = nullptr;               // counter, table, order, mixed scratch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" void slqr_batch_plan_destroy(slqr_batch_plan *plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->ctx->device);
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->dev) cudaFree(plan->dev);
+  delete plan;
+}
+
+extern "C" slqr_status slqr_batch_plan_create(slqr_ctx *ctx, int count, const int *m,
+                                              const int *n, const int *ntop, double *const *A,
+                                              const int *lda, double *const *up,
+                                              double *const *b, int prec, int *status,
+                                              double *err, slqr_batch_plan **out) {
+  if (!ctx || !out) return SLQR_EINVAL;
+  NvtxRange nvtx_range("slqr_batch_plan_create");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  slqr_batch_plan *plan = new (std::nothrow) slqr_batch_plan();
+  if (!plan) return SLQR_ENOMEM;
+  plan->ctx = ctx;
+  plan->count = count;
+  slqr_status st = batch_build(ctx, count, m, n, ntop, A, lda, up, b, prec, plan->bs);
+  if (st != SLQR_OK) {
+    delete plan;
+    return st;
+  }
+  const size_t bytes = plan->bs.head + plan->bs.af_bytes + plan->bs.gt_bytes;
+  if (ctx->hbm_budget && bytes > ctx->hbm_budget) {
+    delete plan;
+    return fail(ctx, SLQR_EBUSY, "batch plan of %zu bytes exceeds the HBM budget", bytes);
+  }
+  e = cudaMalloc(&plan->dev, bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->dev + 256, plan->bs.probs.data(), sizeof(BatchProblem) * count,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->dev + 256 + plan->bs.table_bytes, plan->bs.order.data(),
+                   sizeof(int) * count, cudaMemcpyHostToDevice);
+  cudaStream_t cs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(plan->dev, 0, 256, cs);
+    batch_kernel_launch(plan->bs, plan->dev, count, status, err, cs);
+    e = cudaStreamEndCapture(cs, &plan->graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    slqr_batch_plan_destroy(plan);
+    return fail(ctx, SLQR_ECUDA, "batch plan: %s", cudaGetErrorString(e));
+  }
+  *out = plan;
+  return SLQR_OK;
+}
+
+extern "C" slqr_status slqr_batch_plan_launch(slqr_batch_plan *plan, void *stream) {
+  if (!plan) return SLQR_EINVAL;
+  NvtxRange nvtx_range("slqr_batch_plan_launch");
+  slqr_ctx *ctx = plan->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int slot = prof_begin(ctx, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(plan->exec, s);
+  prof_end(ctx, s, slot, kBatch, plan->bs.flops);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "batch plan launch: %s", cudaGetErrorString(e));
+  return SLQR_OK;
 }

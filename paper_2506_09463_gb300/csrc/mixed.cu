@@ -140,7 +140,7 @@ __global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ 
 // partials of all CTAs in the same fixed order, forms W' = T^T W (or T W) and
 // updates its own rows.  One barrier per panel instead of three launches.
 // --------------------------------------------------------------------------
-constexpr int kQvRows = 128;     // rows of f per CTA (at least; more CTAs when m is large)
+constexpr int kQvRows = 128;     // rows of f per CTA (more when m exceeds 128 per SM)
 
 // T of panel p (float, ld nb + 1): column j solves U y = e_j by back
 // substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and

@@ -217,3 +217,44 @@ def test_batch_mixed_full_size_sampled(ctx):
     rng = np.random.default_rng(1)
     check_mixed(ms, ns, A0, b0, b, a_off, b_off, status, err,
                 rng.choice(len(ms), size=200, replace=False))
+
+
+def test_batch_plan_replays_with_new_values(ctx):
+    """A batch plan (CUDA graph of the persistent launch) gives the results of
+    slqr_batch_factor on the same problems, and again after the inputs are
+    refilled in place with other values."""
+    from paper_2506_09463_gb300 import abi
+    ms, ns = workloads.batch_shapes(80, seed=31)
+    A_flat, b_flat, a_off, b_off = workloads.batch_problems_device(ms, ns, 31)
+    A_next, b_next, _, _ = workloads.batch_problems_device(ms, ns, 32)
+    A0, b0 = A_flat.clone(), b_flat.clone()
+    count = len(ms)
+    up_flat = torch.zeros(int(sum(ns)) + 1, dtype=torch.float64, device="cuda")
+    up_off = np.concatenate([[0], np.cumsum(ns)[:-1]]).astype(np.int64)
+    A_ptrs = [A_flat.data_ptr() + int(a_off[i]) * 8 for i in range(count)]
+    b_ptrs = [b_flat.data_ptr() + int(b_off[i]) * 8 for i in range(count)]
+    up_ptrs = [up_flat.data_ptr() + int(up_off[i]) * 8 for i in range(count)]
+    status = torch.full((count,), 99, dtype=torch.int32, device="cuda")
+    st, plan = abi.slqr_batch_plan_create(ctx.ctx, list(ms), list(ns), None, A_ptrs,
+                                          [int(m) for m in ms], up_ptrs, b_ptrs, abi.SLQR_FP64,
+                                          status.data_ptr(), None)
+    assert st == 0, abi.slqr_last_error(ctx.ctx)
+    try:
+        stream = torch.cuda.current_stream().cuda_stream
+        for A_in, b_in in ((A0, b0), (A_next, b_next), (A0, b0)):
+            A_flat.copy_(A_in)
+            b_flat.copy_(b_in)
+            status.fill_(99)
+            assert abi.slqr_batch_plan_launch(plan, stream) == 0
+            assert ctx.sync() == 0
+            assert np.all(status.cpu().numpy() == 0)
+            res = dict(A0=A_in, b0=b_in, A=A_flat, b=b_flat, up=up_flat, a_off=a_off,
+                       b_off=b_off, up_off=up_off)
+            for i in range(0, count, 7):
+                check_problem(*problem(res, i, int(ms[i]), int(ns[i])))
+    finally:
+        abi.slqr_batch_plan_destroy(plan)
+    # invalid arguments are refused before anything is made
+    st, plan = abi.slqr_batch_plan_create(ctx.ctx, [3], [5], None, [A_flat.data_ptr()], [3],
+                                          [up_flat.data_ptr()], None, abi.SLQR_FP64, None, None)
+    assert st == abi.SLQR_EINVAL and not plan
