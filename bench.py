@@ -54,6 +54,23 @@ TRAFFIC_PER_LAUNCH = {"vtx": {"dram": 58.52e6, "algorithmic": 52.23e6},
                       "upd": {"dram": 85.63e6, "algorithmic": 101.72e6}}
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (the job's time): an all-reduce MAX over the
+    ranks (NCCL on the GPU, gloo on the CPU), or `ms` itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(flops_per_step, steps, world, t_max_ms):
+    """Whole-job GFLOP/s of `world` replicas, each doing `steps` steps, timed
+    by the slowest rank (weak scaling: the work per rank is fixed)."""
+    return world * flops_per_step * steps / (t_max_ms / 1e3) / 1e9
+
+
 def step_flops(shapes=SHAPES, nrhs=NRHS):
     total = 0.0
     for m, n, _ in shapes:
@@ -262,14 +279,10 @@ def run_ours(args, rank, world, local_rank):
     st = ctx.sync()
     if st != 0:
         raise RuntimeError(f"device status {st}: {abi.slqr_last_error(ctx.ctx)}")
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist, device)
     ms_per_step = t_max / args.steps
     flops = step_flops()
-    value = world * flops * args.steps / (t_max / 1e3) / 1e9
+    value = job_throughput(flops, args.steps, world, t_max)
 
     # ---- end-to-end through the public API with host buffers ----
     pinned = []
@@ -298,12 +311,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * flops * args.steps / (e2e_ms / 1e3) / 1e9
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
+    e2e_value = job_throughput(flops, args.steps, world, e2e_ms)
     if ctx.sync() != 0:
         raise RuntimeError(abi.slqr_last_error(ctx.ctx))
 
