@@ -16,8 +16,9 @@
 //    the other panel columns, which also give striu(V^T V)), then the update
 //    of the later panel columns;
 //  * the trailing columns (and b, as one more column) are updated in tiles of
-//    32 columns: W = V^T C (one warp per column, lanes over rows), then
-//    W' = T^T W by forward substitution (one lane per column), then C -= V W'.
+//    32 columns: W = V^T C (8 lanes per column, each over every 8th row),
+//    then W' = T^T W by forward substitution (one lane per column), then
+//    C -= V W' (the same lanes as W).
 // All arithmetic is FP64 (DFMA).
 #include "slqr_internal.cuh"
 
@@ -31,6 +32,9 @@ constexpr int kBNB = 16;          // reflectors per panel
 constexpr int kBMaxRows = 512;    // rows of a batched problem (panel slice in smem)
 constexpr int kBCols = 32;        // trailing columns per tile
 constexpr int kBWarps = kThreads / 32;
+constexpr int kBRowGroups = 8;                  // lanes of a column in the tile phases
+constexpr int kBGroupCols = 32 / kBRowGroups;   // columns of one warp in the tile phases
+static_assert(kBGroupCols * kBWarps == kBCols, "one column group per warp covers the tile");
 constexpr int kBMaxRefine = 12;        // refinement sweeps of the mixed path
 constexpr double kBRefineTol = 1e-14;  // stop when ||dx||_inf <= tol ||x||_inf
 constexpr double kBStallOk = 1e-10;    // a stalled refinement is accepted below this
@@ -63,42 +67,35 @@ __device__ __forceinline__ double b_pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Sum over a warp of 16 per-lane values acc[0..15] (each lane its own
-// partials): a halving exchange -- at each of four levels a lane keeps half of
-// its values and adds the other half received from its partner -- then one
-// last exchange.  16 shuffles and 16 adds per lane instead of 80 of each for
-// 16 separate butterflies.  Lanes 2a and 2a+1 end with the total of value a.
+// Sum of 16 per-lane values acc[0..15] over the 8 lanes g = lane & 7 of one
+// column group by a halving exchange: at each of three levels a lane keeps
+// half of its values and adds the other half received from its partner (14
+// shuffles and adds per lane instead of 48 for 16 separate butterflies).
+// Afterwards lane g holds the totals of values 2g and 2g + 1 in acc[0], acc[1].
 template <typename T>
-__device__ __forceinline__ T b_warp_sum16(T (&acc)[kBNB], int lane) {
-  static_assert(kBNB == 16, "four halving levels");
+__device__ __forceinline__ void b_group8_sum16(T (&acc)[kBNB], int g) {
+  static_assert(kBNB == 16, "three halving levels over 8 lanes");
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const bool hi = (lane & 16) != 0;
+    const bool hi = (g & 4) != 0;
     const T send = hi ? acc[i] : acc[i + 8];
     const T keep = hi ? acc[i + 8] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const bool hi = (lane & 8) != 0;
+    const bool hi = (g & 2) != 0;
     const T send = hi ? acc[i] : acc[i + 4];
     const T keep = hi ? acc[i + 4] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const bool hi = (lane & 4) != 0;
+    const bool hi = (g & 1) != 0;
     const T send = hi ? acc[i] : acc[i + 2];
     const T keep = hi ? acc[i + 2] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
   }
-  {
-    const bool hi = (lane & 2) != 0;
-    const T send = hi ? acc[0] : acc[1];
-    const T keep = hi ? acc[1] : acc[0];
-    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
 }
 
 __device__ __forceinline__ double b_warp_sum(double v) {
@@ -139,6 +136,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
                                   double *G_out, double *tau_out, char *smraw, int ntop) {
   using SM = BatchSmem<T>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g8 = lane & (kBRowGroups - 1);
   T *Ps = (T *)smraw;
   T *Wt = Ps + SM::kPanel;
   double *Gs = (double *)(smraw + align_up_c(SM::kBytesT, 16));
@@ -273,22 +271,31 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     const int NT = n - (k0 + nbw);
     const int NC = NT + (Bcol ? 1 : 0);
     for (int t0 = 0; t0 < NC; t0 += kBCols) {
-      // phase A: W[a][col] = sum_r V[a][r] C[r][col]
-      for (int cc = warp; cc < kBCols; cc += kBWarps) {
+      // phase A: W[a][col] = sum_r V[a][r] C[r][col].  Warp w takes the four
+      // columns 4w .. 4w+3 of the tile; lane = 8 * (column - 4w) + g walks
+      // the rows r = g (mod 8), so a column's 16 partial sums are combined
+      // over 8 lanes only (14 adds per lane) and a ragged M leaves at most
+      // 7 lanes of a column idle on its last row step.
+      if (t0 + kBGroupCols * warp < NC) {
+        const int cc = kBGroupCols * warp + (lane >> 3);
         const int col = t0 + cc;
-        if (col >= NC) break;
-        const T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (const T *)(Bcol + k0);
         T acc[kBNB];
 #pragma unroll
         for (int a = 0; a < kBNB; ++a) acc[a] = T(0);
-        for (int r = lane; r < M; r += 32) {
-          const T cv = C[prow(r)];
+        if (col < NC) {
+          const T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (const T *)(Bcol + k0);
+          for (int r = g8; r < M; r += kBRowGroups) {
+            const T cv = C[prow(r)];
 #pragma unroll
-          for (int a = 0; a < kBNB; ++a)
-            if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
+            for (int a = 0; a < kBNB; ++a)
+              if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
+          }
         }
-        const T v = b_warp_sum16(acc, lane);        // lanes 2a, 2a+1 hold W[a]
-        if ((lane & 1) == 0) Wt[(lane >> 1) * (kBCols + 1) + cc] = v;
+        b_group8_sum16(acc, g8);                // lane g holds W[2g], W[2g + 1]
+        if (col < NC) {
+          Wt[(2 * g8) * (kBCols + 1) + cc] = acc[0];
+          Wt[(2 * g8 + 1) * (kBCols + 1) + cc] = acc[1];
+        }
       }
       __syncthreads();
       // phase B: W' = T^T W, one lane per column (FP64 arithmetic)
@@ -306,21 +313,23 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         }
       }
       __syncthreads();
-      // phase C: C -= V W'
-      for (int cc = warp; cc < kBCols; cc += kBWarps) {
+      // phase C: C -= V W', the same lane layout as phase A
+      {
+        const int cc = kBGroupCols * warp + (lane >> 3);
         const int col = t0 + cc;
-        if (col >= NC) break;
-        T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (T *)(Bcol + k0);
-        T w[kBNB];
+        if (col < NC) {
+          T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (T *)(Bcol + k0);
+          T w[kBNB];
 #pragma unroll
-        for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
-        for (int r = lane; r < M; r += 32) {
-          const int pr = prow(r);
-          T cv = C[pr];
+          for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
+          for (int r = g8; r < M; r += kBRowGroups) {
+            const int pr = prow(r);
+            T cv = C[pr];
 #pragma unroll
-          for (int a = 0; a < kBNB; ++a)
-            if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
-          C[pr] = cv;
+            for (int a = 0; a < kBNB; ++a)
+              if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
+            C[pr] = cv;
+          }
         }
       }
       __syncthreads();

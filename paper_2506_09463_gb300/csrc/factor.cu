@@ -60,9 +60,10 @@ struct PanelParams {
   void *A;             // T * (the storage type of the factorization)
   double *up;          // global up array (n doubles)
   double *wy;          // this panel's compact-WY block (Vtop | G | tau)
-  double *rec;         // 2 * P * NB doubles, layout [buf][cta][entry]
+  double *rec;         // NB * P * NB doubles: per column j the records [j][cta][entry]
+  double *srec;        // P * NB doubles: per-CTA column scales (panel start)
   double *gpart;       // P * NB*(NB-1)/2 doubles: per-CTA partial Gram terms
-  double *prow;        // 2 * NB doubles
+  double *prow;        // NB * NB doubles: per column j the pivot row [j][entry]
   unsigned *bar;       // monotonic arrival counter
   int *status;
   int m, lda, k0, nbw;
@@ -93,6 +94,30 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// Per-column records are exchanged without a grid barrier: every slot is
+// written once per panel, and until then it holds kUnset, a signalling-NaN
+// bit pattern that no arithmetic result has (FP operations return the
+// canonical quiet NaN).  A reader polls the slot until it holds a value, so
+// the value itself is the message (one 8-byte store, single-copy atomic).
+constexpr unsigned long long kUnset = 0x7ff0dead5a5a5a5aull;
+
+__device__ __forceinline__ bool is_unset(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kUnset;
+}
+
+// Publish v (relaxed, GPU scope); a copied input that happens to carry the
+// kUnset pattern goes out as the canonical quiet NaN instead.
+__device__ __forceinline__ void publish(double *p, double v) {
+  if (is_unset(v)) v = __longlong_as_double(0x7fffffffffffffffll);
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // One CTA per slice of R rows of the panel (rows [k0, m), NB columns); the
 // slice stays in shared memory for the whole panel.
 //
@@ -111,10 +136,11 @@ __device__ __forceinline__ double pow2(int e) {
 //            terms of V^T V) are kept in a CTA-local accumulator.  Lane
 //            partials are reduced through shared memory (every FP64
 //            instruction works on 32 useful lanes).
-//   barrier
-//   phase 2  every CTA reduces the published partials: thread (g, c) sums
-//            entry c over its slice g of the CTAs (all loads in flight), the
-//            slices are added in a fixed order (the same in every CTA);
+//   phase 2  every CTA waits until each CTA's record of column j has arrived
+//            (one warp polls the records; no grid barrier per column), then
+//            reduces the published partials: thread (g, c) sums entry c over
+//            its slice g of the CTAs (all loads in flight), the slices are
+//            added in a fixed order (the same in every CTA);
 //   pivot    one thread forms s, cl, up, b and 1/b; sigma_c = (up p_c + D_c)/b;
 //   phase 3  update of the later panel columns.
 // At the end the local Gram terms are published and reduced once, each CTA
@@ -163,13 +189,20 @@ panel_kernel(PanelParams p) {
         zero ? T(0) : A[SLQR_IDX(panel_row(p.k0, nbw, p.skip, row0 + r), p.k0 + c, lda)];
   }
   for (int idx = tid; idx < NB * NB; idx += kThreads) Gloc[idx] = 0.0;
+  // this CTA's record slots of every column (and CTA 0: the pivot rows) back
+  // to kUnset; the grid barrier below orders this before any publish or poll
+  for (int idx = tid; idx < nbw * NB; idx += kThreads) {
+    const int jj = idx / NB, c = idx - jj * NB;
+    p.rec[((size_t)jj * p.P + cta) * NB + c] = __longlong_as_double((long long)kUnset);
+    if (cta == 0) p.prow[idx] = __longlong_as_double((long long)kUnset);
+  }
   double *G = p.wy + (size_t)NB * NB;
   double *tau = p.wy + 2 * (size_t)NB * NB;
   __syncthreads();
 
   // ---- panel start: column scales ------------------------------------------
   {
-    double *rec = p.rec + (size_t)1 * RECW * p.P;    // buffer 1 (column 0 uses buffer 0)
+    double *rec = p.srec;
 #pragma unroll
     for (int t = 0; t < CPW; ++t) {
       const int c = warp + t * NW;
@@ -185,7 +218,7 @@ panel_kernel(PanelParams p) {
   if (!grid_barrier(p.bar, p.bar_base + (unsigned)p.P, p.status, &s_ok)) return;
   {
     constexpr int QMAX = (PMAX + GROUPS - 1) / GROUPS;
-    const double *rec = p.rec + (size_t)1 * RECW * p.P;
+    const double *rec = p.srec;
     const int g = tid / NB, c = tid - g * NB;
     const int per = (p.P + GROUPS - 1) / GROUPS;
     const int q0 = g * per, q1 = min(p.P, q0 + per);
@@ -210,10 +243,9 @@ panel_kernel(PanelParams p) {
   __syncthreads();
 
   for (int j = 0; j < nbw; ++j) {
-    const int buf = j & 1;
-    double *rec = p.rec + (size_t)buf * RECW * p.P;
-    double *myrec = rec + (size_t)cta * RECW;
-    double *prow = p.prow + buf * NB;
+    const double *rec = p.rec + (size_t)j * p.P * RECW;   // records of column j
+    double *myrec = p.rec + ((size_t)j * p.P + cta) * RECW;
+    double *prow = p.prow + (size_t)j * NB;
     const int r_tail = (cta == 0) ? j + 1 : 0;       // rows strictly below the pivot
     const T *x = Ps + j * R;
 
@@ -248,7 +280,7 @@ panel_kernel(PanelParams p) {
         if (c < NB && c != j) s_lane[c][lane] = (Acc)acc[t];
       }
       if (norm_warp) s_nlane[lane] = nacc;
-      if (cta == 0 && tid < nbw) prow[tid] = (double)Ps[tid * R + j];
+      if (cta == 0 && tid < nbw) publish(prow + tid, (double)Ps[tid * R + j]);
     }
     __syncthreads();
     {
@@ -273,34 +305,89 @@ panel_kernel(PanelParams p) {
       double v = s_part[0][c];
 #pragma unroll
       for (int qq = 1; qq < LQ; ++qq) v += s_part[qq][c];
-      if (c >= j) myrec[c] = v;                       // norm (c == j) and dots: published
+      if (c >= j) publish(myrec + c, v);              // norm (c == j) and dots
       else Gloc[c + j * NB] = v;                      // Gram term: kept
     }
-
-    // ---- grid barrier ----------------------------------------------------
-    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(j + 2) * (unsigned)p.P, p.status, &s_ok))
-      return;
 
     // ---- phase 2 ---------------------------------------------------------
     {
       constexpr int QMAX = (PMAX + GROUPS - 1) / GROUPS;
-      const double prow_v = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
+      static_assert(QMAX <= 64, "one pending bit per polled record");
       const int g = tid / NB, c = tid - g * NB;
       const int per = (p.P + GROUPS - 1) / GROUPS;
       const int q0 = g * per, q1 = min(p.P, q0 + per);
-      if (c >= j && c < nbw) {
-        double v[QMAX];
+      const bool sums = c >= j && c < nbw;
+      // warp 0 waits until the norm entry of every CTA's record has arrived
+      // (a record's entries are stored together, so the rest follow at once):
+      // each lane loads its CTAs' entries together, then polls the missing
+      bool ok = true;
+      if (warp == 0) {
+        constexpr int PW = (PMAX + 31) / 32;
+        unsigned pend = 0;
 #pragma unroll
-        for (int t = 0; t < QMAX; ++t)
-          v[t] = (q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + c) : 0.0;
-        double acc = 0.0;
+        for (int t = 0; t < PW; ++t) {
+          const int q = lane + 32 * t;
+          if (q < p.P && is_unset(ld_relaxed_f64(rec + (size_t)q * RECW + j))) pend |= 1u << t;
+        }
+        unsigned it = 0;
+        while (pend != 0) {                           // bounded
+          if (++it > kSpinLimit) { ok = false; break; }
+          if (it > 8) __nanosleep(32);
 #pragma unroll
-        for (int t = 0; t < QMAX; ++t) acc += v[t];
-        s_part[g][c] = acc;
+          for (int t = 0; t < PW; ++t) {
+            if (((pend >> t) & 1u) && !is_unset(ld_relaxed_f64(rec + (size_t)(lane + 32 * t) * RECW + j)))
+              pend &= ~(1u << t);
+          }
+        }
       }
-      if (tid < nbw) s_prow[tid] = prow_v;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) record_status(p.status, SLQR_ETIMEOUT);
+        return;
+      }
+      // every thread loads its entries (all in flight, from L2) and sums them
+      // in a fixed order; an entry not yet visible (rare: it still reads as
+      // kUnset) sends the thread through a bounded re-poll of its slots in
+      // the same order
+      double v[QMAX];
+#pragma unroll
+      for (int t = 0; t < QMAX; ++t)
+        v[t] = (sums && q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + c) : 0.0;
+      double pv = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
+      double acc = 0.0;
+      bool miss = false;
+#pragma unroll
+      for (int t = 0; t < QMAX; ++t) {
+        miss |= is_unset(v[t]);
+        acc += v[t];
+      }
+      if (miss) {
+        acc = 0.0;
+        for (int t = 0; t < QMAX && ok; ++t) {
+          if (!(sums && q0 + t < q1)) continue;
+          double x;
+          unsigned it = 0;
+          while (is_unset(x = ld_relaxed_f64(rec + (size_t)(q0 + t) * RECW + c))) {
+            if (++it > kSpinLimit) { ok = false; break; }
+            __nanosleep(32);
+          }
+          acc += x;
+        }
+      }
+      if (tid < nbw) {
+        unsigned it = 0;
+        while (is_unset(pv)) {
+          if (++it > kSpinLimit) { ok = false; break; }
+          __nanosleep(32);
+          pv = ld_relaxed_f64(prow + tid);
+        }
+      }
+      if (sums) s_part[g][c] = acc;
+      if (tid < nbw) s_prow[tid] = pv;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) record_status(p.status, SLQR_ETIMEOUT);
+        return;
+      }
     }
-    __syncthreads();
     if (tid == 0) {
       double S = s_part[0][j];
       for (int g = 1; g < GROUPS; ++g) S += s_part[g][j];
@@ -377,8 +464,7 @@ panel_kernel(PanelParams p) {
       if (c < jj) mine[jj * (jj - 1) / 2 + c] = Gloc[idx];
     }
   }
-  if (!grid_barrier(p.bar, p.bar_base + (unsigned)(nbw + 2) * (unsigned)p.P, p.status, &s_ok))
-    return;
+  if (!grid_barrier(p.bar, p.bar_base + 2u * (unsigned)p.P, p.status, &s_ok)) return;
   for (int idx = cta + tid * p.P; idx < NB * NB; idx += kThreads * p.P) {
     const int jj = idx / NB, c = idx - jj * NB;
     double v = 0.0;
@@ -903,24 +989,28 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   auto skip_of = [&](int k0, int nbw) { return ntop > 0 ? ntop - (k0 + nbw) : 0; };
   const int np = num_panels(K, NB);
   const int rmin = rows_min_for(m, n);
-  // workspace: [bar (256 B)] [records] [prow] [wy if none given] [trailing work]
+  // workspace: [bar (256 B)] [records] [scale records] [Gram partials] [prow]
+  // [wy if none given] [trailing work]
   const int Pmax = ctx->num_sms;
-  const size_t rec_doubles = 2 * (size_t)(NB + 2) * Pmax;
+  const size_t rec_doubles = (size_t)NB * NB * Pmax;
+  const size_t srec_doubles = (size_t)NB * Pmax;
   const size_t gpart_doubles = (size_t)Pmax * NB * (NB - 1) / 2;
-  const size_t prow_doubles = 2 * (size_t)NB;
+  const size_t prow_doubles = (size_t)NB * NB;
   const size_t wy_doubles = wy ? 0 : wy_panel_doubles(NB) * (size_t)std::max(np, 1);
   // (the FP32 path also keeps a row-major copy of V for the tensor-core update)
   // (the FP32 path also keeps a row-major V, or the BF16 pairs of V and W')
   const size_t work_doubles = panel_update_work_doubles(m, n, NB, ctx->num_sms) +
                               (std::is_same<T, float>::value ? (size_t)(m + n) * NB : 0);
-  const size_t bytes = 256 + (rec_doubles + gpart_doubles + prow_doubles + wy_doubles) * 8 +
+  const size_t bytes = 256 +
+                       (rec_doubles + srec_doubles + gpart_doubles + prow_doubles + wy_doubles) * 8 +
                        work_doubles * sizeof(T) + 256;
   slqr_status st = ensure_workspace(ctx, bytes);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws.ptr;
   unsigned *bar = (unsigned *)base;
   double *rec = (double *)(base + 256);
-  double *gpart = rec + rec_doubles;
+  double *srec = rec + rec_doubles;
+  double *gpart = srec + srec_doubles;
   double *prow = gpart + gpart_doubles;
   double *wy_store = wy ? wy : prow + prow_doubles;
   // 256-byte aligned (vector stores and TMA maps of the trailing update)
@@ -953,8 +1043,8 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
     PanelParams pp;
-    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
-    pp.bar = bar;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.srec = srec; pp.gpart = gpart;
+    pp.prow = prow; pp.bar = bar;
     pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.skip = skip; pp.stacked = ntop > 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
@@ -976,7 +1066,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
         split_bf16_region((const float *)A, lda, k0, m, k0, k0 + nbw, ctx->sh_hi, ctx->sh_lo,
                           ctx->num_sms, s);
     }
-    bar_base += (unsigned)P * (unsigned)(nbw + 2);
+    bar_base += 2u * (unsigned)P;                 // two grid barriers per panel
     return SLQR_OK;
   };
   auto update = [&](int pnl, int c_begin, int c_end) -> slqr_status {
@@ -1221,13 +1311,15 @@ constexpr int kNoAllocMaxCols = 1024;
 constexpr int kNoAllocMaxSms = 256;
 constexpr int kNoAllocMaxDevices = 64;
 constexpr size_t kNoAllocHeadDoubles = 32;                       // 256 B: counter + status
-constexpr size_t kNoAllocRecDoubles = 2 * (64 + 2) * (size_t)kNoAllocMaxSms;
+constexpr size_t kNoAllocRecDoubles = (size_t)64 * 64 * kMaxPanelCtas;
+constexpr size_t kNoAllocSrecDoubles = (size_t)64 * kMaxPanelCtas;
 constexpr size_t kNoAllocGpartDoubles = (size_t)kMaxPanelCtas * 64 * 63 / 2;
-constexpr size_t kNoAllocProwDoubles = 2 * 64;
+constexpr size_t kNoAllocProwDoubles = 64 * 64;
 constexpr size_t kNoAllocWyDoubles = (kNoAllocMaxCols / 64) * (2 * 64 * 64 + 64);
 constexpr size_t kNoAllocWorkDoubles = 384 * 1024;
 constexpr size_t kNoAllocScratchDoubles = kNoAllocHeadDoubles + kNoAllocRecDoubles +
-                                          kNoAllocGpartDoubles + kNoAllocProwDoubles +
+                                          kNoAllocSrecDoubles + kNoAllocGpartDoubles +
+                                          kNoAllocProwDoubles +
                                           kNoAllocWyDoubles + kNoAllocWorkDoubles;
 
 // About 6.9 MB on every device that loads the library, held until exit.
@@ -1337,7 +1429,8 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
   unsigned *bar = (unsigned *)scratch;
   if (!status) status = (int *)(scratch + 16);
   double *rec = scratch + kNoAllocHeadDoubles;
-  double *gpart = rec + kNoAllocRecDoubles;
+  double *srec = rec + kNoAllocRecDoubles;
+  double *gpart = srec + kNoAllocSrecDoubles;
   double *prow = gpart + kNoAllocGpartDoubles;
   double *wy_store = wy ? wy : prow + kNoAllocProwDoubles;
   double *work = prow + kNoAllocProwDoubles + kNoAllocWyDoubles;
@@ -1355,8 +1448,8 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     const int P = (M + R - 1) / R;
     double *wy_panel = wy_store + (size_t)pnl * wy_panel_doubles(NB);
     PanelParams pp;
-    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.gpart = gpart; pp.prow = prow;
-    pp.bar = bar;
+    pp.A = A; pp.up = up; pp.wy = wy_panel; pp.rec = rec; pp.srec = srec; pp.gpart = gpart;
+    pp.prow = prow; pp.bar = bar;
     pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.skip = 0; pp.stacked = 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
     void *args[] = {&pp};
@@ -1364,7 +1457,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     e = cudaLaunchCooperativeKernel(panel_kernel_for<double, NB>(P), dim3(P), dim3(kThreads), args,
                                     smem, stream);
     if (e != cudaSuccess) return SLQR_ECUDA;
-    bar_base += (unsigned)P * (unsigned)(nbw + 2);
+    bar_base += 2u * (unsigned)P;
     const int N = n - (k0 + nbw);
     if (N > 0) {
       slqr_status st = noalloc_update<NB>(num_sms, m, k0, nbw, A, lda, wy_panel,
