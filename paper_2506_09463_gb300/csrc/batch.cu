@@ -113,9 +113,10 @@ template <typename T>
 struct BatchSmem {
   static constexpr int kPanel = kBNB * kBMaxRows;       // Ps[c][r]
   static constexpr int kW = kBNB * (kBCols + 1);        // Wt[a][col]
-  static constexpr size_t kBytesT = (size_t)(kPanel + kW) * sizeof(T);
   static constexpr int kG = kBNB * kBNB;                // G[q][j] (ld kBNB)
-  static constexpr int kMisc = 5 * kBNB + 8;            // dots, sigma, tau, up, scale, norm
+  // T copies of the panel's G and tau for W' = T^T W (phase B)
+  static constexpr size_t kBytesT = (size_t)(kPanel + kW + kG + kBNB) * sizeof(T);
+  static constexpr int kMisc = 6 * kBNB + 8;  // dots, sigma, tau, up, scale, 1/scale, norm
   static constexpr size_t kBytes = align_up_c(kBytesT, 16) + (size_t)(kG + kMisc) * sizeof(double);
 };
 
@@ -139,13 +140,16 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
   const int g8 = lane & (kBRowGroups - 1);
   T *Ps = (T *)smraw;
   T *Wt = Ps + SM::kPanel;
+  T *Gt = Wt + SM::kW;              // G and tau of the panel in T (phase B)
+  T *taut = Gt + SM::kG;
   double *Gs = (double *)(smraw + align_up_c(SM::kBytesT, 16));
   double *dots = Gs + SM::kG;
   double *sig = dots + kBNB;
   double *tau = sig + kBNB;
   double *ups = tau + kBNB;
   double *scl = ups + kBNB;         // per-column scale 2^-E of the panel
-  double *misc = scl + kBNB;        // [0] = norm
+  double *sinv = scl + kBNB;        // and its inverse 2^E
+  double *misc = sinv + kBNB;       // [0] = norm
   const int K = num_reflectors(m, n);
   for (int k = K + tid; k < n; k += kThreads) up_out[k] = 0.0;
 
@@ -177,6 +181,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
           int E = (int)((mx >> 20) & 0x7ff) - 1023;
           E = min(max(E, -1000), 1022);
           scl[c] = b_pow2(-E);
+          sinv[c] = b_pow2(E);
         }
       }
     }
@@ -196,7 +201,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
             S = fma(xs, xs, S);
           }
           S = b_warp_sum(S);
-          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : sqrt(S) / sc;
+          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : sqrt(S) * sinv[j];   // exact rescale
         } else {
           const T *col = Ps + c * kBMaxRows;
           T acc = T(0);
@@ -210,17 +215,17 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
       const double s = misc[0];
       const double x0 = (double)x[j];
       const bool defined = (s != 0.0);
-      double cl = 0.0, upk = 0.0, bk = 1.0, tk = 0.0;
+      double cl = 0.0, upk = 0.0, tk = 0.0;
       if (defined) {
         cl = (x0 > 0.0) ? -s : s;
         upk = x0 - cl;
-        bk = upk * cl;
-        tk = -1.0 / bk;
+        if (warp == 0) tk = -1.0 / (upk * cl);        // tau = -1/b (warp 0 uses it)
       }
       if (tid < nbw) {
         const int c = tid;
         const double pr_c = (double)Ps[c * kBMaxRows + j];
-        if (c > j) sig[c] = defined ? (upk * pr_c + dots[c]) / bk : 0.0;
+        // sigma_c = (up p_c + D_c) / b = -(up p_c + D_c) tau
+        if (c > j) sig[c] = defined ? -(upk * pr_c + dots[c]) * tk : 0.0;
         else if (c < j) Gs[c + j * kBNB] = pr_c * upk + dots[c];
       }
       __syncthreads();
@@ -264,7 +269,9 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     for (int idx = tid; idx < kBNB * kBNB; idx += kThreads) {
       int c = idx / kBNB, r = idx - c * kBNB;
       if (r <= c && r < M) Ps[c * kBMaxRows + r] = (r == c && c < nbw) ? (T)ups[c] : T(0);
+      Gt[idx] = (T)Gs[idx];
     }
+    if (tid < kBNB) taut[tid] = (T)tau[tid];
     __syncthreads();
 
     // trailing columns [k0 + nbw, n), plus Bcol as one more column
@@ -298,17 +305,18 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         }
       }
       __syncthreads();
-      // phase B: W' = T^T W, one lane per column (FP64 arithmetic)
+      // phase B: W' = T^T W, one lane per column, in T (an FP32
+      // factorization keeps this chain off the slow FP64 pipe)
       if (warp == 0 && t0 + lane < NC) {
-        double w[kBNB];
+        T w[kBNB];
 #pragma unroll
         for (int jj = 0; jj < kBNB; ++jj) {
           if (jj < nbw) {
-            double t = (double)Wt[jj * (kBCols + 1) + lane];
+            T t = Wt[jj * (kBCols + 1) + lane];
 #pragma unroll
-            for (int q = 0; q < jj; ++q) t = fma(-Gs[q + jj * kBNB], w[q], t);
-            w[jj] = tau[jj] * t;
-            Wt[jj * (kBCols + 1) + lane] = (T)w[jj];
+            for (int q = 0; q < jj; ++q) t = fma(-Gt[q + jj * kBNB], w[q], t);
+            w[jj] = taut[jj] * t;
+            Wt[jj * (kBCols + 1) + lane] = w[jj];
           }
         }
       }
@@ -444,24 +452,30 @@ __device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, co
       if (lane == 0) w[a] = acc;
     }
     __syncthreads();
-    if (tid == 0) {
+    // T^T w (forward) or T w, right-looking in FP32 on warp 0: lane j holds
+    // w_j and its column (forward) or row of G; at step q lane q's value is
+    // final and the lanes still open subtract its contribution
+    if (warp == 0) {
       const double *Gp = G + (size_t)pnl * kBNB * kBNB;
-      const double *tp = tau + k0;
-      double ww[kBNB];
-      if (forward) {      // T^T w: w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q)
-        for (int j = 0; j < nbw; ++j) {
-          double t = w[j];
-          for (int q = 0; q < j; ++q) t -= Gp[q + j * kBNB] * ww[q];
-          ww[j] = tp[j] * t;
-        }
-      } else {            // T w: w''_j = tau_j (w_j - sum_{q>j} G[j,q] w''_q)
-        for (int j = nbw - 1; j >= 0; --j) {
-          double t = w[j];
-          for (int q = j + 1; q < nbw; ++q) t -= Gp[j + q * kBNB] * ww[q];
-          ww[j] = tp[j] * t;
+      const int j = lane;
+      const bool act = j < nbw;
+      float t = act ? w[j] : 0.f;
+      const float tj = act ? (float)tau[k0 + j] : 0.f;
+      float gl[kBNB];
+#pragma unroll
+      for (int q = 0; q < kBNB; ++q)
+        gl[q] = (act && q < nbw) ? (float)(forward ? Gp[q + j * kBNB] : Gp[j + q * kBNB]) : 0.f;
+      float wf = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < kBNB; ++s2) {
+        const int q = forward ? s2 : kBNB - 1 - s2;
+        if (q < nbw) {                                 // uniform over the warp
+          const float fin = __shfl_sync(0xffffffffu, t * tj, q);
+          if (forward ? (j > q) : (j < q)) t = fmaf(-gl[q], fin, t);
+          if (j == q) wf = fin;
         }
       }
-      for (int j = 0; j < nbw; ++j) w[j] = (float)ww[j];
+      if (act) w[j] = wf;
     }
     __syncthreads();
     for (int i = tid; i < M; i += kThreads) {
@@ -558,10 +572,18 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
     double err = 1.0, prev = 1e300;
     for (int it = 0; it < bp.max_it; ++it) {
       // f = b - r - A x (FP64), one thread per row
+      // (four partial sums: the dependent FP64 chain is a quarter as long)
       for (int i = tid; i < m; i += kThreads) {
-        double acc = pr.b[i] - r[i];
-        for (int j = 0; j < n; ++j) acc = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], acc);
-        f[i] = (float)acc;
+        double a0 = pr.b[i] - r[i], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = 0;
+        for (; j + 3 < n; j += 4) {
+          a0 = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], a0);
+          a1 = fma(-pr.A[SLQR_IDX(i, j + 1, pr.lda)], x[j + 1], a1);
+          a2 = fma(-pr.A[SLQR_IDX(i, j + 2, pr.lda)], x[j + 2], a2);
+          a3 = fma(-pr.A[SLQR_IDX(i, j + 3, pr.lda)], x[j + 3], a3);
+        }
+        for (; j < n; ++j) a0 = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], a0);
+        f[i] = (float)((a0 + a1) + (a2 + a3));
       }
       // g = -A^T r (FP64), one warp per column
       for (int j = warp; j < n; j += kBWarps) {
