@@ -195,17 +195,29 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         if (c >= nbw) continue;
         if (c == j) {
           const double sc = scl[j];
-          double S = 0.0;
-          for (int r = j + lane; r < M; r += 32) {
+          double S = 0.0, S1 = 0.0;                    // two chains
+          int r = j + lane;
+          for (; r + 32 < M; r += 64) {
+            const double xs = (double)x[r] * sc, xs1 = (double)x[r + 32] * sc;
+            S = fma(xs, xs, S);
+            S1 = fma(xs1, xs1, S1);
+          }
+          if (r < M) {
             const double xs = (double)x[r] * sc;
             S = fma(xs, xs, S);
           }
-          S = b_warp_sum(S);
+          S = b_warp_sum(S + S1);
           if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : sqrt(S) * sinv[j];   // exact rescale
         } else {
           const T *col = Ps + c * kBMaxRows;
-          T acc = T(0);
-          for (int r = j + 1 + lane; r < M; r += 32) acc = fma(x[r], col[r], acc);
+          T acc = T(0), acc1 = T(0);                   // two chains
+          int r = j + 1 + lane;
+          for (; r + 32 < M; r += 64) {
+            acc = fma(x[r], col[r], acc);
+            acc1 = fma(x[r + 32], col[r + 32], acc1);
+          }
+          if (r < M) acc = fma(x[r], col[r], acc);
+          acc += acc1;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
           if (lane == 0) dots[c] = (double)acc;
@@ -291,6 +303,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         for (int a = 0; a < kBNB; ++a) acc[a] = T(0);
         if (col < NC) {
           const T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (const T *)(Bcol + k0);
+#pragma unroll 4
           for (int r = g8; r < M; r += kBRowGroups) {
             const T cv = C[prow(r)];
 #pragma unroll
@@ -330,6 +343,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
           T w[kBNB];
 #pragma unroll
           for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
+#pragma unroll 4
           for (int r = g8; r < M; r += kBRowGroups) {
             const int pr = prow(r);
             T cv = C[pr];
@@ -368,7 +382,7 @@ __device__ void batch_solve_fp64(const double *A, int lda, int n, double *b, dou
 
 constexpr size_t kBSmemBytes = BatchSmem<double>::kBytes;
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)   // two CTAs per SM
 batch_factor_fp64_kernel(BatchParams bp) {
   extern __shared__ __align__(16) char smraw[];
   __shared__ int s_item;
@@ -433,8 +447,16 @@ __device__ __forceinline__ float mixed_v(const float *Af, int m, const double *u
 }
 
 // y <- Q^T y (forward = true) or y <- Q y, panel by panel, FP32 arithmetic.
+// Per panel each thread loads the V entries of its rows (at most two: m <=
+// 512) once, all in flight, and keeps them in registers for both products:
+// w = V^T y (per-thread partials, a halving exchange over the warp, then the
+// 8 warp totals), w' = T^T w or T w on warp 0, then y -= V w'.  red holds
+// kBWarps * kBNB floats.
+constexpr int kBRowsPerThread = kBMaxRows / kThreads;
+static_assert(kBRowsPerThread * kThreads == kBMaxRows, "rows per thread");
+
 __device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, const double *tau,
-                              const double *up, float *y, float *w, bool forward) {
+                              const double *up, float *y, float *red, bool forward) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = num_reflectors(m, n);
   const int np = num_panels(K, kBNB);
@@ -443,14 +465,39 @@ __device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, co
     const int k0 = pnl * kBNB;
     const int nbw = min(kBNB, K - k0);
     const int M = m - k0;
-    // w[a] = sum_i V(i, a) y[k0 + i]
-    for (int a = warp; a < nbw; a += kBWarps) {
-      float acc = 0.f;
-      for (int i = lane; i < M; i += 32) acc = fmaf(mixed_v(Af, m, up, k0, nbw, i, a), y[k0 + i], acc);
+    float vr[kBRowsPerThread][kBNB];
+    float yv[kBRowsPerThread];
+    float acc[kBNB];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) w[a] = acc;
+    for (int a = 0; a < kBNB; ++a) acc[a] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kBRowsPerThread; ++t) {
+      const int i = tid + t * kThreads;
+      const bool in = i < M;
+#pragma unroll
+      for (int a = 0; a < kBNB; ++a) {
+        float v = 0.f;
+        if (in && a < nbw && i >= a)
+          v = (i == a) ? (float)up[k0 + a] : Af[SLQR_IDX(k0 + i, k0 + a, m)];
+        vr[t][a] = v;
+      }
+      yv[t] = in ? y[k0 + i] : 0.f;
+#pragma unroll
+      for (int a = 0; a < kBNB; ++a) acc[a] = fmaf(vr[t][a], yv[t], acc[a]);
     }
+    // halving exchange: lanes 2a, 2a + 1 end with the warp's total of acc[a]
+#pragma unroll
+    for (int h = 8, mask = 16; h >= 1; h >>= 1, mask >>= 1) {
+      const bool hi = (lane & mask) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const float send = hi ? acc[i] : acc[i + h];
+        const float keep = hi ? acc[i + h] : acc[i];
+        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+      }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    if ((lane & 1) == 0) red[warp * kBNB + (lane >> 1)] = acc[0];
     __syncthreads();
     // T^T w (forward) or T w, right-looking in FP32 on warp 0: lane j holds
     // w_j and its column (forward) or row of G; at step q lane q's value is
@@ -459,7 +506,11 @@ __device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, co
       const double *Gp = G + (size_t)pnl * kBNB * kBNB;
       const int j = lane;
       const bool act = j < nbw;
-      float t = act ? w[j] : 0.f;
+      float t = 0.f;
+      if (act) {
+#pragma unroll
+        for (int w8 = 0; w8 < kBWarps; ++w8) t += red[w8 * kBNB + j];
+      }
       const float tj = act ? (float)tau[k0 + j] : 0.f;
       float gl[kBNB];
 #pragma unroll
@@ -475,38 +526,78 @@ __device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, co
           if (j == q) wf = fin;
         }
       }
-      if (act) w[j] = wf;
+      __syncwarp();
+      if (act) red[j] = wf;                           // (every lane has read red)
     }
     __syncthreads();
-    for (int i = tid; i < M; i += kThreads) {
-      float v = y[k0 + i];
-      for (int a = 0; a < nbw; ++a) v = fmaf(-mixed_v(Af, m, up, k0, nbw, i, a), w[a], v);
-      y[k0 + i] = v;
+    float wv[kBNB];
+#pragma unroll
+    for (int a = 0; a < kBNB; ++a) wv[a] = (a < nbw) ? red[a] : 0.f;
+#pragma unroll
+    for (int t = 0; t < kBRowsPerThread; ++t) {
+      const int i = tid + t * kThreads;
+      if (i < M) {
+        float v = yv[t];
+#pragma unroll
+        for (int a = 0; a < kBNB; ++a) v = fmaf(-vr[t][a], wv[a], v);
+        y[k0 + i] = v;
+      }
     }
     __syncthreads();
   }
 }
 
-// Triangular solves with R = triu(Af[0:n, 0:n]) in FP32, column-oriented.
-// upper == true: R x = y (back); false: R^T x = y (forward).  y is replaced.
+// Triangular solves with R = triu(Af[0:n, 0:n]) in FP32, in blocks of 32
+// rows.  upper == true: R x = y (back); false: R^T x = y (forward).  y is
+// replaced; a zero diagonal gives x_i = 0 and returns true.  Per block, warp
+// 0 solves the 32 x 32 diagonal block with the block's entries of R in
+// registers (lane l = row; at each step one lane's x is final and is
+// broadcast), then every thread updates the rows not yet solved.
 __device__ bool mixed_trsv(const float *Af, int m, int n, float *y, bool upper) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool zero = false;
-  for (int s = 0; s < n; ++s) {
-    const int i = upper ? n - 1 - s : s;
-    const float d = Af[SLQR_IDX(i, i, m)];
-    if (d == 0.f) zero = true;
-    if (tid == 0) y[i] = (d != 0.f) ? y[i] / d : 0.f;
+  const int nblk = (n + 31) / 32;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int i0 = upper ? max(0, n - 32 * (bi + 1)) : 32 * bi;
+    const int nb = upper ? (n - 32 * bi) - i0 : min(32, n - i0);
+    if (warp == 0) {
+      const int i = i0 + lane;
+      const bool act = lane < nb;
+      float rv[32];
+#pragma unroll
+      for (int s = 0; s < 32; ++s) {
+        // upper: R[i, i0+s] for s > lane; lower: R^T[i, i0+s] = R[i0+s, i] for s < lane
+        const bool need = act && s < nb && (upper ? s > lane : s < lane);
+        rv[s] = need ? (upper ? Af[SLQR_IDX(i, i0 + s, m)] : Af[SLQR_IDX(i0 + s, i, m)]) : 0.f;
+      }
+      const float d = act ? Af[SLQR_IDX(i, i, m)] : 1.f;
+      float yl = act ? y[i] : 0.f;
+      if (__any_sync(0xffffffffu, act && d == 0.f)) zero = true;
+      float xl = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < 32; ++s2) {
+        const int s = upper ? 31 - s2 : s2;
+        if (s < nb) {                                  // uniform over the warp
+          const float xs = __shfl_sync(0xffffffffu, (d != 0.f) ? yl / d : 0.f, s);
+          if (lane == s) xl = xs;
+          if (upper ? lane < s : lane > s) yl = fmaf(-rv[s], xs, yl);
+        }
+      }
+      if (act) y[i] = xl;
+    }
     __syncthreads();
-    const float yi = y[i];
-    if (upper) {
-      for (int l = tid; l < i; l += kThreads) y[l] = fmaf(-Af[SLQR_IDX(l, i, m)], yi, y[l]);
-    } else {
-      for (int l = i + 1 + tid; l < n; l += kThreads) y[l] = fmaf(-Af[SLQR_IDX(i, l, m)], yi, y[l]);
+    // rows not yet solved: upper -> [0, i0), lower -> [i0 + nb, n)
+    const int r0 = upper ? 0 : i0 + nb, r1 = upper ? i0 : n;
+    for (int l = r0 + tid; l < r1; l += kThreads) {
+      float v = y[l];
+#pragma unroll 8
+      for (int s = 0; s < nb; ++s)
+        v = fmaf(-(upper ? Af[SLQR_IDX(l, i0 + s, m)] : Af[SLQR_IDX(i0 + s, l, m)]), y[i0 + s], v);
+      y[l] = v;
     }
     __syncthreads();
   }
-  return zero;
+  return __syncthreads_or(zero);
 }
 
 __device__ double block_max_abs(double v, double *red) {
@@ -522,7 +613,7 @@ __device__ double block_max_abs(double v, double *red) {
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)   // two CTAs per SM
 batch_factor_mixed_kernel(BatchMixedParams bp) {
   extern __shared__ __align__(16) char smraw[];
   __shared__ int s_item;
@@ -563,7 +654,7 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
     float *f = (float *)(dx + kBMaxRows); // m   f, then d = Q^T f, then dr
     float *g = f + kBMaxRows;             // n   g, then h
     float *e = g + kBMaxRows;             // m
-    float *w = e + kBMaxRows;             // kBNB
+    float *w = e + kBMaxRows;             // kBWarps * kBNB (apply_q reductions)
     // r = 0, x = 0: the first sweep is the plain QR solve (see mixed.cu)
     for (int i = tid; i < m; i += kThreads) r[i] = 0.0;
     for (int i = tid; i < n; i += kThreads) x[i] = 0.0;
