@@ -17,6 +17,11 @@
 //  * larger problems run one per stream from a pool of streams (each with its
 //    own context and workspace), so they overlap with each other and with
 //    the batched launches;
+//  * latency routing: one CTA of the batched launch factors a problem at the
+//    FP64 rate of a single SM, while the stream path spreads it over many
+//    SMs; so while at most half of the streams are busy, a small problem with
+//    m * n >= kRouteMN takes the stream path (lower latency on an idle GPU),
+//    and under load it joins the batch (higher throughput);
 //  * residency: a FACTOR request keeps its factorization (A in H12 form, up,
 //    compact-WY store) on the device under a handle until RELEASE; SOLVE
 //    requests reuse it (Q^T b, back-substitution);
@@ -94,6 +99,11 @@ struct Server {
 };
 
 static const size_t kAlign = 256;
+// Smallest m * n a batch-sized problem needs to be sent down the stream path
+// when the streams are idle: about where one SM's FP64 time for the
+// factorization (2 m n^2 flops at ~8 GFLOP/s) overtakes the stream path's
+// per-column latency (~8-10 us per column plus launches).
+static const long long kRouteMN = 60000;
 
 static double *pool_alloc(Server *S, size_t bytes, cudaStream_t s) {
   void *p = nullptr;
@@ -227,7 +237,13 @@ static void admit(Server *S) {
       continue;
     }
     if (budget && S->used_bytes + bytes > budget) break;   // wait for memory to free up
-    const bool small = (r.m <= slqr_batch_max_rows());
+    bool small = (r.m <= slqr_batch_max_rows());
+    if (small && (long long)r.m * r.n >= kRouteMN) {
+      int busy = 0;                                  // units in flight on the stream pool
+      for (const Unit &u : S->inflight)
+        if (u.stream != S->bstream[0] && u.stream != S->bstream[1]) ++busy;
+      if (2 * busy < S->nstreams) small = false;
+    }
     const int pi = (r.prec == SLQR_FP32) ? 1 : 0;
     const int si = small ? -1 : (S->rr++ % S->nstreams);
     cudaStream_t s = small ? S->bstream[pi] : S->streams[si];
