@@ -414,7 +414,7 @@ size_t slqr_server_bytes_in_use(slqr_ctx *ctx);
  * nothing: the caller passes the inputs and outputs, and every other buffer
  * the factorization needs (barrier counter, reduction records, compact-WY
  * store when wy is NULL, partial sums) lives in one fixed array of about
- * 6.9 MB that the library declares in device memory.  Every GPU that loads
+ * 12.1 MB that the library declares in device memory.  Every GPU that loads
  * libslqr holds that array until the process exits.
  *   m, n     m >= n >= 0, m <= slqr_noalloc_max_rows() (8192),
  *            n <= slqr_noalloc_max_cols() (1024); larger sizes return
