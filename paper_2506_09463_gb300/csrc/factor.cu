@@ -157,12 +157,20 @@ panel_kernel(PanelParams p) {
   T *Ps = (T *)smem_raw;                      // [NB][R] column-major panel slice
   double *Gloc = (double *)(smem_raw + ((size_t)NB * p.R * sizeof(T) + 15) / 16 * 16);
                                               // [NB][NB] local Gram terms
-  // lane partials of phase 1: the dots in the storage precision (an FP32
-  // factorization adds them on the FP32 pipe), the norm in FP64
+  // Per-column arithmetic (partial sums, norm, reduction, pivot, multipliers)
+  // runs in the storage precision: an FP32 factorization keeps these chains
+  // on the FP32 pipe (an FP64 operation waits tens of cycles on GB300, and
+  // the chain of one column is the panel's critical path).  The norm stays
+  // overflow-safe through the power-of-two column scale; a column whose scale
+  // is extreme for FP32 (|E| > 60: s^2 or b could leave the FP32 range) forms
+  // its pivot and multipliers in FP64.
   using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+  constexpr bool kF32 = std::is_same<T, float>::value;
   __shared__ Acc s_lane[NB][33];
-  __shared__ double s_nlane[32];
-  __shared__ double s_part[GROUPS][NB];
+  __shared__ Acc s_nlane[32];
+  __shared__ Acc s_part[GROUPS][NB];
+  __shared__ unsigned s_mx[GROUPS][NB];       // column-scale reduction
+  __shared__ Acc s_pivc[3];                   // cl, up, 1/b in Acc (FP32 pivot)
   __shared__ double s_sig[NB];                // sigma per column
   __shared__ double s_up[NB];
   __shared__ double s_prow[NB];               // pivot row of the current column
@@ -229,14 +237,15 @@ panel_kernel(PanelParams p) {
     unsigned mx = 0;
 #pragma unroll
     for (int t = 0; t < QMAX; ++t) mx = max(mx, v[t]);
-    s_part[g][c] = (double)mx;
+    s_mx[g][c] = mx;
   }
   __syncthreads();
   if (tid < NB) {
     unsigned mx = 0;
-    for (int g = 0; g < GROUPS; ++g) mx = max(mx, (unsigned)s_part[g][tid]);
+    for (int g = 0; g < GROUPS; ++g) mx = max(mx, s_mx[g][tid]);
     int E = (int)((mx >> 20) & 0x7ff) - 1023;        // exponent of the largest |entry|
-    E = min(max(E, -1000), 1022);
+    // (FP32: 2^-E and 2^E must both be normal floats)
+    E = kF32 ? min(max(E, -126), 126) : min(max(E, -1000), 1022);
     s_E[tid] = E;
     s_sc[tid] = pow2(-E);
   }
@@ -251,13 +260,13 @@ panel_kernel(PanelParams p) {
 
     // ---- phase 1 ---------------------------------------------------------
     {
-      // dots in the storage type T, the norm in FP64 on scaled entries
+      // dots in the storage type T, the norm on scaled entries
       T acc[CPW];
 #pragma unroll
       for (int t = 0; t < CPW; ++t) acc[t] = T(0);
-      double nacc = 0.0;
+      Acc nacc = Acc(0);
       const bool norm_warp = (warp == (j % NW));
-      const double sc = s_sc[j];
+      const Acc sc = (Acc)s_sc[j];
       for (int r = r_tail + lane; r < RO; r += 32) {
         const T xv = x[r];
 #pragma unroll
@@ -266,12 +275,12 @@ panel_kernel(PanelParams p) {
           if (c < nbw && c != j) acc[t] = fma(xv, Ps[c * R + r], acc[t]);
         }
         if (norm_warp) {
-          const double xs = (double)xv * sc;
+          const Acc xs = (Acc)xv * sc;
           nacc = fma(xs, xs, nacc);
         }
       }
       if (cta == 0 && norm_warp && lane == 0) {     // the pivot entry joins the norm
-        const double xs = (double)x[j] * sc;
+        const Acc xs = (Acc)x[j] * sc;
         nacc = fma(xs, xs, nacc);
       }
 #pragma unroll
@@ -287,26 +296,24 @@ panel_kernel(PanelParams p) {
       // thread (c, quarter) sums 32 / LQ lane partials; then one thread per c
       const int c = tid / LQ, qq = tid - c * LQ;
       constexpr int LPQ = 32 / LQ;
+      Acc v = Acc(0);
       if (c == j) {
-        double v = 0.0;
 #pragma unroll
         for (int l = 0; l < LPQ; ++l) v += s_nlane[qq * LPQ + l];
-        s_part[qq][c] = v;
       } else {
-        Acc v = Acc(0);
 #pragma unroll
         for (int l = 0; l < LPQ; ++l) v += s_lane[c][qq * LPQ + l];
-        s_part[qq][c] = (double)v;
       }
+      s_part[qq][c] = v;
     }
     __syncthreads();
     if (tid < nbw) {
       const int c = tid;
-      double v = s_part[0][c];
+      Acc v = s_part[0][c];
 #pragma unroll
       for (int qq = 1; qq < LQ; ++qq) v += s_part[qq][c];
-      if (c >= j) publish(myrec + c, v);              // norm (c == j) and dots
-      else Gloc[c + j * NB] = v;                      // Gram term: kept
+      if (c >= j) publish(myrec + c, (double)v);      // norm (c == j) and dots
+      else Gloc[c + j * NB] = (double)v;              // Gram term: kept
     }
 
     // ---- phase 2 ---------------------------------------------------------
@@ -353,15 +360,15 @@ panel_kernel(PanelParams p) {
       for (int t = 0; t < QMAX; ++t)
         v[t] = (sums && q0 + t < q1) ? __ldcg(rec + (size_t)(q0 + t) * RECW + c) : 0.0;
       double pv = (tid < nbw) ? __ldcg(prow + tid) : 0.0;
-      double acc = 0.0;
+      Acc acc = Acc(0);
       bool miss = false;
 #pragma unroll
       for (int t = 0; t < QMAX; ++t) {
         miss |= is_unset(v[t]);
-        acc += v[t];
+        acc += (Acc)v[t];
       }
       if (miss) {
-        acc = 0.0;
+        acc = Acc(0);
         for (int t = 0; t < QMAX && ok; ++t) {
           if (!(sums && q0 + t < q1)) continue;
           double x;
@@ -370,7 +377,7 @@ panel_kernel(PanelParams p) {
             if (++it > kSpinLimit) { ok = false; break; }
             __nanosleep(32);
           }
-          acc += x;
+          acc += (Acc)x;
         }
       }
       if (tid < nbw) {
@@ -388,13 +395,27 @@ panel_kernel(PanelParams p) {
         return;
       }
     }
+    // FP32 pivot unless the column's scale is extreme (uniform over the CTA)
+    const bool fast = kF32 && abs(s_E[j]) <= 60;
     if (tid == 0) {
-      double S = s_part[0][j];
-      for (int g = 1; g < GROUPS; ++g) S += s_part[g][j];
-      const bool defined = (S != 0.0);
+      Acc Sa = s_part[0][j];
+      for (int g = 1; g < GROUPS; ++g) Sa += s_part[g][j];
+      const bool defined = (Sa != Acc(0));
       double cl = 0.0, upk = 0.0, rb = 0.0;
-      if (defined) {
-        const double sn = sqrt(S) * pow2(s_E[j]);
+      if (defined && fast) {
+        const Acc sn = sqrt(Sa) * (Acc)pow2(s_E[j]);
+        const Acc x0 = (Acc)s_prow[j];
+        const Acc clc = (x0 > Acc(0)) ? -sn : sn;
+        const Acc upc = x0 - clc;
+        const Acc rbc = Acc(1) / (upc * clc);         // 1 / b
+        s_pivc[0] = clc;
+        s_pivc[1] = upc;
+        s_pivc[2] = rbc;
+        cl = clc;
+        upk = upc;
+        rb = rbc;
+      } else if (defined) {
+        const double sn = sqrt((double)Sa) * pow2(s_E[j]);
         const double x0 = s_prow[j];
         cl = (x0 > 0.0) ? -sn : sn;
         upk = x0 - cl;
@@ -413,10 +434,12 @@ panel_kernel(PanelParams p) {
     if (tid < nbw) {
       const int c = tid;
       if (c > j) {
-        double D = s_part[0][c];
+        Acc D = s_part[0][c];
 #pragma unroll
         for (int g = 1; g < GROUPS; ++g) D += s_part[g][c];
-        s_sig[c] = defined ? (upk * s_prow[c] + D) * rb : 0.0;
+        if (!defined) s_sig[c] = 0.0;
+        else if (fast) s_sig[c] = (double)((s_pivc[1] * (Acc)s_prow[c] + D) * s_pivc[2]);
+        else s_sig[c] = (upk * s_prow[c] + (double)D) * rb;
       } else if (c < j && cta == 0) {
         // G[c, j] = v_c^T v_j = v_c[k] up_j + sum_{r > k} v_c[r] x_r: the first
         // term is added once, by CTA 0
