@@ -98,6 +98,12 @@ __device__ __forceinline__ void b_group8_sum16(T (&acc)[kBNB], int g) {
   }
 }
 
+__device__ __forceinline__ float b_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ double b_warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -116,7 +122,7 @@ struct BatchSmem {
   static constexpr int kG = kBNB * kBNB;                // G[q][j] (ld kBNB)
   // T copies of the panel's G and tau for W' = T^T W (phase B)
   static constexpr size_t kBytesT = (size_t)(kPanel + kW + kG + kBNB) * sizeof(T);
-  static constexpr int kMisc = 6 * kBNB + 8;  // dots, sigma, tau, up, scale, 1/scale, norm
+  static constexpr int kMisc = 7 * kBNB + 8;  // dots, sigma, tau, up, scale, 1/scale, fast, norm
   static constexpr size_t kBytes = align_up_c(kBytesT, 16) + (size_t)(kG + kMisc) * sizeof(double);
 };
 
@@ -149,7 +155,13 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
   double *ups = tau + kBNB;
   double *scl = ups + kBNB;         // per-column scale 2^-E of the panel
   double *sinv = scl + kBNB;        // and its inverse 2^E
-  double *misc = sinv + kBNB;       // [0] = norm
+  double *fst = sinv + kBNB;        // 1: FP32 pivot for this column (T == float, |E| <= 60)
+  double *misc = fst + kBNB;        // [0] = norm
+  // An FP32 factorization (T == float) forms the norm, the pivot and the
+  // multipliers in FP32 (its per-column chain then stays off the FP64 pipe);
+  // a column whose power-of-two scale is extreme for FP32 forms its pivot in
+  // FP64.  T == double: everything FP64.
+  constexpr bool kF32 = std::is_same<T, float>::value;
   const int K = num_reflectors(m, n);
   for (int k = K + tid; k < n; k += kThreads) up_out[k] = 0.0;
 
@@ -179,9 +191,11 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         mx = __reduce_max_sync(0xffffffffu, mx);
         if (lane == 0) {
           int E = (int)((mx >> 20) & 0x7ff) - 1023;
-          E = min(max(E, -1000), 1022);
+          // (FP32: 2^-E and 2^E both normal floats)
+          E = kF32 ? min(max(E, -126), 126) : min(max(E, -1000), 1022);
           scl[c] = b_pow2(-E);
           sinv[c] = b_pow2(E);
+          fst[c] = (kF32 && E >= -60 && E <= 60) ? 1.0 : 0.0;
         }
       }
     }
@@ -194,20 +208,24 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         const int c = warp + kBWarps * t;
         if (c >= nbw) continue;
         if (c == j) {
-          const double sc = scl[j];
-          double S = 0.0, S1 = 0.0;                    // two chains
+          const T sc = (T)scl[j];
+          T S = T(0), S1 = T(0);                       // two chains
           int r = j + lane;
           for (; r + 32 < M; r += 64) {
-            const double xs = (double)x[r] * sc, xs1 = (double)x[r + 32] * sc;
+            const T xs = x[r] * sc, xs1 = x[r + 32] * sc;
             S = fma(xs, xs, S);
             S1 = fma(xs1, xs1, S1);
           }
           if (r < M) {
-            const double xs = (double)x[r] * sc;
+            const T xs = x[r] * sc;
             S = fma(xs, xs, S);
           }
           S = b_warp_sum(S + S1);
-          if (lane == 0) misc[0] = (S == 0.0) ? 0.0 : sqrt(S) * sinv[j];   // exact rescale
+          if (lane == 0) {                             // exact rescale by 2^E
+            if (S == T(0)) misc[0] = 0.0;
+            else if (kF32 && fst[j] != 0.0) misc[0] = (double)(sqrt(S) * (T)sinv[j]);
+            else misc[0] = sqrt((double)S) * sinv[j];
+          }
         } else {
           const T *col = Ps + c * kBMaxRows;
           T acc = T(0), acc1 = T(0);                   // two chains
@@ -225,20 +243,39 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
       }
       __syncthreads();
       const double s = misc[0];
-      const double x0 = (double)x[j];
       const bool defined = (s != 0.0);
       double cl = 0.0, upk = 0.0, tk = 0.0;
-      if (defined) {
-        cl = (x0 > 0.0) ? -s : s;
-        upk = x0 - cl;
-        if (warp == 0) tk = -1.0 / (upk * cl);        // tau = -1/b (warp 0 uses it)
-      }
-      if (tid < nbw) {
-        const int c = tid;
-        const double pr_c = (double)Ps[c * kBMaxRows + j];
-        // sigma_c = (up p_c + D_c) / b = -(up p_c + D_c) tau
-        if (c > j) sig[c] = defined ? -(upk * pr_c + dots[c]) * tk : 0.0;
-        else if (c < j) Gs[c + j * kBNB] = pr_c * upk + dots[c];
+      if (kF32 && fst[j] != 0.0) {                     // FP32 pivot and multipliers
+        const T sT = (T)s, x0 = x[j];
+        T clT = T(0), upT = T(0), tkT = T(0);
+        if (defined) {
+          clT = (x0 > T(0)) ? -sT : sT;
+          upT = x0 - clT;
+          if (warp == 0) tkT = T(-1) / (upT * clT);    // tau = -1/b (warp 0 uses it)
+        }
+        if (tid < nbw) {
+          const int c = tid;
+          const T pr_c = Ps[c * kBMaxRows + j];
+          if (c > j) sig[c] = defined ? (double)(-(upT * pr_c + (T)dots[c]) * tkT) : 0.0;
+          else if (c < j) Gs[c + j * kBNB] = (double)(pr_c * upT + (T)dots[c]);
+        }
+        cl = clT;
+        upk = upT;
+        tk = tkT;
+      } else {
+        const double x0 = (double)x[j];
+        if (defined) {
+          cl = (x0 > 0.0) ? -s : s;
+          upk = x0 - cl;
+          if (warp == 0) tk = -1.0 / (upk * cl);      // tau = -1/b (warp 0 uses it)
+        }
+        if (tid < nbw) {
+          const int c = tid;
+          const double pr_c = (double)Ps[c * kBMaxRows + j];
+          // sigma_c = (up p_c + D_c) / b = -(up p_c + D_c) tau
+          if (c > j) sig[c] = defined ? -(upk * pr_c + dots[c]) * tk : 0.0;
+          else if (c < j) Gs[c + j * kBNB] = pr_c * upk + dots[c];
+        }
       }
       __syncthreads();
       if (defined) {
