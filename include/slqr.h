@@ -313,8 +313,8 @@ void slqr_batch_plan_destroy(slqr_batch_plan *plan);
 /*
  * slqr_lstsq_mixed -- least squares min ||A x - b|| for one large problem in
  * mixed precision, error stated against FP64.  The H12 factorization
- * (Alg. 2) runs on an FP32 copy of A: the reflector norm, up, b and the
- * compact-WY coefficients are FP64, the trailing-update products FP32.  The
+ * (Alg. 2) runs on an FP32 copy of A (FP32 arithmetic; up and the compact-WY
+ * coefficients are stored in FP64).  The
  * FP64 solution is then recovered by iterative refinement of the augmented
  * system [I A; A^T 0][r; x] = [b; 0] with residuals computed in FP64 from A
  * and corrections through the FP32 factorization.

@@ -127,8 +127,10 @@ struct BatchSmem {
 };
 
 // The H12 factorization of one m x n problem by one CTA (see the file
-// header).  Reflector constants (norm, cl, up, b, tau, sigma) are FP64; dot
-// products and updates run in T.  When G_out/tau_out are given, each panel's
+// header).  T == double: all FP64.  T == float: dot products, updates, the
+// norm, cl, up, b and sigma in FP32 (FP64 for a column whose power-of-two
+// scale is extreme for FP32), up, tau and G stored in FP64.  When
+// G_out/tau_out are given, each panel's
 // striu(V^T V) and tau are kept there (the mixed path reuses them to apply Q).
 // Bcol (T == double only) is an extra right-hand-side column updated with the
 // trailing columns, giving Q^T b.
@@ -450,7 +452,7 @@ batch_factor_fp64_kernel(BatchParams bp) {
 
 // --------------------------------------------------------------------------
 // Mixed precision (SLQR_FP32): the factorization runs in FP32 on a scratch
-// copy of A (FP64 reflector constants), and the LS solution is recovered by
+// copy of A (up, tau and G stored in FP64), and the LS solution is recovered by
 // iterative refinement of the augmented system [I A; A^T 0][r; x] = [b; 0]
 // (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64 from the
 // original A, the correction through the FP32 QR:

@@ -1,9 +1,10 @@
 // mixed.cu -- mixed-precision least squares for large matrices
 // (slqr_lstsq_mixed).
 //
-// The factorization (Alg. 2, H12 storage) runs on an FP32 copy of A: reflector
-// norm, up, b and the compact-WY coefficients are FP64, the trailing-update
-// products FP32 (SLQR_FP32: FP32 FMA pipe).  The LS solution is then refined
+// The factorization (Alg. 2, H12 storage) runs on an FP32 copy of A: the
+// trailing-update products and the panel's per-column arithmetic (norm, up, b,
+// multipliers) in FP32, up and the compact-WY coefficients stored in FP64
+// (SLQR_FP32: FP32 FMA pipe).  The LS solution is then refined
 // against the FP64 A with the augmented system [I A; A^T 0][r; x] = [b; 0]
 // (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64, the correction
 // through the FP32 QR, h = R^-T g, d = Q^T f, dx = R^-1 (d[0:n] - h),

@@ -221,8 +221,8 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
                                cudaStream_t stream, int skip = 0);
 size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
 
-// FP32 factorization (FP64 reflector constants) used by the mixed-precision
-// driver.
+// FP32 factorization (up and the compact-WY store in FP64) used by the
+// mixed-precision driver.
 slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
                        cudaStream_t stream);
 
