@@ -358,14 +358,19 @@ slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int l
  * fit waits until memory is freed, and one larger than the whole budget
  * fails with SLQR_EBUSY.  Admitted requests with m <= slqr_batch_max_rows()
  * of one precision share one persistent batched launch; larger ones run one
- * per stream on a pool of streams; all of them overlap on the device.
- * Requests that arrive while others run are admitted as memory frees up.
+ * per stream on a pool of streams (FP64 factorization for either precision);
+ * all of them overlap on the device.  Latency routing: while at most half of
+ * those streams are busy, a batch-sized request with m * n >= 60000 also runs
+ * on a stream (its factorization is spread over many SMs instead of one CTA
+ * of the batched launch).  Requests that arrive while others run are
+ * admitted as memory frees up.
  *
  * A, b and x are HOST pointers owned by the caller; they must stay valid
  * until slqr_poll reports the request done (A and b are copied in at
  * admission; x receives n doubles at completion).  prec: SLQR_FP64, or
  * SLQR_FP32 for FACTOR_SOLVE with m <= slqr_batch_max_rows() (FP32
- * factorization with FP64-residual refinement, see slqr_batch_factor).
+ * factorization with FP64-residual refinement, see slqr_batch_factor, when
+ * the request joins a batched launch; FP64 when it runs on a stream).
  * slqr_poll returns SLQR_PENDING until the request is done, then SLQR_OK with
  * *out filled (out->status is the request's own status) and forgets the
  * ticket; SLQR_ENOTFOUND for an unknown or already collected ticket.
