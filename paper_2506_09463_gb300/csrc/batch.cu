@@ -22,6 +22,8 @@
 // All arithmetic is FP64 (DFMA).
 #include "slqr_internal.cuh"
 
+#include <math_constants.h>
+
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -736,12 +738,18 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
       double dmax = 0.0, xmax = 0.0;
       for (int i = tid; i < n; i += kThreads) {
         x[i] += dx[i];
-        dmax = fmax(dmax, fabs(dx[i]));
-        xmax = fmax(xmax, fabs(x[i]));
+        // a non-finite entry (an FP32 overflow) counts as +inf: never "converged"
+        dmax = fmax(dmax, isfinite(dx[i]) ? fabs(dx[i]) : CUDART_INF);
+        xmax = fmax(xmax, isfinite(x[i]) ? fabs(x[i]) : CUDART_INF);
       }
       for (int i = tid; i < m; i += kThreads) r[i] += (double)f[i];
       dmax = block_max_abs(dmax, red);
       xmax = block_max_abs(xmax, red);
+      if (!isfinite(dmax) || !isfinite(xmax)) {
+        status = SLQR_ENOCONV;
+        err = CUDART_INF;
+        break;
+      }
       err = (xmax > 0.0) ? dmax / xmax : 0.0;
       if (zero) { status = SLQR_ERANK; break; }
       if (err <= bp.tol) { status = SLQR_OK; break; }

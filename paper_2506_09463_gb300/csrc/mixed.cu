@@ -13,6 +13,9 @@
 // u_low) is below 1, for consistent and inconsistent right-hand sides.
 #include "slqr_internal.cuh"
 
+#include <math_constants.h>
+#include <cmath>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -94,8 +97,10 @@ __global__ void update_kernel(float *__restrict__ d, const float *__restrict__ h
     const double v = (double)dx[i];
     const double xn = x[i] + v;
     x[i] = xn;
-    a = fabs(v);
-    c = fabs(xn);
+    // a non-finite entry (an FP32 overflow in the factorization) becomes +inf,
+    // which the max below keeps and the driver reports as non-convergence
+    a = isfinite(v) ? fabs(v) : CUDART_INF;
+    c = isfinite(xn) ? fabs(xn) : CUDART_INF;
   }
   s_dx[threadIdx.x] = a;
   s_x[threadIdx.x] = c;
@@ -603,6 +608,11 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
     for (int k = 0; k < ublocks; ++k) {
       dmax = std::max(dmax, hmax[2 * k]);
       xmax = std::max(xmax, hmax[2 * k + 1]);
+    }
+    if (!std::isfinite(dmax) || !std::isfinite(xmax)) {   // overflow: never "converged"
+      e_cur = HUGE_VAL;
+      status = SLQR_ENOCONV;
+      break;
     }
     e_cur = (xmax > 0.0) ? dmax / xmax : 0.0;
     if (zflag) { status = SLQR_ERANK; break; }

@@ -182,3 +182,40 @@ def test_bf16x3_full_size_8192x4096(ctx):
     st, its, err, x = mixed(ctx, A, b_cons, abi.SLQR_BF16X3)
     assert st == 0, (st, its, err)
     assert float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)) <= 1e3 * 1e2 * EPS
+
+
+@pytest.mark.parametrize("scale_exp", [70, -80])
+def test_mixed_extreme_scales_never_report_a_wrong_answer(ctx, scale_exp):
+    """Every column scaled by 2^70 or 2^-80 (kappa unchanged at 1e3).  The
+    FP32 factorizations do not rescale the matrix, so products of such
+    entries overflow or underflow FP32; the result must then be either the
+    correct solution (1e-10 against the oracle) or SLQR_ENOCONV, never a
+    non-finite or wrong x reported as converged.  Large path and batched
+    path."""
+    from paper_2506_09463_gb300 import abi
+    m, n = 900, 300
+    A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, 1e3, seed=11)
+    As = (A * 2.0 ** scale_exp).t().contiguous().t()
+    x_o = oracle.lstsq(As.cpu().numpy(), b_rand.cpu().numpy())[0]
+    st, its, err, x = mixed(ctx, As, b_rand)
+    assert st in (abi.SLQR_OK, abi.SLQR_ENOCONV), (st, its, err)
+    if st == abi.SLQR_OK:
+        rel = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= 1e-10, (rel, its, err)
+    # the batched FP32 path on a problem of the batch size class
+    mb, nb = 400, 150
+    Ab = As[:mb, :nb].t().contiguous().t()
+    bb = b_rand[:mb].clone()
+    xb_o = oracle.lstsq(Ab.cpu().numpy(), bb.cpu().numpy())[0]
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    errs = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = abi.slqr_batch_factor(ctx.ctx, [mb], [nb], [Ab.data_ptr()], [mb], None, [bb.data_ptr()],
+                               abi.SLQR_FP32, status.data_ptr(), errs.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    ps = int(status.item())
+    assert ps in (abi.SLQR_OK, abi.SLQR_ENOCONV), (ps, float(errs.item()))
+    if ps == abi.SLQR_OK:
+        rel = np.linalg.norm(bb[:nb].cpu().numpy() - xb_o) / np.linalg.norm(xb_o)
+        assert rel <= 1e-10, rel
