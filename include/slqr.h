@@ -62,6 +62,8 @@ typedef int slqr_status;
 #define SLQR_EBUSY     (-6)  /* over the HBM budget of the context */
 #define SLQR_ENOTFOUND (-7)  /* unknown ticket or handle */
 #define SLQR_ENOCONV   (-8)  /* iterative refinement did not reach its tolerance */
+#define SLQR_FALLBACK    2   /* slqr_lstsq_mixed_ex: the mixed-precision refinement
+                                failed and x comes from the opt-in FP64 solve */
 
 typedef struct slqr_ctx slqr_ctx;
 
@@ -337,6 +339,87 @@ void slqr_batch_plan_destroy(slqr_batch_plan *plan);
 slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int lda,
                              const double *b, double *x, int prec, int max_iter, double tol,
                              int *iters, double *err, void *stream);
+
+/*
+ * slqr_lstsq_mixed_ex -- slqr_lstsq_mixed with a choice of refinement method
+ * and an opt-in FP64 fallback, so that every problem gets an answer and the
+ * caller always learns how it was obtained.  The paper factors in one
+ * precision only; the refinement is this library's way of reusing one
+ * low-precision H12 factorization (Alg. 2) for an FP64-accurate LS solution.
+ *
+ * Refinement methods (opts->refine):
+ *   SLQR_REFINE_AUTO    Bjorck sweeps as in slqr_lstsq_mixed; when they do
+ *                       not converge, GMRES-IR from the plain solve
+ *   SLQR_REFINE_BJORCK  Bjorck sweeps only (slqr_lstsq_mixed)
+ *   SLQR_REFINE_GMRES   GMRES-IR only
+ * GMRES-IR (Carson, Higham and Pranesh, three-precision GMRES-based iterative
+ * refinement for least squares, SIAM J. Sci. Comput. 42(6), 2020): each
+ * refinement step forms the residual [f; g] = [b - r - A x; -A^T r] of the
+ * augmented system [I A; A^T 0][r; x] = [b; 0] in FP64 and solves for the
+ * correction with GMRES (FP64 Krylov basis, at most gmres_restart vectors),
+ * left-preconditioned by the augmented matrix of the low-precision QR (one
+ * Bjorck correction, applied in FP64 arithmetic to the FP32 factors).  It
+ * converges where kappa(A) times the factorization's backward error is above
+ * 1 (where the Bjorck sweeps diverge), at the price of one preconditioner
+ * application per Krylov iteration (about as much as one Bjorck sweep).  A
+ * step is accepted when ||dx||_inf <= tol ||x||_inf, or when its inner solve
+ * reached gmres_tol and the step is at the FP64 noise level of the problem,
+ * max(1e-10, 100 kappa_est 2^-53), with kappa_est = max|R_ii| / min|R_ii|.
+ *
+ * Options (opts may be NULL: every field 0):
+ *   refine           SLQR_REFINE_AUTO (0), _BJORCK or _GMRES
+ *   max_sweeps       Bjorck sweeps (<= 0: 30)
+ *   tol              stop at ||dx||_inf <= tol ||x||_inf (<= 0: 1e-14)
+ *   gmres_max_iters  Krylov iterations over all GMRES-IR steps (<= 0: 300)
+ *   gmres_restart    Krylov vectors per GMRES cycle, <= 512 (<= 0:
+ *                    min(gmres_max_iters, 200)); the basis takes
+ *                    (gmres_restart + 1) (m + n) doubles of device memory
+ *   gmres_tol        relative residual of each inner GMRES solve (<= 0: 1e-10)
+ *   fp64_fallback    1: when the refinement fails, solve in FP64 instead
+ *                    (slqr_factor, slqr_apply_qt, slqr_solve_r on a copy of
+ *                    A; m n + 2 m doubles more of device memory) and return
+ *                    SLQR_FALLBACK; 0: return SLQR_ENOCONV
+ * Report (info may be NULL), HOST struct:
+ *   method       how x was obtained: SLQR_REFINE_BJORCK, SLQR_REFINE_GMRES or
+ *                SLQR_REFINE_FP64 (the fallback)
+ *   sweeps       Bjorck sweeps done
+ *   gmres_steps  GMRES-IR refinement steps;  gmres_iters  Krylov iterations
+ *   err          the last refinement step ||dx||_inf / ||x||_inf of the
+ *                mixed-precision refinement (also after a fallback)
+ *   kappa_est    max|R_ii| / min|R_ii| of the low-precision R (0 when
+ *                GMRES-IR did not run)
+ * Returns SLQR_OK (x from the mixed-precision refinement), SLQR_FALLBACK (x
+ * from the FP64 solve), SLQR_ENOCONV (no fallback asked for), SLQR_ERANK, or
+ * the errors of slqr_lstsq_mixed.  Synchronous.  Other arguments as for
+ * slqr_lstsq_mixed.
+ */
+#define SLQR_REFINE_AUTO   0
+#define SLQR_REFINE_BJORCK 1
+#define SLQR_REFINE_GMRES  2
+#define SLQR_REFINE_FP64   3   /* slqr_mixed_info.method only */
+
+typedef struct {
+  int refine;
+  int max_sweeps;
+  double tol;
+  int gmres_max_iters;
+  int gmres_restart;
+  double gmres_tol;
+  int fp64_fallback;
+} slqr_mixed_opts;
+
+typedef struct {
+  int method;
+  int sweeps;
+  int gmres_steps;
+  int gmres_iters;
+  double err;
+  double kappa_est;
+} slqr_mixed_info;
+
+slqr_status slqr_lstsq_mixed_ex(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                const double *b, double *x, int prec, const slqr_mixed_opts *opts,
+                                slqr_mixed_info *info, void *stream);
 
 /*
  * Request loop: continuous batching of least-squares subproblems from many

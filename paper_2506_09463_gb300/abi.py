@@ -29,13 +29,15 @@ SLQR_EBUSY = -6
 SLQR_ENOTFOUND = -7
 
 STATUS_NAMES = {
-    -8: "SLQR_ENOCONV",
+    -8: "SLQR_ENOCONV", 2: "SLQR_FALLBACK",
     SLQR_OK: "SLQR_OK", SLQR_PENDING: "SLQR_PENDING", SLQR_EINVAL: "SLQR_EINVAL",
     SLQR_ENOMEM: "SLQR_ENOMEM", SLQR_ECUDA: "SLQR_ECUDA", SLQR_ETIMEOUT: "SLQR_ETIMEOUT",
     SLQR_ERANK: "SLQR_ERANK", SLQR_EBUSY: "SLQR_EBUSY", SLQR_ENOTFOUND: "SLQR_ENOTFOUND",
 }
 
 SLQR_ENOCONV = -8
+SLQR_FALLBACK = 2
+SLQR_REFINE_AUTO, SLQR_REFINE_BJORCK, SLQR_REFINE_GMRES, SLQR_REFINE_FP64 = 0, 1, 2, 3
 SLQR_REQ_FACTOR, SLQR_REQ_SOLVE, SLQR_REQ_FACTOR_SOLVE, SLQR_REQ_RELEASE = 1, 2, 3, 4
 
 
@@ -44,6 +46,18 @@ class SlqrRequest(ctypes.Structure):
                 ("lda", ctypes.c_int), ("A", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("x", ctypes.c_void_p), ("handle", ctypes.c_uint64), ("prec", ctypes.c_int),
                 ("structure", ctypes.c_int)]
+
+
+class SlqrMixedOpts(ctypes.Structure):
+    _fields_ = [("refine", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
+                ("gmres_max_iters", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("fp64_fallback", ctypes.c_int)]
+
+
+class SlqrMixedInfo(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("sweeps", ctypes.c_int), ("gmres_steps", ctypes.c_int),
+                ("gmres_iters", ctypes.c_int), ("err", ctypes.c_double),
+                ("kappa_est", ctypes.c_double)]
 
 
 class SlqrResult(ctypes.Structure):
@@ -98,6 +112,9 @@ SIGNATURES = [
     ("slqr_server_bytes_in_use", _c_size, [_vp]),
     ("slqr_lstsq_mixed", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int, _c_int, _dbl,
                                   ctypes.POINTER(_c_int), ctypes.POINTER(_dbl), _vp]),
+    ("slqr_lstsq_mixed_ex", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int,
+                                     ctypes.POINTER(SlqrMixedOpts), ctypes.POINTER(SlqrMixedInfo),
+                                     _vp]),
     ("slqr_noalloc_max_rows", _c_int, []),
     ("slqr_noalloc_max_cols", _c_int, []),
 ]
@@ -292,6 +309,18 @@ def slqr_lstsq_mixed(ctx, m, n, A, lda, b, x, prec, max_iter, tol, stream):
     st = _lib.slqr_lstsq_mixed(ctx, m, n, A, lda, b, x, prec, max_iter, tol, ctypes.byref(it),
                                ctypes.byref(err), stream)
     return st, it.value, err.value
+
+
+def slqr_lstsq_mixed_ex(ctx, m, n, A, lda, b, x, prec, stream, refine=SLQR_REFINE_AUTO,
+                        max_sweeps=0, tol=0.0, gmres_max_iters=0, gmres_restart=0,
+                        gmres_tol=0.0, fp64_fallback=0):
+    """Returns (status, info) with info a dict of the SlqrMixedInfo fields."""
+    opts = SlqrMixedOpts(refine, max_sweeps, tol, gmres_max_iters, gmres_restart, gmres_tol,
+                         fp64_fallback)
+    info = SlqrMixedInfo()
+    st = _lib.slqr_lstsq_mixed_ex(ctx, m, n, A, lda, b, x, prec, ctypes.byref(opts),
+                                  ctypes.byref(info), stream)
+    return st, {f: getattr(info, f) for f, _ in SlqrMixedInfo._fields_}
 
 
 def slqr_server_bytes_in_use(ctx) -> int:

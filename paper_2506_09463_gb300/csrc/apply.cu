@@ -177,7 +177,7 @@ extern "C" slqr_status slqr_apply_qt(slqr_ctx *ctx, int m, int n, const double *
                                      int ldb, void *stream) {
   NvtxRange nvtx_range("slqr_apply_qt");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (m < 0 || n < 0 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 0 (m=%d n=%d)", m, n);
   if (nrhs < 0) return fail(ctx, SLQR_EINVAL, "nrhs=%d < 0", nrhs);
   if (n == 0 || nrhs == 0 || m == 0) return SLQR_OK;
@@ -196,7 +196,7 @@ extern "C" slqr_status slqr_apply_qt_stacked(slqr_ctx *ctx, int n, int m_eq, con
                                              int nrhs, double *B, int ldb, void *stream) {
   NvtxRange nvtx_range("slqr_apply_qt_stacked");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);
   if (nrhs < 0) return fail(ctx, SLQR_EINVAL, "nrhs=%d < 0", nrhs);
   const int m = n + m_eq;

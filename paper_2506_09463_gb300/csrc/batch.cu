@@ -745,13 +745,19 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
       for (int i = tid; i < m; i += kThreads) r[i] += (double)f[i];
       dmax = block_max_abs(dmax, red);
       xmax = block_max_abs(xmax, red);
+      // an exact zero on the diagonal of R is a rank statement whatever the
+      // step looks like, so it is reported before the non-finite guard
+      if (zero) {
+        status = SLQR_ERANK;
+        err = (isfinite(dmax) && isfinite(xmax) && xmax > 0.0) ? dmax / xmax : CUDART_INF;
+        break;
+      }
       if (!isfinite(dmax) || !isfinite(xmax)) {
         status = SLQR_ENOCONV;
         err = CUDART_INF;
         break;
       }
       err = (xmax > 0.0) ? dmax / xmax : 0.0;
-      if (zero) { status = SLQR_ERANK; break; }
       if (err <= bp.tol) { status = SLQR_OK; break; }
       if (it >= 2 && err > 0.5 * prev) {        // no longer contracting: FP64 noise level
         status = (err <= kBStallOk) ? SLQR_OK : SLQR_ENOCONV;
@@ -913,7 +919,7 @@ slqr_status batch_factor_locked(slqr_ctx *ctx, int count, const int *m, const in
                                 double *const *up, double *const *b, int prec, int *status,
                                 double *err, void *stream) {
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   return batch_launch(ctx, count, m, n, ntop, A, lda, up, b, prec, status, err, stream);
 }
 
@@ -925,7 +931,7 @@ extern "C" slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m,
                                          void *stream) {
   NvtxRange nvtx_range("slqr_batch_factor");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   return batch_launch(ctx, count, m, n, nullptr, A, lda, up, b, prec, status, err, stream);
 }
 
@@ -936,7 +942,7 @@ extern "C" slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const
                                                  double *err, void *stream) {
   NvtxRange nvtx_range("slqr_batch_factor_stacked");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (count < 0) return fail(ctx, SLQR_EINVAL, "count=%d < 0", count);
   if (count > 0 && (!n || !m_eq)) return fail(ctx, SLQR_EINVAL, "NULL size array");
   std::vector<int> m(std::max(count, 0));
@@ -980,7 +986,7 @@ extern "C" slqr_status slqr_batch_plan_create(slqr_ctx *ctx, int count, const in
                                               double *err, slqr_batch_plan **out) {
   if (!ctx || !out) return SLQR_EINVAL;
   NvtxRange nvtx_range("slqr_batch_plan_create");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   *out = nullptr;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -1028,7 +1034,7 @@ extern "C" slqr_status slqr_batch_plan_launch(slqr_batch_plan *plan, void *strea
   if (!plan) return SLQR_EINVAL;
   NvtxRange nvtx_range("slqr_batch_plan_launch");
   slqr_ctx *ctx = plan->ctx;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaError_t e = cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   int slot = prof_begin(ctx, s);

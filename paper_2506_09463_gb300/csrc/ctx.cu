@@ -113,7 +113,7 @@ using namespace slqr;
 
 extern "C" int slqr_profile(slqr_ctx *ctx, int enable) {
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   prof_collect(ctx);
   if (enable) {
@@ -130,7 +130,7 @@ extern "C" int slqr_profile(slqr_ctx *ctx, int enable) {
 extern "C" slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms,
                                          long long *launches, double *flops) {
   if (!ctx || kernel < 0 || kernel >= kNumKernelIds) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   prof_collect(ctx);
   if (ms) *ms = ctx->prof.ms[kernel];
@@ -141,7 +141,7 @@ extern "C" slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms,
 
 extern "C" long long slqr_launch_count(slqr_ctx *ctx) {
   if (!ctx) return -1;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   return ctx->launch_count;
 }
 
@@ -228,7 +228,7 @@ __global__ void wait_probe_kernel(const unsigned *word, unsigned polls, int *sta
 extern "C" slqr_status slqr_check_bounded_wait(slqr_ctx *ctx, unsigned polls, void *stream) {
   if (!ctx || polls == 0 || polls > (1u << 20)) return SLQR_EINVAL;
   NvtxRange nvtx_range("slqr_check_bounded_wait");
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaError_t e = cudaSetDevice(ctx->device);
   unsigned *word = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&word, sizeof(unsigned));
@@ -254,7 +254,7 @@ extern "C" const char *slqr_last_error(slqr_ctx *ctx) {
 
 extern "C" slqr_status slqr_sync(slqr_ctx *ctx, void *stream) {
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "stream: %s", cudaGetErrorString(e));

@@ -1296,7 +1296,7 @@ extern "C" slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int l
                                    double *wy, void *stream) {
   NvtxRange nvtx_range("slqr_factor");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (m < 0 || n < 0 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 0 (m=%d n=%d)", m, n);
   if (n == 0) return SLQR_OK;
   if (lda < std::max(1, m)) return fail(ctx, SLQR_EINVAL, "lda=%d < m=%d", lda, m);
@@ -1313,7 +1313,7 @@ extern "C" slqr_status slqr_factor_stacked(slqr_ctx *ctx, int n, int m_eq, doubl
                                            double *up, double *wy, void *stream) {
   NvtxRange nvtx_range("slqr_factor_stacked");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (n < 0 || m_eq < 0) return fail(ctx, SLQR_EINVAL, "need n, m_eq >= 0 (n=%d m_eq=%d)", n, m_eq);
   if (n == 0) return SLQR_OK;
   const int m = n + m_eq;
@@ -1352,7 +1352,8 @@ constexpr size_t kNoAllocScratchDoubles = kNoAllocHeadDoubles + kNoAllocRecDoubl
                                           kNoAllocProwDoubles +
                                           kNoAllocWyDoubles + kNoAllocWorkDoubles;
 
-// About 6.9 MB on every device that loads the library, held until exit.
+// kNoAllocScratchDoubles doubles, about 12.1 MB, on every device that loads the
+// library, held until exit.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 static std::mutex g_noalloc_mu;

@@ -23,6 +23,10 @@
 namespace slqr {
 
 constexpr int kRowsPerCta = 256;
+
+// fused multiply-add in the vector type of a kernel (FP32 or FP64)
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 // A refinement whose steps stop contracting is accepted when its last step is
 // below this (the 1e-10 solution-error target): the step then measures the
 // FP64 noise level kappa * eps of an ill-conditioned problem.
@@ -148,17 +152,18 @@ __global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ 
 // --------------------------------------------------------------------------
 constexpr int kQvRows = 128;     // rows of f per CTA (more when m exceeds 128 per SM)
 
-// T of panel p (float, ld nb + 1): column j solves U y = e_j by back
-// substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and
+// T of panel p (VT = float or double, ld nb + 1): column j solves U y = e_j by
+// back substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and
 // y_i = -tau_i sum_{k=i+1..j} G[i,k] y_k (tau = 0: a zero row and column).
+template <typename VT>
 __global__ void __launch_bounds__(64)
-tmat_kernel(const double *__restrict__ wy, int nb, int K, float *__restrict__ Tm) {
+tmat_kernel(const double *__restrict__ wy, int nb, int K, VT *__restrict__ Tm) {
   __shared__ double ys[64][65];
   const int pnl = blockIdx.x, j = threadIdx.x;
   const int nbw = min(nb, K - pnl * nb);
   const double *G = wy + (size_t)pnl * wy_panel_doubles(nb) + (size_t)nb * nb;
   const double *tau = G + (size_t)nb * nb;
-  float *T = Tm + (size_t)pnl * nb * (nb + 1);
+  VT *T = Tm + (size_t)pnl * nb * (nb + 1);
   if (j < nb) {
     for (int i = 0; i < nb; ++i) ys[i][j] = 0.0;
     if (j < nbw) {
@@ -169,16 +174,20 @@ tmat_kernel(const double *__restrict__ wy, int nb, int K, float *__restrict__ Tm
         ys[i][j] = -tau[i] * t;
       }
     }
-    for (int i = 0; i < nb; ++i) T[i + (size_t)j * (nb + 1)] = (float)ys[i][j];
+    for (int i = 0; i < nb; ++i) T[i + (size_t)j * (nb + 1)] = (VT)ys[i][j];
   }
 }
 
+// VT: the type of the vector and of the arithmetic (float for the Bjorck
+// sweeps, double for the preconditioner of GMRES-IR, which must be one fixed
+// linear operator); the reflectors are read from the FP32 factorization.
+template <typename VT>
 struct QvecParams {
   const float *A;        // FP32 factorization (H12 form), ld lda
   const double *up;      // pivot entries of the reflectors
-  const float *Tm;       // explicit T of each panel, nb x nb, ld nb + 1
-  float *f;              // the vector, m entries, updated in place
-  float *part;           // 2 buffers x P CTAs x nb partial sums
+  const VT *Tm;          // explicit T of each panel, nb x nb, ld nb + 1
+  VT *f;                 // the vector, m entries, updated in place
+  VT *part;              // 2 buffers x P CTAs x nb partial sums
   unsigned *bar;         // monotonic arrival counter
   int *status;
   int lda, m, K, nb, np;
@@ -187,17 +196,18 @@ struct QvecParams {
   unsigned bar_base;
 };
 
+template <typename VT>
 __global__ void __launch_bounds__(kThreads)
-qvec_kernel(QvecParams p) {
-  extern __shared__ __align__(16) float qv_smem[];
+qvec_kernel(QvecParams<VT> p) {
+  extern __shared__ __align__(16) unsigned char qv_raw[];
   const int nb = p.nb, R = p.R;
-  const int tsz = nb * (nb + 1);                // one T (multiple of 4 floats)
-  float *Ts2 = qv_smem;                         // [2][nb][nb + 1], 16-byte aligned
-  float *Vs = Ts2 + 2 * tsz;                    // [nb][R + 1]
-  float *fs = Vs + (size_t)nb * (R + 1);        // [R]
-  float *red = fs + R;                          // [kThreads / nb][nb]
-  float *ws = red + kThreads;                   // [nb]
-  float *wt = ws + nb;                          // [nb]
+  const int tsz = nb * (nb + 1);                // one T (a multiple of 16 bytes)
+  VT *Ts2 = (VT *)qv_raw;                       // [2][nb][nb + 1], 16-byte aligned
+  float *Vs = (float *)(Ts2 + 2 * tsz);         // [nb][R + 1]
+  VT *fs = (VT *)(Vs + (size_t)nb * (R + 1));   // [R] (R + 1 odd: 8-byte aligned)
+  VT *red = fs + R;                             // [kThreads / nb][nb]
+  VT *ws = red + kThreads;                      // [nb]
+  VT *wt = ws + nb;                             // [nb]
   __shared__ int s_ok;
   const int tid = threadIdx.x, cta = blockIdx.x;
   const int r0 = cta * R, r1 = min(p.m, r0 + R);
@@ -205,20 +215,21 @@ qvec_kernel(QvecParams p) {
   auto fetch_t = [&](int step, int buf) {
     if (step >= p.np) return;
     const int pnl = p.trans ? step : p.np - 1 - step;
-    const float *src = p.Tm + (size_t)pnl * tsz;
+    constexpr int kPer16 = 16 / (int)sizeof(VT);
+    const VT *src = p.Tm + (size_t)pnl * tsz;
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ts2 + buf * tsz);
-    for (int c = tid; c < tsz / 4; c += kThreads)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst + 16 * c), "l"(src + 4 * c)
-                   : "memory");
+    for (int c = tid; c < tsz / kPer16; c += kThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst + 16 * c),
+                   "l"(src + kPer16 * c) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   fetch_t(0, 0);
   for (int step = 0; step < p.np; ++step) {
     const int pnl = p.trans ? step : p.np - 1 - step;
-    float *Ts = Ts2 + (step & 1) * tsz;
+    VT *Ts = Ts2 + (step & 1) * tsz;
     const int k0 = pnl * nb, nbw = min(nb, p.K - k0);
     const int lo = max(r0, k0), rows = max(0, r1 - lo);
-    float *mypart = p.part + ((size_t)(step & 1) * p.P + cta) * nb;
+    VT *mypart = p.part + ((size_t)(step & 1) * p.P + cta) * nb;
     // phase A: stage V and f of the slice, partial dots V^T f.  The slice
     // starts on a multiple of 64 rows and the columns of A are 128-byte
     // aligned, so whole rows of four go in one 16-byte load (8 in flight per
@@ -265,13 +276,13 @@ qvec_kernel(QvecParams p) {
     __syncthreads();
     {
       const int a = tid % nb, g = tid / nb, G = kThreads / nb;
-      float acc = 0.f;
+      VT acc = 0;
       if (a < nbw)
-        for (int rr = g; rr < rows; rr += G) acc = fmaf(Vs[a * (R + 1) + rr], fs[rr], acc);
+        for (int rr = g; rr < rows; rr += G) acc = fma_t((VT)Vs[a * (R + 1) + rr], fs[rr], acc);
       red[g * nb + a] = acc;
       __syncthreads();
       if (tid < nb) {
-        float v = 0.f;
+        VT v = 0;
         for (int q = 0; q < G; ++q) v += red[q * nb + tid];
         mypart[tid] = v;
       }
@@ -285,8 +296,8 @@ qvec_kernel(QvecParams p) {
     // then W' = T^T W or T W
     {
       const int a = tid % nb, g = tid / nb, G = kThreads / nb;
-      const float *src = p.part + (size_t)(step & 1) * p.P * nb + a;
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+      const VT *src = p.part + (size_t)(step & 1) * p.P * nb + a;
+      VT v0 = 0, v1 = 0, v2 = 0, v3 = 0;
       int q = g;
       for (; q + 3 * G < p.P; q += 4 * G) {
         v0 += __ldcg(src + (size_t)q * nb);
@@ -298,7 +309,7 @@ qvec_kernel(QvecParams p) {
       red[g * nb + a] = (v0 + v1) + (v2 + v3);
       __syncthreads();
       if (tid < nb) {
-        float v = 0.f;
+        VT v = 0;
         for (int gg = 0; gg < G; ++gg) v += red[gg * nb + tid];
         ws[tid] = v;
       }
@@ -307,12 +318,12 @@ qvec_kernel(QvecParams p) {
     {
       // W' entry j: four threads take every fourth term of its dot product
       const int j = tid >> 2, part = tid & 3;
-      float v = 0.f;
+      VT v = 0;
       if (j < nbw) {
         if (p.trans) {
-          for (int q = part; q <= j; q += 4) v = fmaf(Ts[q + j * (nb + 1)], ws[q], v);
+          for (int q = part; q <= j; q += 4) v = fma_t(Ts[q + j * (nb + 1)], ws[q], v);
         } else {
-          for (int q = j + part; q < nbw; q += 4) v = fmaf(Ts[j + q * (nb + 1)], ws[q], v);
+          for (int q = j + part; q < nbw; q += 4) v = fma_t(Ts[j + q * (nb + 1)], ws[q], v);
         }
       }
       v += __shfl_xor_sync(0xffffffffu, v, 1);
@@ -323,15 +334,15 @@ qvec_kernel(QvecParams p) {
     // phase C: f -= V W' on the slice
     if (2 * rows <= kThreads) {                  // two threads per row, half the terms each
       const int rr = tid >> 1, half = tid & 1;
-      float v = 0.f;
+      VT v = 0;
       if (rr < rows)
-        for (int a = half; a < nbw; a += 2) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
+        for (int a = half; a < nbw; a += 2) v = fma_t(-(VT)Vs[a * (R + 1) + rr], wt[a], v);
       v += __shfl_xor_sync(0xffffffffu, v, 1);
       if (rr < rows && half == 0) p.f[lo + rr] = fs[rr] + v;
     } else {
       for (int rr = tid; rr < rows; rr += kThreads) {
-        float v = fs[rr];
-        for (int a = 0; a < nbw; ++a) v = fmaf(-Vs[a * (R + 1) + rr], wt[a], v);
+        VT v = fs[rr];
+        for (int a = 0; a < nbw; ++a) v = fma_t(-(VT)Vs[a * (R + 1) + rr], wt[a], v);
         p.f[lo + rr] = v;
       }
     }
@@ -339,8 +350,10 @@ qvec_kernel(QvecParams p) {
   }
 }
 
+template <typename VT>
 static size_t qvec_smem_bytes(int nb, int R) {
-  return sizeof(float) * (2 * (size_t)nb * (nb + 1) + (size_t)nb * (R + 1) + R + kThreads + 2 * nb);
+  return sizeof(VT) * (2 * (size_t)nb * (nb + 1) + R + kThreads + 2 * (size_t)nb) +
+         sizeof(float) * (size_t)nb * (R + 1);
 }
 
 // FP32 triangular solve with R = triu(A32[0:n, 0:n]) (ld lda) in one
@@ -351,9 +364,10 @@ static size_t qvec_smem_bytes(int nb, int R) {
 // publishes x_b, and every CTA subtracts R_tb x_b (or R_bt^T x_b) from each of
 // its blocks t still to be solved.  An exact zero on the diagonal sets that
 // entry of y to 0 and raises *zero_flag.
+template <typename VT>
 struct TrsvParams {
-  const float *R;
-  float *y;
+  const float *R;        // FP32 factorization; the solve runs in VT arithmetic
+  VT *y;
   int *zero_flag;
   unsigned *bar;
   int *status;
@@ -361,14 +375,14 @@ struct TrsvParams {
   unsigned bar_base;
 };
 
-template <bool UPPER>
+template <bool UPPER, typename VT>
 __global__ void __launch_bounds__(kThreads)
-trsv_coop_kernel(TrsvParams p) {
+trsv_coop_kernel(TrsvParams<VT> p) {
   __shared__ float Rs[64][65];      // diagonal block being solved
   __shared__ float Tu[64][65];      // update tile, [c][r]: R[t r, b c] (UPPER) or R[b c, t r]
-  __shared__ float rdiag[64];
-  __shared__ float xs[64];
-  __shared__ float red[4][64];
+  __shared__ VT rdiag[64];
+  __shared__ VT xs[64];
+  __shared__ VT red[4][64];
   __shared__ int s_ok;
   const int tid = threadIdx.x, cta = blockIdx.x, lane = tid & 31;
   // with one block per CTA the diagonal block stays in shared memory throughout
@@ -385,7 +399,8 @@ trsv_coop_kernel(TrsvParams p) {
       Rs[r][c] = v;
     }
     __syncthreads();
-    if (tid < 64) rdiag[tid] = (tid < rows && Rs[tid][tid] != 0.f) ? 1.f / Rs[tid][tid] : 0.f;
+    if (tid < 64)
+      rdiag[tid] = (tid < rows && Rs[tid][tid] != 0.f) ? (VT)1 / (VT)Rs[tid][tid] : (VT)0;
     __syncthreads();
   };
   auto load_update = [&](int t, int b) {
@@ -406,26 +421,26 @@ trsv_coop_kernel(TrsvParams p) {
     const int b0 = b * 64, rows = min(64, p.n - b0);
     if (b % p.P == cta) {
       if (!one) load_diag(b);
-      if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : 0.f;
+      if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : (VT)0;
       __syncthreads();
       if (tid < 32) {
-        float c0 = xs[lane], c1 = xs[lane + 32];
+        VT c0 = xs[lane], c1 = xs[lane + 32];
         bool zero = false;
         for (int s = 0; s < rows; ++s) {
           const int i = UPPER ? rows - 1 - s : s;
-          const float ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
-          const float rd = rdiag[i];
-          const float xi = ci * rd;
-          zero |= (rd == 0.f);
+          const VT ci = __shfl_sync(0xffffffffu, i < 32 ? c0 : c1, i & 31);
+          const VT rd = rdiag[i];
+          const VT xi = ci * rd;
+          zero |= (rd == (VT)0);
           if (lane == (i & 31)) {
             if (i < 32) c0 = xi; else c1 = xi;
           }
           if (UPPER) {
-            if (lane < i) c0 = fmaf(-Rs[lane][i], xi, c0);
-            if (lane + 32 < i) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+            if (lane < i) c0 = fma_t(-(VT)Rs[lane][i], xi, c0);
+            if (lane + 32 < i) c1 = fma_t(-(VT)Rs[lane + 32][i], xi, c1);
           } else {
-            if (lane > i) c0 = fmaf(-Rs[lane][i], xi, c0);
-            if (lane + 32 > i && lane + 32 < rows) c1 = fmaf(-Rs[lane + 32][i], xi, c1);
+            if (lane > i) c0 = fma_t(-(VT)Rs[lane][i], xi, c0);
+            if (lane + 32 > i && lane + 32 < rows) c1 = fma_t(-(VT)Rs[lane + 32][i], xi, c1);
           }
         }
         if (lane < rows) p.y[b0 + lane] = c0;
@@ -439,7 +454,7 @@ trsv_coop_kernel(TrsvParams p) {
     if (upd_one) load_update(cta, b);
     if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
       return;
-    if (tid < 64) xs[tid] = (tid < rows) ? __ldcg(p.y + b0 + tid) : 0.f;
+    if (tid < 64) xs[tid] = (tid < rows) ? __ldcg(p.y + b0 + tid) : (VT)0;
     __syncthreads();
     for (int t = cta; t < p.nblk; t += p.P) {
       if (UPPER ? t >= b : t <= b) continue;
@@ -449,8 +464,8 @@ trsv_coop_kernel(TrsvParams p) {
       }
       const int t0 = t * 64, trows = min(64, p.n - t0);
       const int r = tid & 63, q = tid >> 6;
-      float acc = 0.f;
-      for (int c = q; c < rows; c += 4) acc = fmaf(Tu[c][r], xs[c], acc);
+      VT acc = 0;
+      for (int c = q; c < rows; c += 4) acc = fma_t((VT)Tu[c][r], xs[c], acc);
       red[q][r] = acc;
       __syncthreads();
       if (tid < trows) p.y[t0 + tid] -= (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
@@ -463,19 +478,693 @@ trsv_coop_kernel(TrsvParams p) {
 
 namespace slqr {
 
-template <bool UPPER>
-static slqr_status trsv_f32(slqr_ctx *ctx, const float *R, int lda, int n, float *y, int *zero_flag,
+// --------------------------------------------------------------------------
+// GMRES-based iterative refinement (GMRES-IR) of the augmented system
+//   Aaug [r; x] = [b; 0],  Aaug = [I A; A^T 0],
+// left-preconditioned by M^-1, where M is the augmented matrix of the FP32
+// factorization (A ~ Q R in low precision): M^-1 [f; g] is exactly one Bjorck
+// correction, h = R^-T g, d = Q^T f, dx = R^-1 (d[0:n] - h), dr = Q [h; d[n:m]],
+// here applied in FP64 arithmetic to the FP32 factors so that it is one fixed
+// linear operator.  Each refinement step computes the residual [f; g] of the
+// current (r, x) in FP64 from the FP64 A, solves Aaug z = [f; g] by GMRES on
+// M^-1 Aaug z = M^-1 [f; g] (Krylov basis in FP64, classical Gram-Schmidt
+// applied twice, Givens rotations on the host) and adds z.  This is the
+// method of Carson, Higham and Pranesh (three-precision GMRES-IR for least
+// squares, SIAM J. Sci. Comput. 42(6), 2020) with the working and residual
+// precisions both FP64.  It needs far more work per step than the Bjorck
+// sweep, but it converges where kappa times the factorization's backward
+// error is above 1, where the Bjorck iteration diverges.
+// --------------------------------------------------------------------------
+
+// part[chunk][i] of A v (ax_partial_kernel), then
+//   out_s[i] = sgn_v * v_s[i] + sgn_a * sum_chunks part   (fixed order)
+// (Aaug v: sgn_v = 1, sgn_a = 1 with v_s the r-part; the residual b - r - A x:
+// computed by resid64_f_kernel below)
+__global__ void aug_s_kernel(const double *__restrict__ vs, const double *__restrict__ part,
+                             int chunks, int m, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double ax = 0.0;
+  for (int c = 0; c < chunks; ++c) ax += part[(size_t)c * m + i];
+  out[i] = vs[i] + ax;
+}
+
+// f = b - r - sum_chunks part (FP64 output)
+__global__ void resid64_f_kernel(const double *__restrict__ b, const double *__restrict__ r,
+                                 const double *__restrict__ part, int chunks, int m,
+                                 double *__restrict__ f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double ax = 0.0;
+  for (int c = 0; c < chunks; ++c) ax += part[(size_t)c * m + i];
+  f[i] = b[i] - r[i] - ax;
+}
+
+// out[j] = sgn * (A^T v)[j], one warp per column
+__global__ void atv_kernel(const double *__restrict__ A, int lda, int m, int n,
+                           const double *__restrict__ v, double sgn, double *__restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double acc = 0.0;
+  for (int i = lane; i < m; i += 32) acc = fma(A[SLQR_IDX(i, warp, lda)], v[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[warp] = sgn * acc;
+}
+
+// middle of M^-1 [f; g] in place on w = [w_s (m); w_x (n)] after h = R^-T g
+// (in w_x) and d = Q^T f (in w_s): w_x = d[0:n] - h (then solved with R),
+// w_s[0:n] = h (so that w_s = [h; d[n:m]] for the final Q application)
+__global__ void prec_mid_kernel(double *__restrict__ ws, double *__restrict__ wx, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double h = wx[i], d = ws[i];
+  wx[i] = d - h;
+  ws[i] = h;
+}
+
+// block-wide sum of one double per thread (fixed order), result in thread 0
+__device__ __forceinline__ double block_sum_256(double v, double *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// out[q] = V[:, q]^T w for q < k (one CTA per basis vector; V column-major,
+// ld = N)
+__global__ void __launch_bounds__(256)
+basis_dots_kernel(const double *__restrict__ V, size_t N, int k, const double *__restrict__ w,
+                  double *__restrict__ out) {
+  __shared__ double red[256];
+  const int q = blockIdx.x;
+  if (q >= k) return;
+  const double *vq = V + (size_t)q * N;
+  double a0 = 0.0, a1 = 0.0;
+  size_t i = threadIdx.x;
+  for (; i + 256 < N; i += 512) {
+    a0 = fma(vq[i], w[i], a0);
+    a1 = fma(vq[i + 256], w[i + 256], a1);
+  }
+  if (i < N) a0 = fma(vq[i], w[i], a0);
+  const double t = block_sum_256(a0 + a1, red);
+  if (threadIdx.x == 0) out[q] = t;
+}
+
+// w -= V[:, 0:k] h  (h: k doubles, k <= kMaxKrylov + 1)
+constexpr int kMaxKrylov = 512;
+__global__ void __launch_bounds__(256)
+basis_axpy_kernel(const double *__restrict__ V, size_t N, int k, const double *__restrict__ h,
+                  double *__restrict__ w) {
+  __shared__ double hs[kMaxKrylov + 1];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < k; ++q) acc = fma(V[i + (size_t)q * N], hs[q], acc);
+    w[i] -= acc;
+  }
+}
+
+// out[0] = ||w||_2 (one CTA, fixed order)
+__global__ void __launch_bounds__(256)
+vec_norm_kernel(const double *__restrict__ w, size_t N, double *__restrict__ out) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (size_t i = threadIdx.x; i < N; i += 256) a = fma(w[i], w[i], a);
+  const double t = block_sum_256(a, red);
+  if (threadIdx.x == 0) out[0] = sqrt(t);
+}
+
+// w *= s
+__global__ void vec_scale_kernel(double *__restrict__ w, size_t N, double s) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x)
+    w[i] *= s;
+}
+
+// z = V[:, 0:k] y; r += z[0:m], x += z[m:m+n]; per-CTA maxima of |dx| and |x|
+// (a non-finite entry counts as +inf, so that it is never taken as converged)
+__global__ void __launch_bounds__(256)
+gmres_update_kernel(const double *__restrict__ V, size_t N, int k, const double *__restrict__ y,
+                    double *__restrict__ r, int m, double *__restrict__ x, int n,
+                    double *__restrict__ maxima) {
+  __shared__ double ys[kMaxKrylov];
+  __shared__ double s_dx[256], s_x[256];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[q];
+  __syncthreads();
+  double a = 0.0, c = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double z = 0.0;
+    for (int q = 0; q < k; ++q) z = fma(V[i + (size_t)q * N], ys[q], z);
+    if (i < (size_t)m) {
+      r[i] += z;
+    } else {
+      const size_t j = i - m;
+      const double xn = x[j] + z;
+      x[j] = xn;
+      a = fmax(a, isfinite(z) ? fabs(z) : CUDART_INF);
+      c = fmax(c, isfinite(xn) ? fabs(xn) : CUDART_INF);
+    }
+  }
+  s_dx[threadIdx.x] = a;
+  s_x[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_dx[threadIdx.x] = fmax(s_dx[threadIdx.x], s_dx[threadIdx.x + o]);
+      s_x[threadIdx.x] = fmax(s_x[threadIdx.x], s_x[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    maxima[2 * blockIdx.x] = s_dx[0];
+    maxima[2 * blockIdx.x + 1] = s_x[0];
+  }
+}
+
+// out = [max |R_ii|, min |R_ii|] over the diagonal of the FP32 R (one CTA):
+// their ratio is the condition estimate that sets the FP64 noise level below
+__global__ void __launch_bounds__(256)
+diag_range_kernel(const float *__restrict__ R, int lda, int n, double *__restrict__ out) {
+  __shared__ double smax[256], smin[256];
+  double hi = 0.0, lo = CUDART_INF;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double d = fabs((double)R[SLQR_IDX(i, i, lda)]);
+    hi = fmax(hi, d);
+    lo = fmin(lo, d);
+  }
+  smax[threadIdx.x] = hi;
+  smin[threadIdx.x] = lo;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smax[0];
+    out[1] = smin[0];
+  }
+}
+
+template <bool UPPER, typename VT>
+static slqr_status trsv_vec(slqr_ctx *ctx, const float *R, int lda, int n, VT *y, int *zero_flag,
                             unsigned *bar, unsigned &bar_base, cudaStream_t s) {
-  TrsvParams tp;
+  TrsvParams<VT> tp;
   tp.R = R; tp.y = y; tp.zero_flag = zero_flag; tp.bar = bar; tp.status = ctx->d_status;
   tp.lda = lda; tp.n = n; tp.nblk = (n + 63) / 64;
   tp.P = std::min(tp.nblk, ctx->num_sms);
   tp.bar_base = bar_base;
   void *args[] = {&tp};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void *)trsv_coop_kernel<UPPER>, dim3(tp.P),
-                                              dim3(kThreads), args, 0, s);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)trsv_coop_kernel<UPPER, VT>,
+                                              dim3(tp.P), dim3(kThreads), args, 0, s);
+  ++ctx->launch_count;
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "triangular solve: %s", cudaGetErrorString(e));
   bar_base += (unsigned)tp.nblk * (unsigned)tp.P;
+  return SLQR_OK;
+}
+
+// Everything one mixed-precision solve holds on the device.
+struct MixedSolve {
+  slqr_ctx *ctx;
+  cudaStream_t s;
+  int m, n, lda, lda32, nb, K, np, chunks, ublocks;
+  const double *A, *b;
+  double *x;
+  float *A32;
+  double *up, *wy, *r, *part, *maxima;
+  int *zero_flag;
+  float *f32, *g32, *e32, *Tm32, *qpart32;
+  double *Tm64, *qpart64;
+  unsigned *qbar;
+  unsigned qbar_base = 0;
+  int qv_R, qv_P;
+  // GMRES-IR: Krylov basis (restart + 1 vectors of m + n) and small buffers
+  double *Vk = nullptr, *hdev = nullptr, *ydev = nullptr, *drange = nullptr;
+  int restart = 0;
+};
+
+template <typename VT>
+static slqr_status apply_q_vec(MixedSolve &ms, VT *f, const VT *Tm, VT *qpart, bool trans) {
+  if (ms.np == 0) return SLQR_OK;
+  QvecParams<VT> qp;
+  qp.A = ms.A32; qp.up = ms.up; qp.Tm = Tm; qp.f = f; qp.part = qpart; qp.bar = ms.qbar;
+  qp.status = ms.ctx->d_status; qp.lda = ms.lda32; qp.m = ms.m; qp.K = ms.K; qp.nb = ms.nb;
+  qp.np = ms.np; qp.trans = trans ? 1 : 0; qp.R = ms.qv_R; qp.P = ms.qv_P;
+  qp.bar_base = ms.qbar_base;
+  void *args[] = {&qp};
+  cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel<VT>, dim3(ms.qv_P),
+                                               dim3(kThreads), args,
+                                               qvec_smem_bytes<VT>(ms.nb, ms.qv_R), ms.s);
+  ++ms.ctx->launch_count;
+  if (le != cudaSuccess)
+    return fail(ms.ctx, SLQR_ECUDA, "Q application: %s", cudaGetErrorString(le));
+  ms.qbar_base += (unsigned)ms.np * (unsigned)ms.qv_P;
+  return SLQR_OK;
+}
+
+// Read back the per-CTA maxima of |dx| and |x| and the zero-diagonal flag.
+static slqr_status read_step(MixedSolve &ms, int nblocks, double *dmax, double *xmax, int *zflag) {
+  std::vector<double> hmax(2 * (size_t)nblocks);
+  cudaError_t e = cudaMemcpyAsync(hmax.data(), ms.maxima, sizeof(double) * 2 * nblocks,
+                                  cudaMemcpyDeviceToHost, ms.s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(zflag, ms.zero_flag, sizeof(int), cudaMemcpyDeviceToHost, ms.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ms.s);
+  if (e != cudaSuccess) return fail(ms.ctx, SLQR_ECUDA, "refinement: %s", cudaGetErrorString(e));
+  *dmax = 0.0;
+  *xmax = 0.0;
+  for (int k = 0; k < nblocks; ++k) {
+    *dmax = std::max(*dmax, hmax[2 * k]);
+    *xmax = std::max(*xmax, hmax[2 * k + 1]);
+  }
+  return SLQR_OK;
+}
+
+// Bjorck sweeps (FP32 corrections, FP64 residuals) from r = 0, x = 0.
+// Returns the refinement status; *it sweeps done, *e_out the last step.
+static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out, double *e_out) {
+  slqr_ctx *ctx = ms.ctx;
+  cudaStream_t s = ms.s;
+  const int m = ms.m, n = ms.n;
+  init_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.r, m, ms.x, n);
+  int it = 0, status = SLQR_ENOCONV;
+  double e_cur = 1.0, e_prev = 1e300;
+  slqr_status st;
+  for (it = 1; it <= max_iter; ++it) {
+    ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, s>>>(
+        ms.A, ms.lda, m, n, ms.x, ms.part);
+    resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.b, ms.r, ms.part, ms.chunks, m, ms.f32);
+    resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, ms.g32);
+    ctx->launch_count += 3;
+    st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
+    if (st != SLQR_OK) return st;                                       // h = R^-T g
+    st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, true);            // d = Q^T f
+    if (st != SLQR_OK) return st;
+    form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.f32, ms.g32, m, n, ms.e32);
+    ++ctx->launch_count;
+    st = trsv_vec<true>(ctx, ms.A32, ms.lda32, n, ms.e32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
+    if (st != SLQR_OK) return st;                                       // dx = R^-1 (d1 - h)
+    update_kernel<<<ms.ublocks, 256, 0, s>>>(ms.f32, ms.g32, ms.e32, ms.x, n, ms.maxima);
+    ++ctx->launch_count;                                                // d = [h; d2], x += dx
+    st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, false);           // dr = Q [h; d2]
+    if (st != SLQR_OK) return st;
+    add_r_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.r, ms.f32, m);
+    ++ctx->launch_count;
+    double dmax, xmax;
+    int zflag = 0;
+    st = read_step(ms, ms.ublocks, &dmax, &xmax, &zflag);
+    if (st != SLQR_OK) return st;
+    // an exact zero on the diagonal of R is reported first (a rank statement,
+    // whatever the step looks like), then a non-finite step (an overflow:
+    // never "converged")
+    if (zflag) {
+      e_cur = (std::isfinite(dmax) && std::isfinite(xmax) && xmax > 0.0) ? dmax / xmax : HUGE_VAL;
+      status = SLQR_ERANK;
+      break;
+    }
+    if (!std::isfinite(dmax) || !std::isfinite(xmax)) {
+      e_cur = HUGE_VAL;
+      status = SLQR_ENOCONV;
+      break;
+    }
+    e_cur = (xmax > 0.0) ? dmax / xmax : 0.0;
+    if (e_cur <= tol) { status = SLQR_OK; break; }
+    if (it >= 3 && e_cur > 0.5 * e_prev) {      // no longer contracting
+      status = (e_cur <= kStallOk) ? SLQR_OK : SLQR_ENOCONV;
+      break;
+    }
+    e_prev = e_cur;
+  }
+  *it_out = std::min(it, max_iter);
+  *e_out = e_cur;
+  return status;
+}
+
+// w <- M^-1 w in place, w = [w_s (m); w_x (n)] in FP64 (see above)
+static slqr_status precondition64(MixedSolve &ms, double *w) {
+  slqr_ctx *ctx = ms.ctx;
+  double *ws = w, *wx = w + ms.m;
+  slqr_status st = trsv_vec<false>(ctx, ms.A32, ms.lda32, ms.n, wx, ms.zero_flag, ms.qbar,
+                                   ms.qbar_base, ms.s);                 // h = R^-T g
+  if (st != SLQR_OK) return st;
+  st = apply_q_vec(ms, ws, ms.Tm64, ms.qpart64, true);                  // d = Q^T f
+  if (st != SLQR_OK) return st;
+  prec_mid_kernel<<<(ms.n + 255) / 256, 256, 0, ms.s>>>(ws, wx, ms.n);
+  ++ctx->launch_count;
+  st = trsv_vec<true>(ctx, ms.A32, ms.lda32, ms.n, wx, ms.zero_flag, ms.qbar, ms.qbar_base,
+                      ms.s);                                            // dx = R^-1 (d1 - h)
+  if (st != SLQR_OK) return st;
+  return apply_q_vec(ms, ws, ms.Tm64, ms.qpart64, false);               // Q [h; d2]
+}
+
+// y = Aaug v = [v_s + A v_x; A^T v_s]
+static void aug_matvec(MixedSolve &ms, const double *v, double *y) {
+  const int m = ms.m, n = ms.n;
+  ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, ms.s>>>(
+      ms.A, ms.lda, m, n, v + m, ms.part);
+  aug_s_kernel<<<(m + 255) / 256, 256, 0, ms.s>>>(v, ms.part, ms.chunks, m, y);
+  atv_kernel<<<(n * 32 + 255) / 256, 256, 0, ms.s>>>(ms.A, ms.lda, m, n, v, 1.0, y + m);
+  ms.ctx->launch_count += 3;
+}
+
+struct GmresResult {
+  int steps = 0, iters = 0;
+  double err = 1.0;
+};
+
+// GMRES-IR from the current (r, x).  Returns the refinement status.
+static slqr_status gmres_ir(MixedSolve &ms, double tol, int max_iters, double inner_tol,
+                            double noise, GmresResult *res) {
+  slqr_ctx *ctx = ms.ctx;
+  cudaStream_t s = ms.s;
+  const int m = ms.m, n = ms.n;
+  const size_t N = (size_t)m + n;
+  const int k_max = ms.restart;
+  const int gblocks = std::min(4 * ctx->num_sms, (int)((N + 255) / 256));
+  std::vector<double> H((size_t)(k_max + 1) * k_max), cs(k_max), sn(k_max), gv(k_max + 1),
+      y(k_max), hh(2 * (size_t)(k_max + 2));
+  const int max_steps = 20;
+  int status = SLQR_ENOCONV;
+  double e_prev = HUGE_VAL;
+  slqr_status st;
+  for (int step = 1; step <= max_steps && res->iters < max_iters; ++step) {
+    // residual of the augmented system in FP64: f = b - r - A x, g = -A^T r
+    double *V0 = ms.Vk;
+    ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, s>>>(
+        ms.A, ms.lda, m, n, ms.x, ms.part);
+    resid64_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.b, ms.r, ms.part, ms.chunks, m, V0);
+    atv_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, -1.0, V0 + m);
+    ctx->launch_count += 3;
+    st = precondition64(ms, V0);
+    if (st != SLQR_OK) return st;
+    vec_norm_kernel<<<1, 256, 0, s>>>(V0, N, ms.hdev);
+    ++ctx->launch_count;
+    double beta = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&beta, ms.hdev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
+    if (!std::isfinite(beta)) { res->err = HUGE_VAL; return SLQR_ENOCONV; }
+    if (beta == 0.0) { res->err = 0.0; return SLQR_OK; }    // (r, x) solves the system
+    vec_scale_kernel<<<gblocks, 256, 0, s>>>(V0, N, 1.0 / beta);
+    ++ctx->launch_count;
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    bool inner_ok = false;
+    for (int j = 0; j < k_max && res->iters < max_iters; ++j) {
+      double *vj = ms.Vk + (size_t)j * N, *w = ms.Vk + (size_t)(j + 1) * N;
+      aug_matvec(ms, vj, w);                                   // w = Aaug v_j
+      st = precondition64(ms, w);                              // w = M^-1 Aaug v_j
+      if (st != SLQR_OK) return st;
+      // classical Gram-Schmidt, twice
+      basis_dots_kernel<<<j + 1, 256, 0, s>>>(ms.Vk, N, j + 1, w, ms.hdev);
+      basis_axpy_kernel<<<gblocks, 256, 0, s>>>(ms.Vk, N, j + 1, ms.hdev, w);
+      basis_dots_kernel<<<j + 1, 256, 0, s>>>(ms.Vk, N, j + 1, w, ms.hdev + (k_max + 2));
+      basis_axpy_kernel<<<gblocks, 256, 0, s>>>(ms.Vk, N, j + 1, ms.hdev + (k_max + 2), w);
+      vec_norm_kernel<<<1, 256, 0, s>>>(w, N, ms.hdev + (j + 1));
+      ctx->launch_count += 5;
+      e = cudaMemcpyAsync(hh.data(), ms.hdev, sizeof(double) * 2 * (k_max + 2),
+                          cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
+      ++res->iters;
+      double *hc = &H[(size_t)j * (k_max + 1)];
+      for (int q = 0; q <= j; ++q) hc[q] = hh[q] + hh[(k_max + 2) + q];
+      const double hnext = hh[j + 1];
+      hc[j + 1] = hnext;
+      if (!std::isfinite(hnext)) { res->err = HUGE_VAL; return SLQR_ENOCONV; }
+      // previous rotations, then a new one that zeroes H[j+1, j]
+      for (int q = 0; q < j; ++q) {
+        const double a = hc[q], c = hc[q + 1];
+        hc[q] = cs[q] * a + sn[q] * c;
+        hc[q + 1] = -sn[q] * a + cs[q] * c;
+      }
+      const double rho = std::hypot(hc[j], hc[j + 1]);
+      cs[j] = rho > 0.0 ? hc[j] / rho : 1.0;
+      sn[j] = rho > 0.0 ? hc[j + 1] / rho : 0.0;
+      hc[j] = rho;
+      hc[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      k = j + 1;
+      const double rel = std::fabs(gv[j + 1]) / beta;
+      if (rel <= inner_tol) { inner_ok = true; break; }
+      if (hnext <= 1e-300 * beta) { inner_ok = true; break; }   // invariant subspace: exact
+      vec_scale_kernel<<<gblocks, 256, 0, s>>>(w, N, 1.0 / hnext);
+      ++ctx->launch_count;
+    }
+    // y = H[0:k, 0:k]^-1 g[0:k] (upper triangular after the rotations)
+    for (int q = k - 1; q >= 0; --q) {
+      double t = gv[q];
+      for (int c = q + 1; c < k; ++c) t -= H[(size_t)c * (k_max + 1) + q] * y[c];
+      const double d = H[(size_t)q * (k_max + 1) + q];
+      y[q] = d != 0.0 ? t / d : 0.0;
+    }
+    e = cudaMemcpyAsync(ms.ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
+    const int ub = std::min(4 * ctx->num_sms, (int)((N + 255) / 256));
+    gmres_update_kernel<<<ub, 256, 0, s>>>(ms.Vk, N, k, ms.ydev, ms.r, m, ms.x, n, ms.maxima);
+    ++ctx->launch_count;
+    ++res->steps;
+    double dmax, xmax;
+    int zflag = 0;
+    st = read_step(ms, ub, &dmax, &xmax, &zflag);
+    if (st != SLQR_OK) return st;
+    if (zflag) { res->err = HUGE_VAL; return SLQR_ERANK; }
+    if (!std::isfinite(dmax) || !std::isfinite(xmax)) { res->err = HUGE_VAL; return SLQR_ENOCONV; }
+    const double e_cur = (xmax > 0.0) ? dmax / xmax : 0.0;
+    res->err = e_cur;
+    // converged: the step is below tol, or it is at the FP64 noise level of
+    // this problem after an inner solve that reached its tolerance (the
+    // remaining error is then a small fraction of that step)
+    if (e_cur <= tol || (inner_ok && e_cur <= noise)) { status = SLQR_OK; break; }
+    if (step >= 3 && e_cur > 0.5 * e_prev) {           // no longer contracting
+      status = (e_cur <= noise) ? SLQR_OK : SLQR_ENOCONV;
+      break;
+    }
+    e_prev = e_cur;
+  }
+  return status;
+}
+
+// FP64 solve of the same problem (slqr_factor, slqr_apply_qt, slqr_solve_r on
+// a copy of A): the opt-in fallback when the mixed-precision refinement fails.
+static slqr_status fp64_fallback(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                 const double *b, double *x, cudaStream_t s) {
+  const size_t a_bytes = align_up((size_t)m * n * sizeof(double), 256);
+  const size_t up_bytes = align_up((size_t)n * sizeof(double), 256);
+  const size_t wy_bytes = align_up(slqr_wy_size(m, n), 256);
+  const size_t b_bytes = align_up((size_t)m * sizeof(double), 256);
+  cudaError_t e = cudaStreamSynchronize(s);   // the mixed buffers are no longer in use
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "fallback: %s", cudaGetErrorString(e));
+  slqr_status st = ensure_workspace2(ctx, a_bytes + up_bytes + wy_bytes + b_bytes);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws2.ptr;
+  double *A64 = (double *)base;
+  double *up = (double *)(base + a_bytes);
+  double *wy = (double *)(base + a_bytes + up_bytes);
+  double *B = (double *)(base + a_bytes + up_bytes + wy_bytes);
+  int st_before = 0;
+  e = cudaMemcpy2DAsync(A64, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                        (size_t)m * sizeof(double), n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B, b, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st_before, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "fallback: %s", cudaGetErrorString(e));
+  st = slqr_factor(ctx, m, n, A64, m, up, wy, s);
+  if (st == SLQR_OK) st = slqr_apply_qt(ctx, m, n, A64, m, up, wy, 1, B, m, s);
+  if (st == SLQR_OK) st = slqr_solve_r(ctx, n, A64, m, 1, B, m, s);
+  if (st != SLQR_OK) return st;
+  int st_after = 0;
+  e = cudaMemcpyAsync(x, B, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st_after, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "fallback: %s", cudaGetErrorString(e));
+  if (st_before == 0 && st_after != 0) {      // raised by this solve: report it here
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return st_after;
+  }
+  return SLQR_OK;
+}
+
+static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                    const double *b, double *x, int prec,
+                                    const slqr_mixed_opts &o, slqr_mixed_info *info,
+                                    cudaStream_t s) {
+  const int nb = panel_width(m, n);
+  const int K = num_reflectors(m, n);
+  const int np = num_panels(K, nb);
+  const bool use_gmres = o.refine != SLQR_REFINE_BJORCK;
+  const bool use_bjorck = o.refine != SLQR_REFINE_GMRES;
+  MixedSolve ms;
+  ms.ctx = ctx; ms.s = s; ms.m = m; ms.n = n; ms.lda = lda; ms.nb = nb; ms.K = K; ms.np = np;
+  ms.A = A; ms.b = b; ms.x = x;
+  ms.chunks = (n + kColChunk - 1) / kColChunk;
+  ms.ublocks = (n + 255) / 256;
+  // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t of = off; off = align_up(off + bytes, 256); return of; };
+  ms.lda32 = (m + 31) / 32 * 32;   // 128-byte aligned columns (TMA-friendly)
+  const size_t o_a32 = take((size_t)ms.lda32 * n * sizeof(float));
+  const size_t o_up = take((size_t)n * sizeof(double));
+  const size_t o_wy = take(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double));
+  const size_t o_r = take((size_t)m * sizeof(double));
+  const size_t o_f = take((size_t)m * sizeof(float));
+  const size_t o_g = take((size_t)n * sizeof(float));
+  const size_t o_e = take((size_t)m * sizeof(float));
+  const size_t o_part = take((size_t)ms.chunks * m * sizeof(double));
+  const size_t N = (size_t)m + n;
+  const int max_blocks = std::max(ms.ublocks, std::min(4 * ctx->num_sms, (int)((N + 255) / 256)));
+  const size_t o_max = take((size_t)2 * max_blocks * sizeof(double));
+  const size_t o_flag = take(sizeof(int));
+  // fused Q application: rows per CTA, explicit T per panel, partials, barrier
+  // (a multiple of 64 rows: every slice starts 16-byte aligned for the vector loads)
+  ms.qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
+  ms.qv_P = (m + ms.qv_R - 1) / ms.qv_R;
+  const size_t t_elems = (size_t)std::max(np, 1) * nb * (nb + 1);
+  const size_t o_tm = take(t_elems * sizeof(float));
+  const size_t o_qpart = take((size_t)2 * ms.qv_P * nb * sizeof(float));
+  const size_t o_bar = take(256);
+  // BF16 hi / lo shadows of the FP32 matrix (SLQR_BF16X3)
+  const size_t sh_bytes = (prec == SLQR_BF16X3) ? (size_t)ms.lda32 * n * 2 : 0;
+  const size_t o_shh = take(sh_bytes);
+  const size_t o_shl = take(sh_bytes);
+  // GMRES-IR: FP64 T and partials, the Krylov basis, the Hessenberg column
+  int gm_iters = o.gmres_max_iters > 0 ? o.gmres_max_iters : 300;
+  int restart = o.gmres_restart > 0 ? o.gmres_restart : std::min(gm_iters, 200);
+  restart = std::max(1, std::min(restart, kMaxKrylov));
+  const size_t o_tm64 = use_gmres ? take(t_elems * sizeof(double)) : 0;
+  const size_t o_qpart64 = use_gmres ? take((size_t)2 * ms.qv_P * nb * sizeof(double)) : 0;
+  const size_t o_vk = use_gmres ? take((size_t)(restart + 1) * N * sizeof(double)) : 0;
+  const size_t o_h = use_gmres ? take((size_t)2 * (restart + 2) * sizeof(double)) : 0;
+  const size_t o_y = use_gmres ? take((size_t)restart * sizeof(double)) : 0;
+  const size_t o_dr = take(2 * sizeof(double));
+  slqr_status st = ensure_workspace2(ctx, off);
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws2.ptr;
+  ms.A32 = (float *)(base + o_a32);
+  ms.up = (double *)(base + o_up);
+  ms.wy = (double *)(base + o_wy);
+  ms.r = (double *)(base + o_r);
+  ms.f32 = (float *)(base + o_f);
+  ms.g32 = (float *)(base + o_g);
+  ms.e32 = (float *)(base + o_e);
+  ms.part = (double *)(base + o_part);
+  ms.maxima = (double *)(base + o_max);
+  ms.zero_flag = (int *)(base + o_flag);
+  ms.Tm32 = (float *)(base + o_tm);
+  ms.qpart32 = (float *)(base + o_qpart);
+  ms.qbar = (unsigned *)(base + o_bar);
+  ms.drange = (double *)(base + o_dr);
+  if (use_gmres) {
+    ms.Tm64 = (double *)(base + o_tm64);
+    ms.qpart64 = (double *)(base + o_qpart64);
+    ms.Vk = (double *)(base + o_vk);
+    ms.hdev = (double *)(base + o_h);
+    ms.ydev = (double *)(base + o_y);
+    ms.restart = restart;
+  }
+  cudaError_t e = cudaFuncSetAttribute(qvec_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)qvec_smem_bytes<float>(nb, ms.qv_R));
+  if (e == cudaSuccess && use_gmres)
+    e = cudaFuncSetAttribute(qvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)qvec_smem_bytes<double>(nb, ms.qv_R));
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
+
+  // the FP32 factorization
+  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, ms.A32, ms.lda32);
+  ++ctx->launch_count;
+  ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
+  if (prec == SLQR_BF16X3) {
+    ctx->sh_hi = base + o_shh;
+    ctx->sh_lo = base + o_shl;
+    split_bf16_region(ms.A32, ms.lda32, 0, m, 0, n, ctx->sh_hi, ctx->sh_lo, ctx->num_sms, s);
+  }
+  st = factor_f32(ctx, m, n, ms.A32, ms.lda32, ms.up, ms.wy, s);
+  ctx->tc_mode = 0;
+  ctx->sh_hi = ctx->sh_lo = nullptr;
+  if (st != SLQR_OK) return st;
+  if (np > 0) {
+    tmat_kernel<float><<<np, 64, 0, s>>>(ms.wy, nb, K, ms.Tm32);
+    ++ctx->launch_count;
+    if (use_gmres) {
+      tmat_kernel<double><<<np, 64, 0, s>>>(ms.wy, nb, K, ms.Tm64);
+      ++ctx->launch_count;
+    }
+  }
+  cudaMemsetAsync(ms.qbar, 0, 256, s);
+  cudaMemsetAsync(ms.zero_flag, 0, sizeof(int), s);
+  info->method = SLQR_REFINE_BJORCK;
+  int status = SLQR_ENOCONV;
+  double e_cur = HUGE_VAL;
+  if (use_bjorck) {
+    status = bjorck(ms, o.max_sweeps, o.tol, &info->sweeps, &e_cur);
+    info->err = e_cur;
+  } else {
+    init_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.r, m, x, n);
+    ++ctx->launch_count;
+  }
+  if (status == SLQR_ENOCONV && use_gmres) {
+    // condition estimate from the diagonal of R: the FP64 noise level that a
+    // converged refinement stalls at is about kappa * u
+    diag_range_kernel<<<1, 256, 0, s>>>(ms.A32, ms.lda32, n, ms.drange);
+    ++ctx->launch_count;
+    double dr[2] = {0.0, 0.0};
+    e = cudaMemcpyAsync(dr, ms.drange, sizeof(dr), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
+    const double kappa_est = (dr[1] > 0.0) ? dr[0] / dr[1] : HUGE_VAL;
+    info->kappa_est = kappa_est;
+    const double noise = std::max(kStallOk, 100.0 * kappa_est * std::ldexp(1.0, -53));
+    if (use_bjorck) {
+      // the Bjorck iterate may have diverged: start again from the plain solve
+      init_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.r, m, x, n);
+      ++ctx->launch_count;
+    }
+    GmresResult gr;
+    const double inner_tol = o.gmres_tol > 0.0 ? o.gmres_tol : 1e-10;
+    status = gmres_ir(ms, o.tol, gm_iters, inner_tol, noise, &gr);
+    info->method = SLQR_REFINE_GMRES;
+    info->gmres_steps = gr.steps;
+    info->gmres_iters = gr.iters;
+    info->err = gr.err;
+    e_cur = gr.err;
+  }
+  st = check_launch(ctx, "lstsq_mixed");
+  if (st != SLQR_OK) return st;
+  if (status == SLQR_ENOCONV && o.fp64_fallback) {
+    st = fp64_fallback(ctx, m, n, A, lda, b, x, s);
+    if (st != SLQR_OK) return st;
+    info->method = SLQR_REFINE_FP64;
+    return SLQR_FALLBACK;
+  }
+  if (status != SLQR_OK)
+    fail(ctx, status, status == SLQR_ENOCONV ? "refinement did not reach its tolerance"
+                                             : "R has an exact zero on its diagonal");
+  return status;
+}
+
+static slqr_status check_mixed_args(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                    const double *b, double *x, int prec) {
+  if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);
+  if (lda < m || !A || !b || !x) return fail(ctx, SLQR_EINVAL, "bad lda or NULL pointer");
+  if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
+  if (prec != SLQR_FP32 && prec != SLQR_TF32 && prec != SLQR_BF16X3)
+    return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
   return SLQR_OK;
 }
 
@@ -488,147 +1177,44 @@ extern "C" slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const doubl
                                         double tol, int *iters, double *err, void *stream) {
   NvtxRange nvtx_range("slqr_lstsq_mixed");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  if (m < 1 || n < 1 || m < n) return fail(ctx, SLQR_EINVAL, "need m >= n >= 1 (m=%d n=%d)", m, n);
-  if (lda < m || !A || !b || !x) return fail(ctx, SLQR_EINVAL, "bad lda or NULL pointer");
-  if (m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "m=%d above slqr_max_rows()", m);
-  if (prec != SLQR_FP32 && prec != SLQR_TF32 && prec != SLQR_BF16X3)
-    return fail(ctx, SLQR_EINVAL, "precision %d not available", prec);
-  if (max_iter < 1) max_iter = 30;
-  if (!(tol > 0.0)) tol = 1e-14;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  slqr_status st = check_mixed_args(ctx, m, n, A, lda, b, x, prec);
+  if (st != SLQR_OK) return st;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-  cudaStream_t s = (cudaStream_t)stream;
-  const int nb = panel_width(m, n);
-  const int K = num_reflectors(m, n);
-  const int np = num_panels(K, nb);
-  const int chunks = (n + kColChunk - 1) / kColChunk;
-  const int ublocks = (n + 255) / 256;
-  // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  const int lda32 = (m + 31) / 32 * 32;   // 128-byte aligned columns (TMA-friendly)
-  const size_t o_a32 = take((size_t)lda32 * n * sizeof(float));
-  const size_t o_up = take((size_t)n * sizeof(double));
-  const size_t o_wy = take(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double));
-  const size_t o_r = take((size_t)m * sizeof(double));
-  const size_t o_f = take((size_t)m * sizeof(float));
-  const size_t o_g = take((size_t)n * sizeof(float));
-  const size_t o_e = take((size_t)m * sizeof(float));
-  const size_t o_part = take((size_t)chunks * m * sizeof(double));
-  const size_t o_max = take((size_t)2 * ublocks * sizeof(double));
-  const size_t o_flag = take(sizeof(int));
-  // fused Q application: rows per CTA, explicit T per panel, partials, barrier
-  // (a multiple of 64 rows: every slice starts 16-byte aligned for the vector loads)
-  const int qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
-  const int qv_P = (m + qv_R - 1) / qv_R;
-  const size_t o_tm = take((size_t)std::max(np, 1) * nb * (nb + 1) * sizeof(float));
-  const size_t o_qpart = take((size_t)2 * qv_P * nb * sizeof(float));
-  const size_t o_bar = take(256);
-  // BF16 hi / lo shadows of the FP32 matrix (SLQR_BF16X3)
-  const size_t sh_bytes = (prec == SLQR_BF16X3) ? (size_t)lda32 * n * 2 : 0;
-  const size_t o_shh = take(sh_bytes);
-  const size_t o_shl = take(sh_bytes);
-  slqr_status st = ensure_workspace2(ctx, off);
-  if (st != SLQR_OK) return st;
-  char *base = (char *)ctx->ws2.ptr;
-  float *A32 = (float *)(base + o_a32);
-  double *up = (double *)(base + o_up);
-  double *wy = (double *)(base + o_wy);
-  double *r = (double *)(base + o_r);
-  float *f32 = (float *)(base + o_f);
-  float *g32 = (float *)(base + o_g);
-  float *e32 = (float *)(base + o_e);
-  double *part = (double *)(base + o_part);
-  double *maxima = (double *)(base + o_max);
-  int *zero_flag = (int *)(base + o_flag);
-  float *Tm = (float *)(base + o_tm);
-  float *qpart = (float *)(base + o_qpart);
-  unsigned *qbar = (unsigned *)(base + o_bar);
-  const size_t qv_smem = qvec_smem_bytes(nb, qv_R);
-  e = cudaFuncSetAttribute(qvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qv_smem);
-  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
-  unsigned qbar_base = 0;
-  // f <- Q^T f (trans) or Q f with one cooperative launch
-  auto apply_q = [&](bool trans) -> slqr_status {
-    if (np == 0) return SLQR_OK;
-    QvecParams qp;
-    qp.A = A32; qp.up = up; qp.Tm = Tm; qp.f = f32; qp.part = qpart; qp.bar = qbar;
-    qp.status = ctx->d_status; qp.lda = lda32; qp.m = m; qp.K = K; qp.nb = nb; qp.np = np;
-    qp.trans = trans ? 1 : 0; qp.R = qv_R; qp.P = qv_P; qp.bar_base = qbar_base;
-    void *args[] = {&qp};
-    cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel, dim3(qv_P),
-                                                 dim3(kThreads), args, qv_smem, s);
-    if (le != cudaSuccess)
-      return fail(ctx, SLQR_ECUDA, "Q application: %s", cudaGetErrorString(le));
-    qbar_base += (unsigned)np * (unsigned)qv_P;
-    return SLQR_OK;
-  };
+  slqr_mixed_opts o = {};
+  o.refine = SLQR_REFINE_BJORCK;
+  o.max_sweeps = max_iter >= 1 ? max_iter : 30;
+  o.tol = tol > 0.0 ? tol : 1e-14;
+  slqr_mixed_info info = {};
+  st = lstsq_mixed_impl(ctx, m, n, A, lda, b, x, prec, o, &info, (cudaStream_t)stream);
+  if (iters) *iters = info.sweeps;
+  if (err) *err = info.err;
+  return st;
+}
 
-  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, A32, lda32);
-  ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
-  if (prec == SLQR_BF16X3) {
-    ctx->sh_hi = base + o_shh;
-    ctx->sh_lo = base + o_shl;
-    split_bf16_region(A32, lda32, 0, m, 0, n, ctx->sh_hi, ctx->sh_lo, ctx->num_sms, s);
-  }
-  st = factor_f32(ctx, m, n, A32, lda32, up, wy, s);
-  ctx->tc_mode = 0;
-  ctx->sh_hi = ctx->sh_lo = nullptr;
+extern "C" slqr_status slqr_lstsq_mixed_ex(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                           const double *b, double *x, int prec,
+                                           const slqr_mixed_opts *opts, slqr_mixed_info *info,
+                                           void *stream) {
+  NvtxRange nvtx_range("slqr_lstsq_mixed_ex");
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  slqr_status st = check_mixed_args(ctx, m, n, A, lda, b, x, prec);
   if (st != SLQR_OK) return st;
-  if (np > 0) tmat_kernel<<<np, 64, 0, s>>>(wy, nb, K, Tm);
-  cudaMemsetAsync(qbar, 0, 256, s);
-  init_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, m, x, n);
-  cudaMemsetAsync(zero_flag, 0, sizeof(int), s);
-  std::vector<double> hmax(2 * ublocks);
-  int it = 0, status = SLQR_ENOCONV;
-  double e_cur = 1.0, e_prev = 1e300;
-  for (it = 1; it <= max_iter; ++it) {
-    ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, chunks), kRowsPerCta, 0, s>>>(
-        A, lda, m, n, x, part);
-    resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(b, r, part, chunks, m, f32);
-    resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, r, g32);
-    st = trsv_f32<false>(ctx, A32, lda32, n, g32, zero_flag, qbar, qbar_base, s);  // h = R^-T g
-    if (st != SLQR_OK) return st;
-    st = apply_q(true);                                                 // d = Q^T f
-    if (st != SLQR_OK) return st;
-    form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(f32, g32, m, n, e32);
-    st = trsv_f32<true>(ctx, A32, lda32, n, e32, zero_flag, qbar, qbar_base, s);   // dx = R^-1 (d1 - h)
-    if (st != SLQR_OK) return st;
-    update_kernel<<<ublocks, 256, 0, s>>>(f32, g32, e32, x, n, maxima);  // d = [h; d2], x += dx
-    st = apply_q(false);                                                // dr = Q [h; d2]
-    if (st != SLQR_OK) return st;
-    add_r_kernel<<<(m + 255) / 256, 256, 0, s>>>(r, f32, m);
-    int zflag = 0;
-    e = cudaMemcpyAsync(hmax.data(), maxima, sizeof(double) * 2 * ublocks, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&zflag, zero_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "refinement: %s", cudaGetErrorString(e));
-    double dmax = 0.0, xmax = 0.0;
-    for (int k = 0; k < ublocks; ++k) {
-      dmax = std::max(dmax, hmax[2 * k]);
-      xmax = std::max(xmax, hmax[2 * k + 1]);
-    }
-    if (!std::isfinite(dmax) || !std::isfinite(xmax)) {   // overflow: never "converged"
-      e_cur = HUGE_VAL;
-      status = SLQR_ENOCONV;
-      break;
-    }
-    e_cur = (xmax > 0.0) ? dmax / xmax : 0.0;
-    if (zflag) { status = SLQR_ERANK; break; }
-    if (e_cur <= tol) { status = SLQR_OK; break; }
-    if (it >= 3 && e_cur > 0.5 * e_prev) {      // no longer contracting
-      status = (e_cur <= kStallOk) ? SLQR_OK : SLQR_ENOCONV;
-      break;
-    }
-    e_prev = e_cur;
-  }
-  if (iters) *iters = std::min(it, max_iter);
-  if (err) *err = e_cur;
-  st = check_launch(ctx, "lstsq_mixed");
-  if (st != SLQR_OK) return st;
-  if (status != SLQR_OK)
-    fail(ctx, status, status == SLQR_ENOCONV ? "refinement did not reach its tolerance"
-                                             : "R has an exact zero on its diagonal");
-  return status;
+  slqr_mixed_opts o = {};
+  if (opts) o = *opts;
+  if (o.refine < SLQR_REFINE_AUTO || o.refine > SLQR_REFINE_GMRES)
+    return fail(ctx, SLQR_EINVAL, "refine = %d is not a refinement method", o.refine);
+  if (o.gmres_restart > kMaxKrylov)
+    return fail(ctx, SLQR_EINVAL, "gmres_restart = %d above %d", o.gmres_restart, kMaxKrylov);
+  if (o.max_sweeps < 1) o.max_sweeps = 30;
+  if (!(o.tol > 0.0)) o.tol = 1e-14;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  slqr_mixed_info inf = {};
+  inf.err = HUGE_VAL;
+  st = lstsq_mixed_impl(ctx, m, n, A, lda, b, x, prec, o, &inf, (cudaStream_t)stream);
+  if (info) *info = inf;
+  return st;
 }

@@ -551,7 +551,7 @@ extern "C" slqr_status slqr_submit(slqr_ctx *ctx, const slqr_request *req, uint6
       return fail(ctx, SLQR_EINVAL, "request: unknown kind %d", r.kind);
   }
   {
-    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     slqr_status st = server_start(ctx);
     if (st != SLQR_OK) return st;
   }

@@ -78,7 +78,9 @@ struct slqr_ctx {
   int tc_mode = 0;
   void *sh_hi = nullptr, *sh_lo = nullptr;
   std::string last_error;
-  std::mutex mu;
+  // serialises the entry points of one context; recursive so that a driver
+  // (the mixed-precision solve's FP64 fallback) can call other entry points
+  std::recursive_mutex mu;
 };
 
 namespace slqr {

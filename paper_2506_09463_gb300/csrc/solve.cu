@@ -148,7 +148,7 @@ extern "C" slqr_status slqr_solve_r(slqr_ctx *ctx, int n, const double *A, int l
                                     double *B, int ldb, void *stream) {
   NvtxRange nvtx_range("slqr_solve_r");
   if (!ctx) return SLQR_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (n < 0 || nrhs < 0) return fail(ctx, SLQR_EINVAL, "n=%d nrhs=%d must be >= 0", n, nrhs);
   if (n == 0 || nrhs == 0) return SLQR_OK;
   if (lda < std::max(1, n)) return fail(ctx, SLQR_EINVAL, "lda=%d < n=%d", lda, n);

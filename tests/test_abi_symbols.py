@@ -70,3 +70,28 @@ def test_null_context_is_rejected(lib):
     from paper_2506_09463_gb300 import abi
     assert abi.slqr_factor(None, 4, 2, None, 4, None, None, None) == abi.SLQR_EINVAL
     assert abi.slqr_solve_r(None, 2, None, 2, 1, None, 2, None) == abi.SLQR_EINVAL
+
+
+def test_mixed_opts_and_info_layout_match_the_header(tmp_path):
+    """The ctypes mirrors of slqr_mixed_opts / slqr_mixed_info have the field
+    offsets and sizes the C compiler gives the header's structs."""
+    import subprocess
+    from paper_2506_09463_gb300 import abi
+    src = tmp_path / "layout.c"
+    fields = {"slqr_mixed_opts": abi.SlqrMixedOpts, "slqr_mixed_info": abi.SlqrMixedInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slqr.h"', 'int main(void) {']
+    for cname, cls in fields.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+    lines.append('  return 0;\n}')
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", f"-I{os.path.join(ROOT, 'include')}", "-o", str(exe),
+                           str(src)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for cls in fields.values():
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f, _ in cls._fields_]
+    assert out == want
