@@ -170,6 +170,96 @@ def cpu_sample_desc():
             f"8192x{CPU_SAMPLE_COLS})")
 
 
+SERVE_ORACLE_SAMPLE = 24       # requests of the serving stream timed on the oracle
+BATCH_ORACLE_PER_CORE = 200    # batch problems per host core in the all-cores oracle run
+
+
+def start_oracle_legs(mixed_in):
+    """The CPU legs beyond the headline sample, started before the GPU work so
+    that they run on the host cores meanwhile (spawned worker processes,
+    oracle/jobs.py): the oracle's solves of the 8192 x 4096 conditioned
+    matrices (their timing, and the reference solutions every mixed-precision
+    cell is compared with) and a sample of the request stream, one request at
+    a time on one core."""
+    from oracle import jobs
+    import workloads
+    r = jobs.Runner(workers=4)
+    for kappa, (A, bc, xt, br) in (mixed_in or {}).items():
+        r.submit(f"cond_{kappa:.0e}", A.cpu().numpy(), [bc.cpu().numpy(), br.cpu().numpy()])
+    t, n, meq, seeds = workloads.serving_stream(SERVE_ORACLE_SAMPLE, 100.0)
+    r.submit_call("requests", jobs.requests_job,
+                  list(zip(n.tolist(), meq.tolist(), seeds.tolist())))
+    return r
+
+
+def _warm(_):
+    return os.getpid()
+
+
+def oracle_batch_all_cores():
+    """The oracle on a bounded sample of the 20,000-problem batch (its first
+    BATCH_ORACLE_PER_CORE x cores problems: the same shape distribution), one
+    chunk of problems per host core in spawned processes, and the same
+    per-core rate.  Returns problems/s over all cores and per core."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    import workloads
+    from oracle import jobs
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ms, ns = workloads.batch_shapes(BATCH_COUNT)
+    count = min(BATCH_COUNT, BATCH_ORACLE_PER_CORE * cores)
+    chunks = [(ms[i:count:cores].tolist(), ns[i:count:cores].tolist(), workloads.SEED_BATCH + 17 + i)
+              for i in range(cores)]
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_warm, range(cores)))                  # workers started and imported
+        t0 = time.perf_counter()
+        secs = list(pool.map(jobs.batch_chunk_job, *zip(*chunks)))
+        wall = time.perf_counter() - t0
+    flops = sum(2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + 4.0 * m * n - n * n
+                for m, n in zip(ms[:count].tolist(), ns[:count].tolist()))
+    return {"problems": count, "cores": cores, "wall_s": wall,
+            "problems_per_s_all_cores": count / wall, "gflops_all_cores": flops / wall / 1e9,
+            "problems_per_s_per_core": count / sum(secs),
+            "sample": f"the first {count} problems of the seeded batch (m ~ U{{16..512}}, "
+                      f"n ~ U{{ceil(m/4)..m}}), one chunk per core"}
+
+
+def finish_oracle_legs(r, mixed, sols, inputs):
+    """Collect the background legs, state every mixed cell's error against the
+    oracle, then time the all-cores batch sample and the 256 x 128 problem."""
+    import oracle
+    import workloads
+    res, oracle_x = {}, {}
+    m3, n3 = MIXED_SHAPE
+    fl3 = 2.0 * m3 * n3 * n3 - 2.0 * n3 ** 3 / 3.0
+    for kappa in (MIXED_KAPPAS if inputs else ()):
+        out = r.result(f"cond_{kappa:.0e}", timeout=1200)
+        oracle_x[kappa] = out["x"]
+        res[f"config3_8192x4096_kappa_{kappa:.0e}"] = {
+            "factor_s": out["factor_seconds"], "solve_s_2rhs": out["solve_seconds"],
+            "factor_gflops": fl3 / out["factor_seconds"] / 1e9, "cores": 1}
+    if mixed is not None and inputs:
+        mixed_errors(mixed, sols, inputs, oracle_x)
+    req = np.array(r.value("requests", timeout=900)) * 1e3
+    res["config5_requests"] = {"count": int(req.size), "p50_ms": float(np.percentile(req, 50)),
+                               "p99_ms": float(np.percentile(req, 99)),
+                               "mean_ms": float(req.mean()), "cores": 1,
+                               "sample": f"the first {req.size} requests of the seeded stream "
+                                         "(dense oracle LS solve of [L^T; C], one at a time)"}
+    r.shutdown()
+    res["config4_batch"] = oracle_batch_all_cores()
+    A1, b1 = workloads.gaussian(256, 128, workloads.SEED_SMALL)
+    ts = []
+    for _ in range(25):
+        t0 = time.perf_counter()
+        oracle.lstsq(A1, b1)
+        ts.append(time.perf_counter() - t0)
+    res["config1_256x128_us"] = float(np.median(ts) * 1e6)
+    return res
+
+
 def gen_inputs():
     import workloads
     mats = []
@@ -228,6 +318,11 @@ def run_ours(args, rank, world, local_rank):
     ctx = api.Context(local_rank)
     stream = torch.cuda.current_stream(device)
     mats_h = gen_inputs()
+    # the 8192 x 4096 conditioned matrices, and the CPU legs that run on the
+    # host cores while the GPU works (rank 0 of a single-GPU run only)
+    cpu_legs = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+    mixed_in = mixed_inputs(device) if not args.no_mixed else None
+    legs = start_oracle_legs(mixed_in if cpu_legs else None) if cpu_legs else None
 
     # device-resident inputs and working buffers
     bufs = []
@@ -362,9 +457,13 @@ def run_ours(args, rank, world, local_rank):
     if ctx.sync() != 0:
         raise RuntimeError(abi.slqr_last_error(ctx.ctx))
 
+    # ---- the 256 x 128 single problem: latency of one LS solve ----
+    single = single_problem_latency(ctx, device, stream, barrier)
+
     # ---- batched workload: 20,000 uneven problems in one persistent launch ----
     batch = run_batch_workload(ctx, device, stream, barrier) if not args.no_batch else None
-    mixed = run_mixed_workload(ctx, device, stream, barrier) if not args.no_mixed else None
+    mixed, sols = (run_mixed_workload(ctx, device, stream, barrier, mixed_in)
+                   if not args.no_mixed else (None, None))
     serving = run_serving_workload(local_rank) if not args.no_serving else None
 
     # ---- roofline of the dominant kernel (most device time in the timed region) ----
@@ -388,8 +487,10 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return 0
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    cpu, oracle_legs = None, None
+    if cpu_legs:
+        oracle_legs = finish_oracle_legs(legs, mixed, sols, mixed_in)
+        single["oracle_us"] = oracle_legs["config1_256x128_us"]
         f, s = oracle_sample(mats_h)
         cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": cpu_sample_desc(), "seconds": s}
@@ -410,30 +511,47 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "kernels": kernels,
         "factor_only": factor_only,
+        "single_256x128": single,
         "batch": batch,
         "mixed_8192x4096": mixed,
         "serving": serving,
+        "oracle": oracle_legs,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
 
 
-def run_mixed_workload(ctx, device, stream, barrier, kappas=(1e2, 1e6, 1e10), m=8192, n=4096):
-    """8192 x 4096 matrices U diag(sigma) V^T with cond 1e2 / 1e6 / 1e10: the FP64
-    path (factor + Q^T b + solve) against the mixed path (FP32 factorization +
-    FP64-residual refinement), errors stated against x_true (consistent b) and
-    against the FP64 solution (random b)."""
-    import torch
+MIXED_KAPPAS = (1e2, 1e6, 1e10)
+MIXED_SHAPE = (8192, 4096)
+U64 = 2.0 ** -53
+
+
+def mixed_inputs(device):
+    """The 8192 x 4096 conditioned matrices (kappa 1e2 / 1e6 / 1e10, seeds 4 / 5 /
+    6), drawn on the device: {kappa: (A, b_consistent, x_true, b_random)}."""
     import workloads
+    m, n = MIXED_SHAPE
+    return {k: workloads.conditioned_device(m, n, k, device=device) for k in MIXED_KAPPAS}
+
+
+def run_mixed_workload(ctx, device, stream, barrier, inputs):
+    """Every (kappa, b, precision) cell of the 8192 x 4096 conditioned workload:
+    the FP64 path (factor + Q^T b + solve) and slqr_lstsq_mixed_ex in its
+    automatic mode (Bjorck sweeps, then GMRES-IR, then the flagged FP64
+    fallback) for SLQR_FP32 / SLQR_TF32 / SLQR_BF16X3.  Returns the timings and
+    statuses, and the solutions (host) whose errors against the oracle
+    mixed_errors() states once the oracle's solves are done."""
+    import torch
     from paper_2506_09463_gb300 import abi
-    out = {}
+    m, n = MIXED_SHAPE
+    out, sols = {}, {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flops = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + (4.0 * m * n - 2.0 * n * n) + n * n
-    for kappa in kappas:
-        A, b_cons, x_true, b_rand = workloads.conditioned_device(m, n, kappa, device=device)
+    precs = (("fp32", abi.SLQR_FP32), ("tf32", abi.SLQR_TF32), ("bf16x3", abi.SLQR_BF16X3))
+    for kappa in MIXED_KAPPAS:
+        A, b_cons, x_true, b_rand = inputs[kappa]
         rec = {}
-        # FP64 path
         for name, b in (("consistent", b_cons), ("random", b_rand)):
             Aw, bw = A.t().clone().t(), b.clone()
             barrier()
@@ -442,56 +560,98 @@ def run_mixed_workload(ctx, device, stream, barrier, kappas=(1e2, 1e6, 1e10), m=
             e1.record(stream)
             barrier()
             t64 = e0.elapsed_time(e1)
-            x64 = x64.clone()
-            xm = torch.zeros(n, dtype=torch.float64, device=device)
-            barrier()
-            e0.record(stream)
-            st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
-                                                xm.data_ptr(), abi.SLQR_FP32, 0, 0.0,
-                                                stream.cuda_stream)
-            e1.record(stream)
-            barrier()
-            tm = e0.elapsed_time(e1)
-            r = {"fp64_ms": t64, "fp64_gflops": flops / (t64 / 1e3) / 1e9,
-                 "mixed_fp32_ms": tm, "mixed_gflops_equiv": flops / (tm / 1e3) / 1e9,
-                 "mixed_status": abi.STATUS_NAMES.get(st, st), "refine_iters": its,
-                 "refine_last_step": err,
-                 "mixed_vs_fp64_rel": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))}
-            # the same with the trailing update on the tensor cores (TF32)
-            xt = torch.zeros(n, dtype=torch.float64, device=device)
-            barrier()
-            e0.record(stream)
-            st2, its2, err2 = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
-                                                   xt.data_ptr(), abi.SLQR_TF32, 0, 0.0,
-                                                   stream.cuda_stream)
-            e1.record(stream)
-            barrier()
-            tt = e0.elapsed_time(e1)
-            r.update({"tf32_tc_ms": tt, "tf32_status": abi.STATUS_NAMES.get(st2, st2),
-                      "tf32_refine_iters": its2, "tf32_refine_last_step": err2,
-                      "tf32_vs_fp64_rel": float(torch.linalg.norm(xt - x64) / torch.linalg.norm(x64))})
-            # and with BF16 operands split into hi + lo on the tensor cores
-            xb = torch.zeros(n, dtype=torch.float64, device=device)
-            barrier()
-            e0.record(stream)
-            st3, its3, err3 = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
-                                                   xb.data_ptr(), abi.SLQR_BF16X3, 0, 0.0,
-                                                   stream.cuda_stream)
-            e1.record(stream)
-            barrier()
-            tb = e0.elapsed_time(e1)
-            r.update({"bf16x3_tc_ms": tb, "bf16x3_status": abi.STATUS_NAMES.get(st3, st3),
-                      "bf16x3_refine_iters": its3, "bf16x3_refine_last_step": err3,
-                      "bf16x3_vs_fp64_rel": float(torch.linalg.norm(xb - x64) / torch.linalg.norm(x64))})
+            r = {"fp64_ms": t64, "fp64_gflops": flops / (t64 / 1e3) / 1e9}
+            sols[(kappa, name, "fp64")] = x64.cpu().numpy().copy()
+            del Aw, bw
+            for pname, prec in precs:
+                x = torch.zeros(n, dtype=torch.float64, device=device)
+                barrier()
+                e0.record(stream)
+                st, info = abi.slqr_lstsq_mixed_ex(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
+                                                   x.data_ptr(), prec, stream.cuda_stream,
+                                                   fp64_fallback=1)
+                e1.record(stream)
+                barrier()
+                tm = e0.elapsed_time(e1)
+                method = {abi.SLQR_REFINE_BJORCK: "bjorck", abi.SLQR_REFINE_GMRES: "gmres-ir",
+                          abi.SLQR_REFINE_FP64: "fp64-fallback"}.get(info["method"], info["method"])
+                r[pname] = {"ms": tm, "speedup_vs_fp64": t64 / tm,
+                            "status": abi.STATUS_NAMES.get(st, st), "method": method,
+                            "sweeps": info["sweeps"], "gmres_steps": info["gmres_steps"],
+                            "gmres_iters": info["gmres_iters"], "last_step": info["err"],
+                            "kappa_est": info["kappa_est"]}
+                sols[(kappa, name, pname)] = x.cpu().numpy().copy()
             if name == "consistent":
-                r["fp64_err_vs_x_true"] = float(torch.linalg.norm(x64 - x_true) / torch.linalg.norm(x_true))
-                r["mixed_err_vs_x_true"] = float(torch.linalg.norm(xm - x_true) / torch.linalg.norm(x_true))
+                xt = x_true.cpu().numpy()
+                r["fp64_err_vs_x_true"] = float(np.linalg.norm(sols[(kappa, name, "fp64")] - xt)
+                                                / np.linalg.norm(xt))
             rec[name] = r
         out[f"kappa_{kappa:.0e}"] = rec
-        del A, b_cons, x_true, b_rand
     if ctx.sync() != 0:
         raise RuntimeError("device status after the mixed workload")
-    return out
+    return out, sols
+
+
+def mixed_errors(mixed, sols, inputs, oracle_x):
+    """Per cell: ||x - x_o|| / ||x_o|| and max |x_i - x_o,i| / ||x_o||_inf against
+    the oracle's solution x_o, and the tolerance max(1e-10, 64 (kappa + kappa^2
+    ||r|| / (||A|| ||x_o||)) u) (||A|| = 1 by construction)."""
+    for kappa in MIXED_KAPPAS:
+        if kappa not in oracle_x:
+            continue
+        A, b_cons, x_true, b_rand = inputs[kappa]
+        rec = mixed[f"kappa_{kappa:.0e}"]
+        for j, (name, b) in enumerate((("consistent", b_cons), ("random", b_rand))):
+            x_o = oracle_x[kappa][:, j]
+            r_o = b.cpu().numpy() - A.cpu().numpy() @ x_o
+            tol = max(1e-10, 64.0 * (kappa + kappa ** 2 * np.linalg.norm(r_o) /
+                                     np.linalg.norm(x_o)) * U64)
+            rec[name]["tol_vs_oracle"] = tol
+            for pname in ("fp64", "fp32", "tf32", "bf16x3"):
+                x = sols[(kappa, name, pname)]
+                rel = float(np.linalg.norm(x - x_o) / np.linalg.norm(x_o))
+                mx = float(np.max(np.abs(x - x_o)) / np.max(np.abs(x_o)))
+                if pname == "fp64":
+                    rec[name]["fp64_err_vs_oracle"] = rel
+                    rec[name]["fp64_maxerr_vs_oracle"] = mx
+                else:
+                    rec[name][pname]["err_vs_oracle"] = rel
+                    rec[name][pname]["maxerr_vs_oracle"] = mx
+                    rec[name][pname]["within_tol"] = bool(rel <= tol and mx <= tol)
+
+
+def single_problem_latency(ctx, device, stream, barrier, reps=50):
+    """The 256 x 128 problem (seed 1): one factor + Q^T b + back-substitution,
+    device time (CUDA events) and host time through the API (from the first
+    call to the end of the solve, with a stream synchronisation), medians."""
+    import torch
+    import workloads
+    A, b = workloads.gaussian(256, 128, workloads.SEED_SMALL)
+    A0 = colmajor_cuda(A, device)
+    b0 = torch.from_numpy(b.copy()).to(device)
+    Aw = A0.t().clone().t()
+    bw = b0.clone()
+    up = torch.empty(128, dtype=torch.float64, device=device)
+    wy = ctx.wy_buffer(256, 128, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev_us, host_us = [], []
+    for _ in range(reps + 5):
+        Aw.copy_(A0)
+        bw.copy_(b0)
+        barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        ctx.factor(Aw, up, wy)
+        ctx.apply_qt(Aw, up, bw, wy=wy)
+        ctx.solve_r(Aw, bw)
+        e1.record(stream)
+        stream.synchronize()
+        host_us.append((time.perf_counter() - t0) * 1e6)
+        dev_us.append(e0.elapsed_time(e1) * 1e3)
+    if ctx.sync() != 0:
+        raise RuntimeError("device status after the 256 x 128 problem")
+    return {"device_us": float(np.median(dev_us[5:])), "host_us": float(np.median(host_us[5:])),
+            "reps": reps}
 
 
 def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):

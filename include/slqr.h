@@ -102,6 +102,21 @@ slqr_status slqr_sync(slqr_ctx *ctx, void *stream);
 slqr_status slqr_check_bounded_wait(slqr_ctx *ctx, unsigned polls, void *stream);
 
 /*
+ * Set how many polls a bounded device wait of this context makes before it
+ * gives up (1 .. 2^24; 0 restores the default 2^24, about 1.5 s): the panel
+ * factorization's polled exchange of per-column records and grid barrier,
+ * and the grid barriers of the mixed-precision Q application and triangular
+ * solves.  A wait that gives up records SLQR_ETIMEOUT in the status word
+ * (slqr_sync; slqr_lstsq_mixed and slqr_lstsq_mixed_ex return it) and its
+ * kernel returns, leaving that call's outputs unspecified; the context stays
+ * usable.  The tensor-core kernels' mbarrier waits keep the fixed default.
+ * A failure-detection aid (no counterpart in the paper): with a limit of a
+ * few polls the waits run out on purpose.  Not while calls are in flight.
+ * Errors: SLQR_EINVAL (polls above 2^24, NULL context).
+ */
+slqr_status slqr_set_spin_limit(slqr_ctx *ctx, unsigned polls);
+
+/*
  * Panel width the factorization uses for an m x n problem (columns per
  * compact-WY block).  It depends only on (m, n).
  */

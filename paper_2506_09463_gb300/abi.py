@@ -74,6 +74,7 @@ SIGNATURES = [
     ("slqr_last_error", ctypes.c_char_p, [_vp]),
     ("slqr_sync", _c_int, [_vp, _vp]),
     ("slqr_check_bounded_wait", _c_int, [_vp, ctypes.c_uint, _vp]),
+    ("slqr_set_spin_limit", _c_int, [_vp, ctypes.c_uint]),
     ("slqr_panel_width", _c_int, [_c_int, _c_int]),
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
@@ -197,6 +198,10 @@ def slqr_autotune(ctx, m, n):
 
 def slqr_check_bounded_wait(ctx, polls, stream=None) -> int:
     return _lib.slqr_check_bounded_wait(ctx, polls, stream)
+
+
+def slqr_set_spin_limit(ctx, polls: int) -> int:
+    return _lib.slqr_set_spin_limit(ctx, polls)
 
 
 def slqr_factor(ctx, m, n, A, lda, up, wy, stream) -> int:

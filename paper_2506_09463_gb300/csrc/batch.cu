@@ -477,7 +477,9 @@ struct BatchMixedParams {
 };
 
 constexpr int kBMaxPanels = kBMaxRows / kBNB;
-constexpr size_t kBGtDoubles = (size_t)kBMaxPanels * kBNB * kBNB + 2 * kBMaxRows;
+// per-CTA global scratch of the mixed kernel: G of every panel, tau, up and
+// the column scales d_j of the equilibration
+constexpr size_t kBGtDoubles = (size_t)kBMaxPanels * kBNB * kBNB + 3 * kBMaxRows;
 
 // V(i, a) of panel p from the FP32 factorization (rows relative to k0 = p*kBNB)
 __device__ __forceinline__ float mixed_v(const float *Af, int m, const double *up, int k0,
@@ -663,6 +665,7 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
   double *G = bp.gt + (size_t)blockIdx.x * kBGtDoubles;
   double *tau = G + (size_t)kBMaxPanels * kBNB * kBNB;
   double *up = tau + kBMaxRows;
+  double *dcol = up + kBMaxRows;       // d_j = 2^-e_j: the FP32 copy is of A D
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
     if (tid == 0) s_item = (int)atomicAdd(bp.counter, 1u);
@@ -680,10 +683,28 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
       }
       continue;
     }
-    // FP32 working copy (ld = m), then the FP32 factorization
+    // column equilibration by exact powers of two (the largest entry of each
+    // column of A D in [1/2, 1): no FP32 overflow or underflow of products for
+    // any column scale), the FP32 working copy of A D (ld = m), then its FP32
+    // factorization; the refinement solves for y with x = D y
+    for (int j = warp; j < n; j += kBWarps) {
+      double mx = 0.0;
+      for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(pr.A[SLQR_IDX(i, j, pr.lda)]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) {
+        int ex = 0;
+        if (mx > 0.0 && isfinite(mx)) {
+          frexp(mx, &ex);
+          ex = max(-1000, min(1000, ex));
+        }
+        dcol[j] = ldexp(1.0, -ex);
+      }
+    }
+    __syncthreads();
     for (int idx = tid; idx < m * n; idx += kThreads) {
       int c = idx / m, r = idx - c * m;
-      Af[idx] = (float)pr.A[SLQR_IDX(r, c, pr.lda)];
+      Af[idx] = (float)(pr.A[SLQR_IDX(r, c, pr.lda)] * dcol[c]);
     }
     __syncthreads();
     batch_factor_core<float>(Af, m, m, n, up, nullptr, G, tau, smraw, pr.ntop);
@@ -717,13 +738,13 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
         for (; j < n; ++j) a0 = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], a0);
         f[i] = (float)((a0 + a1) + (a2 + a3));
       }
-      // g = -A^T r (FP64), one warp per column
+      // g = -D A^T r (FP64), one warp per column
       for (int j = warp; j < n; j += kBWarps) {
         double acc = 0.0;
         for (int i = lane; i < m; i += 32) acc = fma(pr.A[SLQR_IDX(i, j, pr.lda)], r[i], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) g[j] = (float)(-acc);
+        if (lane == 0) g[j] = (float)(-acc * dcol[j]);
       }
       __syncthreads();
       bool zero = mixed_trsv(Af, m, n, g, false);            // h = R^-T g (in g)
@@ -731,7 +752,7 @@ batch_factor_mixed_kernel(BatchMixedParams bp) {
       for (int i = tid; i < m; i += kThreads) e[i] = (i < n) ? f[i] - g[i] : f[i];
       __syncthreads();
       zero |= mixed_trsv(Af, m, n, e, true);                 // dx = R^-1 (d1 - h) (in e[0:n])
-      for (int i = tid; i < n; i += kThreads) dx[i] = (double)e[i];
+      for (int i = tid; i < n; i += kThreads) dx[i] = (double)e[i] * dcol[i];
       for (int i = tid; i < m; i += kThreads) f[i] = (i < n) ? g[i] : f[i];   // [h; d2]
       __syncthreads();
       mixed_apply_q(Af, m, n, G, tau, up, f, w, false);       // dr = Q [h; d2] (in f)

@@ -247,6 +247,13 @@ extern "C" slqr_status slqr_check_bounded_wait(slqr_ctx *ctx, unsigned polls, vo
   return st;
 }
 
+extern "C" slqr_status slqr_set_spin_limit(slqr_ctx *ctx, unsigned polls) {
+  if (!ctx || polls > kSpinLimit) return SLQR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->spin_limit = polls == 0 ? kSpinLimit : polls;
+  return SLQR_OK;
+}
+
 extern "C" const char *slqr_last_error(slqr_ctx *ctx) {
   if (!ctx) return "NULL context";
   return ctx->last_error.c_str();

@@ -71,6 +71,7 @@ struct PanelParams {
   int stacked;         // stacked [L^T; C]: the diagonal block's strict lower part is zero
   int P, R;            // CTAs, rows per CTA
   unsigned bar_base;   // counter value when this panel starts
+  unsigned spin;       // polls of a bounded wait before it gives up
 };
 
 // Row map of a panel: row i of the panel (0 <= i < m - k0 - skip) is matrix
@@ -223,7 +224,7 @@ panel_kernel(PanelParams p) {
       if (lane == 0 && c < nbw) rec[(size_t)cta * RECW + c] = (double)mx;
     }
   }
-  if (!grid_barrier(p.bar, p.bar_base + (unsigned)p.P, p.status, &s_ok)) return;
+  if (!grid_barrier(p.bar, p.bar_base + (unsigned)p.P, p.status, &s_ok, p.spin)) return;
   {
     constexpr int QMAX = (PMAX + GROUPS - 1) / GROUPS;
     const double *rec = p.srec;
@@ -338,7 +339,7 @@ panel_kernel(PanelParams p) {
         }
         unsigned it = 0;
         while (pend != 0) {                           // bounded
-          if (++it > kSpinLimit) { ok = false; break; }
+          if (++it > p.spin) { ok = false; break; }
           if (it > 8) __nanosleep(32);
 #pragma unroll
           for (int t = 0; t < PW; ++t) {
@@ -374,7 +375,7 @@ panel_kernel(PanelParams p) {
           double x;
           unsigned it = 0;
           while (is_unset(x = ld_relaxed_f64(rec + (size_t)(q0 + t) * RECW + c))) {
-            if (++it > kSpinLimit) { ok = false; break; }
+            if (++it > p.spin) { ok = false; break; }
             __nanosleep(32);
           }
           acc += (Acc)x;
@@ -383,7 +384,7 @@ panel_kernel(PanelParams p) {
       if (tid < nbw) {
         unsigned it = 0;
         while (is_unset(pv)) {
-          if (++it > kSpinLimit) { ok = false; break; }
+          if (++it > p.spin) { ok = false; break; }
           __nanosleep(32);
           pv = ld_relaxed_f64(prow + tid);
         }
@@ -487,7 +488,7 @@ panel_kernel(PanelParams p) {
       if (c < jj) mine[jj * (jj - 1) / 2 + c] = Gloc[idx];
     }
   }
-  if (!grid_barrier(p.bar, p.bar_base + 2u * (unsigned)p.P, p.status, &s_ok)) return;
+  if (!grid_barrier(p.bar, p.bar_base + 2u * (unsigned)p.P, p.status, &s_ok, p.spin)) return;
   for (int idx = cta + tid * p.P; idx < NB * NB; idx += kThreads * p.P) {
     const int jj = idx / NB, c = idx - jj * NB;
     double v = 0.0;
@@ -1077,6 +1078,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     pp.prow = prow; pp.bar = bar;
     pp.status = ctx->d_status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.skip = skip; pp.stacked = ntop > 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    pp.spin = ctx->spin_limit;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(T));
     // algorithmic flops of the panel: per column j a norm over M-j entries and,
@@ -1483,6 +1485,7 @@ static slqr_status noalloc_factor_impl(double *scratch, int num_sms, int m, int 
     pp.prow = prow; pp.bar = bar;
     pp.status = status; pp.m = m; pp.lda = lda; pp.k0 = k0; pp.nbw = nbw;
     pp.skip = 0; pp.stacked = 0; pp.P = P; pp.R = R; pp.bar_base = bar_base;
+    pp.spin = kSpinLimit;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(double));
     e = cudaLaunchCooperativeKernel(panel_kernel_for<double, NB>(P), dim3(P), dim3(kThreads), args,

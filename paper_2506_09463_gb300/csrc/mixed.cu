@@ -33,25 +33,50 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 constexpr double kStallOk = 1e-10;
 constexpr int kColChunk = 256;
 
-// A32 = (float) A
+// Column equilibration by exact powers of two: D = diag(d_j), d_j = 2^-e_j
+// with 2^(e_j - 1) <= max_i |a_ij| < 2^e_j, so that every column of A D has
+// its largest entry in [1/2, 1).  The low-precision factorization is of A D
+// (no FP32 overflow or underflow of products for any column scale); the
+// refinement solves for y with x = D y, its residuals still in FP64 from A.
+// One warp per column.
+__global__ void col_scale_kernel(const double *__restrict__ A, int lda, int m, int n,
+                                 double *__restrict__ d) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double mx = 0.0;
+  for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(A[SLQR_IDX(i, warp, lda)]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) {
+      frexp(mx, &e);
+      e = max(-1000, min(1000, e));     // d_j stays a finite power of two
+    }
+    d[warp] = ldexp(1.0, -e);
+  }
+}
+
+// A32 = (float) (A D)
 __global__ void to_f32_kernel(const double *__restrict__ A, int lda, int m, int n,
-                              float *__restrict__ A32, int lda32) {
+                              const double *__restrict__ d, float *__restrict__ A32, int lda32) {
   const size_t total = (size_t)lda32 * n;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(idx / lda32), i = (int)(idx - (size_t)j * lda32);
-    A32[idx] = (i < m) ? (float)A[SLQR_IDX(i, j, lda)] : 0.f;
+    A32[idx] = (i < m) ? (float)(A[SLQR_IDX(i, j, lda)] * d[j]) : 0.f;
   }
 }
 
-// partial row sums of A x over column chunks: part[chunk][i]
+// partial row sums of A (D x) over column chunks: part[chunk][i] (d NULL: D = I)
 __global__ void __launch_bounds__(kRowsPerCta)
 ax_partial_kernel(const double *__restrict__ A, int lda, int m, int n,
-                  const double *__restrict__ x, double *__restrict__ part) {
+                  const double *__restrict__ x, const double *__restrict__ d,
+                  double *__restrict__ part) {
   const int i = blockIdx.x * kRowsPerCta + threadIdx.x;
   const int j0 = blockIdx.y * kColChunk, j1 = min(n, j0 + kColChunk);
   __shared__ double xs[kColChunk];
-  for (int j = j0 + threadIdx.x; j < j1; j += kRowsPerCta) xs[j - j0] = x[j];
+  for (int j = j0 + threadIdx.x; j < j1; j += kRowsPerCta) xs[j - j0] = d ? x[j] * d[j] : x[j];
   __syncthreads();
   if (i >= m) return;
   double acc = 0.0;
@@ -70,16 +95,17 @@ __global__ void resid_f_kernel(const double *__restrict__ b, const double *__res
   f32[i] = (float)(b[i] - r[i] - ax);
 }
 
-// g = -A^T r (one warp per column), g32 = (float) g
+// g = -(A D)^T r (one warp per column), g32 = (float) g
 __global__ void resid_g_kernel(const double *__restrict__ A, int lda, int m, int n,
-                               const double *__restrict__ r, float *__restrict__ g32) {
+                               const double *__restrict__ r, const double *__restrict__ d,
+                               float *__restrict__ g32) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   double acc = 0.0;
   for (int i = lane; i < m; i += 32) acc = fma(A[SLQR_IDX(i, warp, lda)], r[i], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) g32[warp] = (float)(-acc);
+  if (lane == 0) g32[warp] = (float)(-acc * d[warp]);
 }
 
 // e[0:n] = d[0:n] - h ; keep d[n:m] in e (e aliases nothing)
@@ -89,16 +115,16 @@ __global__ void form_e_kernel(const float *__restrict__ d, const float *__restri
   if (i < m) e[i] = (i < n) ? d[i] - h[i] : d[i];
 }
 
-// d[0:n] = h (so that d = [h; d2]); x += dx (FP64); per-CTA maxima of |dx|, |x|
+// d[0:n] = h (so that d = [h; d2]); x += D dy (FP64); per-CTA maxima of |D dy|, |x|
 __global__ void update_kernel(float *__restrict__ d, const float *__restrict__ h,
-                              const float *__restrict__ dx, double *__restrict__ x, int n,
-                              double *__restrict__ maxima) {
+                              const float *__restrict__ dx, const double *__restrict__ cs,
+                              double *__restrict__ x, int n, double *__restrict__ maxima) {
   __shared__ double s_dx[256], s_x[256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, c = 0.0;
   if (i < n) {
     d[i] = h[i];
-    const double v = (double)dx[i];
+    const double v = (double)dx[i] * cs[i];
     const double xn = x[i] + v;
     x[i] = xn;
     // a non-finite entry (an FP32 overflow in the factorization) becomes +inf,
@@ -194,6 +220,7 @@ struct QvecParams {
   int trans;             // 1: Q^T f, 0: Q f
   int R, P;
   unsigned bar_base;
+  unsigned spin;         // polls of the grid barrier before it gives up
 };
 
 template <typename VT>
@@ -288,7 +315,8 @@ qvec_kernel(QvecParams<VT> p) {
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");      // this panel's T has landed
-    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok,
+                      p.spin))
       return;
     fetch_t(step + 1, (step + 1) & 1);                   // the next panel's T, in flight
     // phase B: W (all CTAs, fixed order: thread (a, g) sums the partials of
@@ -373,6 +401,7 @@ struct TrsvParams {
   int *status;
   int lda, n, nblk, P;
   unsigned bar_base;
+  unsigned spin;         // polls of the grid barrier before it gives up
 };
 
 template <bool UPPER, typename VT>
@@ -452,7 +481,8 @@ trsv_coop_kernel(TrsvParams<VT> p) {
     // loaded while the owner of block b solves
     const bool upd_one = one && (UPPER ? cta < b : cta > b);
     if (upd_one) load_update(cta, b);
-    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok))
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned)(step + 1) * (unsigned)p.P, p.status, &s_ok,
+                      p.spin))
       return;
     if (tid < 64) xs[tid] = (tid < rows) ? __ldcg(p.y + b0 + tid) : (VT)0;
     __syncthreads();
@@ -520,16 +550,17 @@ __global__ void resid64_f_kernel(const double *__restrict__ b, const double *__r
   f[i] = b[i] - r[i] - ax;
 }
 
-// out[j] = sgn * (A^T v)[j], one warp per column
+// out[j] = sgn * d_j * (A^T v)[j], one warp per column
 __global__ void atv_kernel(const double *__restrict__ A, int lda, int m, int n,
-                           const double *__restrict__ v, double sgn, double *__restrict__ out) {
+                           const double *__restrict__ v, double sgn, const double *__restrict__ d,
+                           double *__restrict__ out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   double acc = 0.0;
   for (int i = lane; i < m; i += 32) acc = fma(A[SLQR_IDX(i, warp, lda)], v[i], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[warp] = sgn * acc;
+  if (lane == 0) out[warp] = sgn * acc * d[warp];
 }
 
 // middle of M^-1 [f; g] in place on w = [w_s (m); w_x (n)] after h = R^-T g
@@ -607,12 +638,12 @@ __global__ void vec_scale_kernel(double *__restrict__ w, size_t N, double s) {
     w[i] *= s;
 }
 
-// z = V[:, 0:k] y; r += z[0:m], x += z[m:m+n]; per-CTA maxima of |dx| and |x|
+// z = V[:, 0:k] y; r += z[0:m], x += D z[m:m+n]; per-CTA maxima of |dx| and |x|
 // (a non-finite entry counts as +inf, so that it is never taken as converged)
 __global__ void __launch_bounds__(256)
 gmres_update_kernel(const double *__restrict__ V, size_t N, int k, const double *__restrict__ y,
                     double *__restrict__ r, int m, double *__restrict__ x, int n,
-                    double *__restrict__ maxima) {
+                    const double *__restrict__ d, double *__restrict__ maxima) {
   __shared__ double ys[kMaxKrylov];
   __shared__ double s_dx[256], s_x[256];
   for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[q];
@@ -626,9 +657,10 @@ gmres_update_kernel(const double *__restrict__ V, size_t N, int k, const double 
       r[i] += z;
     } else {
       const size_t j = i - m;
-      const double xn = x[j] + z;
+      const double dz = z * d[j];
+      const double xn = x[j] + dz;
       x[j] = xn;
-      a = fmax(a, isfinite(z) ? fabs(z) : CUDART_INF);
+      a = fmax(a, isfinite(dz) ? fabs(dz) : CUDART_INF);
       c = fmax(c, isfinite(xn) ? fabs(xn) : CUDART_INF);
     }
   }
@@ -683,6 +715,7 @@ static slqr_status trsv_vec(slqr_ctx *ctx, const float *R, int lda, int n, VT *y
   tp.lda = lda; tp.n = n; tp.nblk = (n + 63) / 64;
   tp.P = std::min(tp.nblk, ctx->num_sms);
   tp.bar_base = bar_base;
+  tp.spin = ctx->spin_limit;
   void *args[] = {&tp};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)trsv_coop_kernel<UPPER, VT>,
                                               dim3(tp.P), dim3(kThreads), args, 0, s);
@@ -701,6 +734,7 @@ struct MixedSolve {
   double *x;
   float *A32;
   double *up, *wy, *r, *part, *maxima;
+  double *colscale;                    // D: powers of two, x = D y
   int *zero_flag;
   float *f32, *g32, *e32, *Tm32, *qpart32;
   double *Tm64, *qpart64;
@@ -720,6 +754,7 @@ static slqr_status apply_q_vec(MixedSolve &ms, VT *f, const VT *Tm, VT *qpart, b
   qp.status = ms.ctx->d_status; qp.lda = ms.lda32; qp.m = ms.m; qp.K = ms.K; qp.nb = ms.nb;
   qp.np = ms.np; qp.trans = trans ? 1 : 0; qp.R = ms.qv_R; qp.P = ms.qv_P;
   qp.bar_base = ms.qbar_base;
+  qp.spin = ms.ctx->spin_limit;
   void *args[] = {&qp};
   cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel<VT>, dim3(ms.qv_P),
                                                dim3(kThreads), args,
@@ -761,9 +796,10 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
   slqr_status st;
   for (it = 1; it <= max_iter; ++it) {
     ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, s>>>(
-        ms.A, ms.lda, m, n, ms.x, ms.part);
+        ms.A, ms.lda, m, n, ms.x, nullptr, ms.part);
     resid_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.b, ms.r, ms.part, ms.chunks, m, ms.f32);
-    resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, ms.g32);
+    resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, ms.colscale,
+                                                         ms.g32);
     ctx->launch_count += 3;
     st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
     if (st != SLQR_OK) return st;                                       // h = R^-T g
@@ -773,7 +809,8 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
     ++ctx->launch_count;
     st = trsv_vec<true>(ctx, ms.A32, ms.lda32, n, ms.e32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
     if (st != SLQR_OK) return st;                                       // dx = R^-1 (d1 - h)
-    update_kernel<<<ms.ublocks, 256, 0, s>>>(ms.f32, ms.g32, ms.e32, ms.x, n, ms.maxima);
+    update_kernel<<<ms.ublocks, 256, 0, s>>>(ms.f32, ms.g32, ms.e32, ms.colscale, ms.x, n,
+                                             ms.maxima);
     ++ctx->launch_count;                                                // d = [h; d2], x += dx
     st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, false);           // dr = Q [h; d2]
     if (st != SLQR_OK) return st;
@@ -826,13 +863,14 @@ static slqr_status precondition64(MixedSolve &ms, double *w) {
   return apply_q_vec(ms, ws, ms.Tm64, ms.qpart64, false);               // Q [h; d2]
 }
 
-// y = Aaug v = [v_s + A v_x; A^T v_s]
+// y = Aaug v = [v_s + A D v_x; D A^T v_s] (the augmented matrix of A D)
 static void aug_matvec(MixedSolve &ms, const double *v, double *y) {
   const int m = ms.m, n = ms.n;
   ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, ms.s>>>(
-      ms.A, ms.lda, m, n, v + m, ms.part);
+      ms.A, ms.lda, m, n, v + m, ms.colscale, ms.part);
   aug_s_kernel<<<(m + 255) / 256, 256, 0, ms.s>>>(v, ms.part, ms.chunks, m, y);
-  atv_kernel<<<(n * 32 + 255) / 256, 256, 0, ms.s>>>(ms.A, ms.lda, m, n, v, 1.0, y + m);
+  atv_kernel<<<(n * 32 + 255) / 256, 256, 0, ms.s>>>(ms.A, ms.lda, m, n, v, 1.0, ms.colscale,
+                                                     y + m);
   ms.ctx->launch_count += 3;
 }
 
@@ -857,12 +895,13 @@ static slqr_status gmres_ir(MixedSolve &ms, double tol, int max_iters, double in
   double e_prev = HUGE_VAL;
   slqr_status st;
   for (int step = 1; step <= max_steps && res->iters < max_iters; ++step) {
-    // residual of the augmented system in FP64: f = b - r - A x, g = -A^T r
+    // residual of the augmented system in FP64: f = b - r - A x, g = -D A^T r
     double *V0 = ms.Vk;
     ax_partial_kernel<<<dim3((m + kRowsPerCta - 1) / kRowsPerCta, ms.chunks), kRowsPerCta, 0, s>>>(
-        ms.A, ms.lda, m, n, ms.x, ms.part);
+        ms.A, ms.lda, m, n, ms.x, nullptr, ms.part);
     resid64_f_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.b, ms.r, ms.part, ms.chunks, m, V0);
-    atv_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, -1.0, V0 + m);
+    atv_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, -1.0, ms.colscale,
+                                                    V0 + m);
     ctx->launch_count += 3;
     st = precondition64(ms, V0);
     if (st != SLQR_OK) return st;
@@ -932,7 +971,8 @@ static slqr_status gmres_ir(MixedSolve &ms, double tol, int max_iters, double in
     e = cudaMemcpyAsync(ms.ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
     const int ub = std::min(4 * ctx->num_sms, (int)((N + 255) / 256));
-    gmres_update_kernel<<<ub, 256, 0, s>>>(ms.Vk, N, k, ms.ydev, ms.r, m, ms.x, n, ms.maxima);
+    gmres_update_kernel<<<ub, 256, 0, s>>>(ms.Vk, N, k, ms.ydev, ms.r, m, ms.x, n, ms.colscale,
+                                           ms.maxima);
     ++ctx->launch_count;
     ++res->steps;
     double dmax, xmax;
@@ -1052,6 +1092,7 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
   const size_t o_h = use_gmres ? take((size_t)2 * (restart + 2) * sizeof(double)) : 0;
   const size_t o_y = use_gmres ? take((size_t)restart * sizeof(double)) : 0;
   const size_t o_dr = take(2 * sizeof(double));
+  const size_t o_cs = take((size_t)n * sizeof(double));
   slqr_status st = ensure_workspace2(ctx, off);
   if (st != SLQR_OK) return st;
   char *base = (char *)ctx->ws2.ptr;
@@ -1069,6 +1110,7 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
   ms.qpart32 = (float *)(base + o_qpart);
   ms.qbar = (unsigned *)(base + o_bar);
   ms.drange = (double *)(base + o_dr);
+  ms.colscale = (double *)(base + o_cs);
   if (use_gmres) {
     ms.Tm64 = (double *)(base + o_tm64);
     ms.qpart64 = (double *)(base + o_qpart64);
@@ -1085,9 +1127,10 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
                              (int)qvec_smem_bytes<double>(nb, ms.qv_R));
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
 
-  // the FP32 factorization
-  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, ms.A32, ms.lda32);
-  ++ctx->launch_count;
+  // the FP32 factorization, of A D
+  col_scale_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, ms.colscale);
+  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, ms.colscale, ms.A32, ms.lda32);
+  ctx->launch_count += 2;
   ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
   if (prec == SLQR_BF16X3) {
     ctx->sh_hi = base + o_shh;
@@ -1146,6 +1189,16 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
   }
   st = check_launch(ctx, "lstsq_mixed");
   if (st != SLQR_OK) return st;
+  // a bounded device wait that gave up leaves the factorization or a
+  // correction incomplete: report it (it stays in the status word for
+  // slqr_sync as well)
+  {
+    int dstat = 0;
+    e = cudaMemcpyAsync(&dstat, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "status word: %s", cudaGetErrorString(e));
+    if (dstat == SLQR_ETIMEOUT) return fail(ctx, SLQR_ETIMEOUT, "a bounded device wait gave up");
+  }
   if (status == SLQR_ENOCONV && o.fp64_fallback) {
     st = fp64_fallback(ctx, m, n, A, lda, b, x, s);
     if (st != SLQR_OK) return st;

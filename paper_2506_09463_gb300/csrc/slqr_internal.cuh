@@ -24,7 +24,9 @@ constexpr int kThreads = 256;          // threads per CTA of the tiled kernels
 constexpr int kMaxPanelRowsPerCta = 384;  // rows of a panel one CTA holds in smem (NB=64)
 
 // Upper bound on spin iterations of a device-side wait (each iteration sleeps
-// ~100 ns), after which the kernel records SLQR_ETIMEOUT and returns.
+// ~100 ns), after which the kernel records SLQR_ETIMEOUT and returns.  The
+// default of a context's limit (slqr_set_spin_limit), and the fixed limit of
+// the tensor-core kernels' mbarrier waits.
 constexpr unsigned kSpinLimit = 1u << 24;
 
 // Device status word codes (same values as the C ABI).
@@ -77,6 +79,8 @@ struct slqr_ctx {
   // 2: BF16 split in hi + lo, with the BF16 shadows of the matrix below)
   int tc_mode = 0;
   void *sh_hi = nullptr, *sh_lo = nullptr;
+  // limit of the polled exchanges and grid barriers of the cooperative kernels
+  unsigned spin_limit = slqr::kSpinLimit;
   std::string last_error;
   // serialises the entry points of one context; recursive so that a driver
   // (the mixed-precision solve's FP64 fallback) can call other entry points
@@ -165,11 +169,11 @@ __device__ __forceinline__ void record_status(int *status, int code) {
   atomicCAS(status, kStatusOk, code);
 }
 
-// Arrive at a grid barrier (a monotonic arrival counter) and wait, bounded,
-// until it reaches `target`.  Returns false after recording SLQR_ETIMEOUT.
-// Cooperative launches only (every CTA resident).
+// Arrive at a grid barrier (a monotonic arrival counter) and wait, bounded by
+// `limit` polls, until it reaches `target`.  Returns false after recording
+// SLQR_ETIMEOUT.  Cooperative launches only (every CTA resident).
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
-                                             int *s_ok) {
+                                             int *s_ok, unsigned limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -177,7 +181,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
     unsigned it = 0;
     int ok = 1;
     while (ld_acquire_u32(bar) < target) {
-      if (++it > kSpinLimit) { ok = 0; break; }
+      if (++it > limit) { ok = 0; break; }
       if (it > 256) __nanosleep(64);
     }
     __threadfence();

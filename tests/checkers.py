@@ -89,3 +89,16 @@ def cond_estimate(R, iters: int = 40, seed: int = 0):
         smin_inv = float(torch.linalg.norm(w)) ** 0.5
         w = w / torch.linalg.norm(w)
     return smax * smin_inv
+
+
+def norm2_estimate(R, iters: int = 40, seed: int = 1):
+    """||R||_2 by power iteration on R^T R."""
+    n = R.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    v = torch.randn(n, 1, generator=g, dtype=R.dtype).to(R.device)
+    s = 0.0
+    for _ in range(iters):
+        v = R.T @ (R @ v)
+        s = float(torch.linalg.norm(v)) ** 0.5
+        v = v / torch.linalg.norm(v)
+    return s
