@@ -734,7 +734,8 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
     out = {"problems": count, "shapes": "m ~ U{16..512}, n ~ U{ceil(m/4)..m}, N(0,1), seed 7",
            "algorithmic_gflop": flops / 1e9}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for name, prec in (("fp64", abi.SLQR_FP64), ("mixed_fp32", abi.SLQR_FP32)):
+
+    def time_batch(prec):
         times = []
         for rep in range(reps + 1):
             A_flat.copy_(A0)
@@ -749,11 +750,29 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
             barrier()
             if rep:
                 times.append(e0.elapsed_time(e1))
-        t = min(times)
+        return min(times)
+
+    import time as _t
+    for name, prec in (("fp64", abi.SLQR_FP64), ("mixed_fp32", abi.SLQR_FP32)):
+        # the default setting (panels of 16, tiles of 32 for every size class),
+        # then the autotuner's choice per size class, which the batch uses
+        abi.slqr_batch_set_tuning(prec, -1, 0, 0)
+        t_default = time_batch(prec)
+        t0 = _t.perf_counter()
+        stt, choice, tms = abi.slqr_batch_autotune(ctx.ctx, prec, list(ms), list(ns))
+        abi.check(ctx.ctx, stt, "slqr_batch_autotune")
+        tune_s = _t.perf_counter() - t0
+        t = time_batch(prec)
         stv = status.cpu().numpy()
         rec = {"ms": t, "problems_per_s": count / (t / 1e3), "gflops": flops / (t / 1e3) / 1e9,
                "ok": int(np.sum(stv == 0)), "erank": int(np.sum(stv == abi.SLQR_ERANK)),
-               "no_conv": int(np.sum(stv == abi.SLQR_ENOCONV))}
+               "no_conv": int(np.sum(stv == abi.SLQR_ENOCONV)),
+               "default_setting_ms": t_default,
+               "default_setting_problems_per_s": count / (t_default / 1e3),
+               "autotune_s": tune_s,
+               "autotune_sample_ms_before_after": list(tms),
+               "tuned_settings": [{"m_max": abi.slqr_batch_class_rows(c), "panel_width": nb,
+                                   "tile_cols": tc} for c, (nb, tc) in enumerate(choice)]}
         if prec == abi.SLQR_FP32:
             ev = err.cpu().numpy()
             rec["refine_err_max"] = float(ev[stv == 0].max()) if np.any(stv == 0) else None
@@ -770,7 +789,8 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
         else:
             x64 = b_flat.clone()
         out[name] = rec
-    # the same FP64 batch as a plan (problem table uploaded once, CUDA-graph launch)
+    # the same FP64 batch as a plan (problem table uploaded once, CUDA-graph
+    # launch), with the tuned settings
     stp, plan = abi.slqr_batch_plan_create(ctx.ctx, list(ms), list(ns), None, A_ptrs, lda,
                                            up_ptrs, b_ptrs, abi.SLQR_FP64, status.data_ptr(),
                                            None)

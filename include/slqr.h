@@ -291,6 +291,52 @@ slqr_status slqr_batch_factor(slqr_ctx *ctx, int count, const int *m, const int 
 int slqr_batch_max_rows(void);
 
 /*
+ * Settings of the batched kernels and their autotuner (the batch form of the
+ * paper's alpha/beta task sizes, Section 4.1).  A batched problem is factored
+ * by one CTA in panels of `panel_width` reflectors (8, 16 or 32), its trailing
+ * columns updated in tiles of `tile_cols` columns (16, 32 or 64); the valid
+ * pairs are those with panel_width * tile_cols >= 256: (8, 32), (8, 64),
+ * (16, 16), (16, 32), (16, 64), (32, 16), (32, 32), (32, 64).  The setting is
+ * chosen per precision (SLQR_FP64, SLQR_FP32) and per size class of the
+ * problem's row count m: class 0 m <= 64, 1 m <= 128, 2 m <= 256, 3 m <= 512
+ * (slqr_batch_class_rows gives the upper bounds); (16, 32) by default.  The
+ * problems of classes that share a setting run in one persistent launch; a
+ * batch whose classes use different settings makes one launch per setting,
+ * one after the other on the caller's stream.  Settings are process-wide:
+ * change them only while no batch or plan creation is in flight (a plan keeps
+ * the settings it was created with).
+ *
+ * slqr_batch_set_tuning  sets the pair of one class (m_class -1: every class);
+ *                        (0, 0) restores the default.  SLQR_EINVAL for an
+ *                        invalid precision, class or pair.
+ * slqr_batch_get_tuning  reads it (HOST outputs, each may be NULL).
+ * slqr_batch_autotune    tunes the settings of `prec` for a mixture of
+ *                        shapes: count, m, n (HOST arrays) give the shapes of
+ *                        the caller's batch (count 0 or m NULL: the default
+ *                        law m ~ U{16..512}, n ~ U{ceil(m/4)..m}); a scratch
+ *                        batch of `sample` problems (<= 0: min(count, 3000);
+ *                        every (count/sample)-th shape; generic entries; fused
+ *                        solve) is timed (best of two runs after a warm-up)
+ *                        under each candidate.  Greedy coordinate search: the
+ *                        classes costliest first, each trying every valid
+ *                        pair with the other classes held, a change kept only
+ *                        when the whole scratch batch runs at least 1% faster
+ *                        (a split into several launches must pay for itself).
+ *                        Synchronous; allocates and frees its scratch.  HOST
+ *                        outputs, each may be NULL: panel widths and tile
+ *                        widths per class (slqr_batch_classes() entries), and
+ *                        ms[2] = the scratch batch's time before and after.
+ *                        Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA; on
+ *                        error the previous settings are kept.
+ */
+int slqr_batch_classes(void);
+int slqr_batch_class_rows(int m_class);
+slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_width, int tile_cols);
+slqr_status slqr_batch_get_tuning(int prec, int m_class, int *panel_width, int *tile_cols);
+slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, const int *m, const int *n,
+                                int sample, int *panel_width, int *tile_cols, double *ms);
+
+/*
  * slqr_batch_factor for stacked SLSQP matrices A_i = [L_i^T; C_i]: problem i
  * is (n[i] + m_eq[i]) x n[i] with an upper-triangular top n[i] x n[i] block,
  * factored with the structure of slqr_factor_stacked.  The strictly lower part

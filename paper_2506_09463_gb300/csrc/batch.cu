@@ -1,811 +1,89 @@
-// batch.cu -- many independent H12 least-squares problems in one persistent
-// launch (slqr_batch_factor).
+// batch.cu -- host side of the batched H12 least squares (slqr_batch_factor,
+// slqr_batch_factor_stacked, batch plans) and the batch autotuner.
 //
 // Each problem is the factorization of Alg. 2 (update_pivot_row, then
 // update_trailing_non_pivot_row on every later column; Task 1 skip rule),
 // optionally followed by Q^T b and the back-substitution (Section 1: the
-// stored reflectors are reused by the solve).  Problems are independent, so
-// one CTA owns one problem at a time; persistent CTAs take the next problem
-// from a device-side atomic counter over a list ordered costliest first
-// (longest-processing-time first), the GPU descendant of the paper's shared
-// main_queue of ready tasks (Alg. 5).
+// stored reflectors are reused by the solve); the kernels are in
+// batch_core.cuh.  Problems are independent, so one CTA owns one problem at a
+// time; persistent CTAs take the next problem from a device-side atomic
+// counter over a list ordered costliest first (longest-processing-time
+// first), the GPU descendant of the paper's shared main_queue of ready tasks
+// (Alg. 5).
 //
-// Inside a CTA a problem is factored in panels of kBNB reflectors:
-//  * the panel (rows k0..m-1, kBNB columns) sits in shared memory; each column
-//    is one block-level reduction (scaled norm, dots of the column tail with
-//    the other panel columns, which also give striu(V^T V)), then the update
-//    of the later panel columns;
-//  * the trailing columns (and b, as one more column) are updated in tiles of
-//    32 columns: W = V^T C (8 lanes per column, each over every 8th row),
-//    then W' = T^T W by forward substitution (one lane per column), then
-//    C -= V W' (the same lanes as W).
-// All arithmetic is FP64 (DFMA).
-#include "slqr_internal.cuh"
-
-#include <math_constants.h>
+// Settings.  The panel width NB and the tile width TC of the kernels are
+// chosen per size class of the problems (m <= 64, <= 128, <= 256, <= 512) and
+// per precision, the batch form of the paper's alpha/beta task sizes
+// (Section 4.1): slqr_batch_autotune times every valid setting on scratch
+// batches of each class and keeps the fastest; by default every class uses
+// NB = 16, TC = 32.  The problems of the classes that share a setting go into
+// one persistent launch (with its own costliest-first order and work
+// counter); the launches of a batch follow each other on the caller's stream,
+// costliest group first.
+#include "batch_core.cuh"
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
 namespace slqr {
 
-constexpr int kBNB = 16;          // reflectors per panel
-constexpr int kBMaxRows = 512;    // rows of a batched problem (panel slice in smem)
-constexpr int kBCols = 32;        // trailing columns per tile
-constexpr int kBWarps = kThreads / 32;
-constexpr int kBRowGroups = 8;                  // lanes of a column in the tile phases
-constexpr int kBGroupCols = 32 / kBRowGroups;   // columns of one warp in the tile phases
-static_assert(kBGroupCols * kBWarps == kBCols, "one column group per warp covers the tile");
-constexpr int kBMaxRefine = 12;        // refinement sweeps of the mixed path
-constexpr double kBRefineTol = 1e-14;  // stop when ||dx||_inf <= tol ||x||_inf
-constexpr double kBStallOk = 1e-10;    // a stalled refinement is accepted below this
+BatchKernels batch_kernels_nb16(int tc) {
+  switch (tc) {
+    case 16: return batch_kernels_of<16, 16>();
+    case 32: return batch_kernels_of<16, 32>();
+    case 64: return batch_kernels_of<16, 64>();
+    default: return BatchKernels{};
+  }
+}
 
-struct BatchProblem {
-  double *A;
-  double *up;
-  double *b;
-  int m, n, lda;
-  int ntop;          // > 0: stacked [L^T; C] with an upper-triangular top block of ntop rows
+// kernels of a setting (null pointers when not valid)
+static BatchKernels batch_kernels(int nb, int tc) {
+  switch (nb) {
+    case 8: return batch_kernels_nb8(tc);
+    case 16: return batch_kernels_nb16(tc);
+    case 32: return batch_kernels_nb32(tc);
+    default: return BatchKernels{};
+  }
+}
+
+// size classes of the problems by their row count
+constexpr int kBClasses = 4;
+static const int kBClassHi[kBClasses] = {64, 128, 256, kBMaxRows};
+static int batch_class(int m) {
+  for (int c = 0; c < kBClasses; ++c)
+    if (m <= kBClassHi[c]) return c;
+  return kBClasses - 1;
+}
+
+struct BatchSetting {
+  int nb = kBNBDefault, tc = kBTCDefault;
+  bool operator==(const BatchSetting &o) const { return nb == o.nb && tc == o.tc; }
 };
+// per precision (0: SLQR_FP64, 1: SLQR_FP32) and size class
+static BatchSetting g_batch_setting[2][kBClasses];
+static std::mutex g_batch_mu;
 
-struct BatchParams {
-  const BatchProblem *probs;
-  const int *order;
-  int count;
-  unsigned *counter;
-  int *status;
-};
-
-// Exponent bits of |x| (as a double): the integer order of these bit patterns
-// is the numeric order, so a max over them finds the largest magnitude.
-template <typename T>
-__device__ __forceinline__ unsigned b_abs_hi(T x) {
-  return (unsigned)((unsigned long long)__double_as_longlong((double)x) >> 32) & 0x7fffffffu;
+static BatchSetting batch_setting(int prec, int cls) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  return g_batch_setting[prec == SLQR_FP32 ? 1 : 0][cls];
 }
 
-// 2^e as a double for e in [-1022, 1023] (exact; built from the exponent bits)
-__device__ __forceinline__ double b_pow2(int e) {
-  return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// Sum of 16 per-lane values acc[0..15] over the 8 lanes g = lane & 7 of one
-// column group by a halving exchange: at each of three levels a lane keeps
-// half of its values and adds the other half received from its partner (14
-// shuffles and adds per lane instead of 48 for 16 separate butterflies).
-// Afterwards lane g holds the totals of values 2g and 2g + 1 in acc[0], acc[1].
-template <typename T>
-__device__ __forceinline__ void b_group8_sum16(T (&acc)[kBNB], int g) {
-  static_assert(kBNB == 16, "three halving levels over 8 lanes");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const bool hi = (g & 4) != 0;
-    const T send = hi ? acc[i] : acc[i + 8];
-    const T keep = hi ? acc[i + 8] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool hi = (g & 2) != 0;
-    const T send = hi ? acc[i] : acc[i + 4];
-    const T keep = hi ? acc[i + 4] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool hi = (g & 1) != 0;
-    const T send = hi ? acc[i] : acc[i + 2];
-    const T keep = hi ? acc[i + 2] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-  }
-}
-
-__device__ __forceinline__ float b_warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ double b_warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Shared-memory layout of the batched kernels.  The panel slice Ps and the
-// W tile are of the working type T (double for SLQR_FP64, float for the
-// mixed-precision path); the small per-panel quantities are double.
-__host__ __device__ constexpr size_t align_up_c(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-template <typename T>
-struct BatchSmem {
-  static constexpr int kPanel = kBNB * kBMaxRows;       // Ps[c][r]
-  static constexpr int kW = kBNB * (kBCols + 1);        // Wt[a][col]
-  static constexpr int kG = kBNB * kBNB;                // G[q][j] (ld kBNB)
-  // T copies of the panel's G and tau for W' = T^T W (phase B)
-  static constexpr size_t kBytesT = (size_t)(kPanel + kW + kG + kBNB) * sizeof(T);
-  static constexpr int kMisc = 7 * kBNB + 8;  // dots, sigma, tau, up, scale, 1/scale, fast, norm
-  static constexpr size_t kBytes = align_up_c(kBytesT, 16) + (size_t)(kG + kMisc) * sizeof(double);
-};
-
-// The H12 factorization of one m x n problem by one CTA (see the file
-// header).  T == double: all FP64.  T == float: dot products, updates, the
-// norm, cl, up, b and sigma in FP32 (FP64 for a column whose power-of-two
-// scale is extreme for FP32), up, tau and G stored in FP64.  When
-// G_out/tau_out are given, each panel's
-// striu(V^T V) and tau are kept there (the mixed path reuses them to apply Q).
-// Bcol (T == double only) is an extra right-hand-side column updated with the
-// trailing columns, giving Q^T b.
-//
-// ntop > 0: A = [L^T; C] with an upper-triangular top block of ntop rows.  A
-// panel at k0 then uses its own nbw diagonal rows and the rows of C only (row
-// r of the panel is matrix row k0 + r for r < nbw, k0 + skip + r below, with
-// skip = ntop - k0 - nbw): the rows between are zero in every reflector and
-// untouched by the update.
-template <typename T>
-__device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, double *Bcol,
-                                  double *G_out, double *tau_out, char *smraw, int ntop) {
-  using SM = BatchSmem<T>;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g8 = lane & (kBRowGroups - 1);
-  T *Ps = (T *)smraw;
-  T *Wt = Ps + SM::kPanel;
-  T *Gt = Wt + SM::kW;              // G and tau of the panel in T (phase B)
-  T *taut = Gt + SM::kG;
-  double *Gs = (double *)(smraw + align_up_c(SM::kBytesT, 16));
-  double *dots = Gs + SM::kG;
-  double *sig = dots + kBNB;
-  double *tau = sig + kBNB;
-  double *ups = tau + kBNB;
-  double *scl = ups + kBNB;         // per-column scale 2^-E of the panel
-  double *sinv = scl + kBNB;        // and its inverse 2^E
-  double *fst = sinv + kBNB;        // 1: FP32 pivot for this column (T == float, |E| <= 60)
-  double *misc = fst + kBNB;        // [0] = norm
-  // An FP32 factorization (T == float) forms the norm, the pivot and the
-  // multipliers in FP32 (its per-column chain then stays off the FP64 pipe);
-  // a column whose power-of-two scale is extreme for FP32 forms its pivot in
-  // FP64.  T == double: everything FP64.
-  constexpr bool kF32 = std::is_same<T, float>::value;
-  const int K = num_reflectors(m, n);
-  for (int k = K + tid; k < n; k += kThreads) up_out[k] = 0.0;
-
-  for (int k0 = 0; k0 < K; k0 += kBNB) {
-    const int nbw = min(kBNB, K - k0);
-    const int skip = ntop > 0 ? ntop - k0 - nbw : 0;
-    const int M = m - k0 - skip;
-    // matrix row (relative to k0) of panel row r
-    auto prow = [&](int r) { return r + (r >= nbw ? skip : 0); };
-    // (stacked: the strictly lower part of the diagonal block is zero, not read)
-    for (int idx = tid; idx < kBNB * M; idx += kThreads) {
-      int c = idx / M, r = idx - c * M;
-      const bool zero = c >= nbw || (ntop > 0 && r < nbw && r > c);
-      Ps[c * kBMaxRows + r] = zero ? T(0) : A[SLQR_IDX(k0 + prow(r), k0 + c, lda)];
-    }
-    __syncthreads();
-    // Per-column scale of the panel for the overflow-safe norm: 2^-E with E the
-    // exponent of the column's largest |entry| from its diagonal down (an exact
-    // power of two; entries that earlier reflectors of the panel add stay
-    // within a factor sqrt(M) of it).
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int c = warp + kBWarps * t;
-      if (c < nbw) {
-        unsigned mx = 0;
-        for (int r = c + lane; r < M; r += 32) mx = max(mx, b_abs_hi(Ps[c * kBMaxRows + r]));
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) {
-          int E = (int)((mx >> 20) & 0x7ff) - 1023;
-          // (FP32: 2^-E and 2^E both normal floats)
-          E = kF32 ? min(max(E, -126), 126) : min(max(E, -1000), 1022);
-          scl[c] = b_pow2(-E);
-          sinv[c] = b_pow2(E);
-          fst[c] = (kF32 && E >= -60 && E <= 60) ? 1.0 : 0.0;
-        }
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < nbw; ++j) {
-      const T *x = Ps + j * kBMaxRows;
-      // phase 1: warp w takes panel columns w and w + 8
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int c = warp + kBWarps * t;
-        if (c >= nbw) continue;
-        if (c == j) {
-          const T sc = (T)scl[j];
-          T S = T(0), S1 = T(0);                       // two chains
-          int r = j + lane;
-          for (; r + 32 < M; r += 64) {
-            const T xs = x[r] * sc, xs1 = x[r + 32] * sc;
-            S = fma(xs, xs, S);
-            S1 = fma(xs1, xs1, S1);
-          }
-          if (r < M) {
-            const T xs = x[r] * sc;
-            S = fma(xs, xs, S);
-          }
-          S = b_warp_sum(S + S1);
-          if (lane == 0) {                             // exact rescale by 2^E
-            if (S == T(0)) misc[0] = 0.0;
-            else if (kF32 && fst[j] != 0.0) misc[0] = (double)(sqrt(S) * (T)sinv[j]);
-            else misc[0] = sqrt((double)S) * sinv[j];
-          }
-        } else {
-          const T *col = Ps + c * kBMaxRows;
-          T acc = T(0), acc1 = T(0);                   // two chains
-          int r = j + 1 + lane;
-          for (; r + 32 < M; r += 64) {
-            acc = fma(x[r], col[r], acc);
-            acc1 = fma(x[r + 32], col[r + 32], acc1);
-          }
-          if (r < M) acc = fma(x[r], col[r], acc);
-          acc += acc1;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) dots[c] = (double)acc;
-        }
-      }
-      __syncthreads();
-      const double s = misc[0];
-      const bool defined = (s != 0.0);
-      double cl = 0.0, upk = 0.0, tk = 0.0;
-      if (kF32 && fst[j] != 0.0) {                     // FP32 pivot and multipliers
-        const T sT = (T)s, x0 = x[j];
-        T clT = T(0), upT = T(0), tkT = T(0);
-        if (defined) {
-          clT = (x0 > T(0)) ? -sT : sT;
-          upT = x0 - clT;
-          if (warp == 0) tkT = T(-1) / (upT * clT);    // tau = -1/b (warp 0 uses it)
-        }
-        if (tid < nbw) {
-          const int c = tid;
-          const T pr_c = Ps[c * kBMaxRows + j];
-          if (c > j) sig[c] = defined ? (double)(-(upT * pr_c + (T)dots[c]) * tkT) : 0.0;
-          else if (c < j) Gs[c + j * kBNB] = (double)(pr_c * upT + (T)dots[c]);
-        }
-        cl = clT;
-        upk = upT;
-        tk = tkT;
-      } else {
-        const double x0 = (double)x[j];
-        if (defined) {
-          cl = (x0 > 0.0) ? -s : s;
-          upk = x0 - cl;
-          if (warp == 0) tk = -1.0 / (upk * cl);      // tau = -1/b (warp 0 uses it)
-        }
-        if (tid < nbw) {
-          const int c = tid;
-          const double pr_c = (double)Ps[c * kBMaxRows + j];
-          // sigma_c = (up p_c + D_c) / b = -(up p_c + D_c) tau
-          if (c > j) sig[c] = defined ? -(upk * pr_c + dots[c]) * tk : 0.0;
-          else if (c < j) Gs[c + j * kBNB] = pr_c * upk + dots[c];
-        }
-      }
-      __syncthreads();
-      if (defined) {
-        const T upT = (T)upk;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int c = warp + kBWarps * t;
-          if (c > j && c < nbw) {
-            T *col = Ps + c * kBMaxRows;
-            const T sg = (T)sig[c];
-            for (int r = j + 1 + lane; r < M; r += 32) col[r] = fma(sg, x[r], col[r]);
-            if (lane == 0) col[j] = fma(sg, upT, col[j]);
-          }
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        if (defined) Ps[j * kBMaxRows + j] = (T)cl;
-        tau[j] = tk;
-        ups[j] = upk;
-      }
-      __syncthreads();
-    }
-    // write the panel back; keep G and tau if asked; then turn the slice into
-    // V (zero above the diagonal, up on it) for the trailing update
-    for (int idx = tid; idx < nbw * M; idx += kThreads) {
-      int c = idx / M, r = idx - c * M;
-      if (!(ntop > 0 && r < nbw && r > c)) A[SLQR_IDX(k0 + prow(r), k0 + c, lda)] = Ps[c * kBMaxRows + r];
-    }
-    if (tid < nbw) up_out[k0 + tid] = ups[tid];
-    if (G_out) {
-      double *Gp = G_out + (size_t)(k0 / kBNB) * kBNB * kBNB;
-      for (int idx = tid; idx < kBNB * kBNB; idx += kThreads) {
-        int jj = idx / kBNB, q = idx - jj * kBNB;
-        Gp[idx] = (q < jj && jj < nbw) ? Gs[idx] : 0.0;
-      }
-      if (tid < kBNB) tau_out[k0 + tid] = (tid < nbw) ? tau[tid] : 0.0;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < kBNB * kBNB; idx += kThreads) {
-      int c = idx / kBNB, r = idx - c * kBNB;
-      if (r <= c && r < M) Ps[c * kBMaxRows + r] = (r == c && c < nbw) ? (T)ups[c] : T(0);
-      Gt[idx] = (T)Gs[idx];
-    }
-    if (tid < kBNB) taut[tid] = (T)tau[tid];
-    __syncthreads();
-
-    // trailing columns [k0 + nbw, n), plus Bcol as one more column
-    const int NT = n - (k0 + nbw);
-    const int NC = NT + (Bcol ? 1 : 0);
-    for (int t0 = 0; t0 < NC; t0 += kBCols) {
-      // phase A: W[a][col] = sum_r V[a][r] C[r][col].  Warp w takes the four
-      // columns 4w .. 4w+3 of the tile; lane = 8 * (column - 4w) + g walks
-      // the rows r = g (mod 8), so a column's 16 partial sums are combined
-      // over 8 lanes only (14 adds per lane) and a ragged M leaves at most
-      // 7 lanes of a column idle on its last row step.
-      if (t0 + kBGroupCols * warp < NC) {
-        const int cc = kBGroupCols * warp + (lane >> 3);
-        const int col = t0 + cc;
-        T acc[kBNB];
-#pragma unroll
-        for (int a = 0; a < kBNB; ++a) acc[a] = T(0);
-        if (col < NC) {
-          const T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (const T *)(Bcol + k0);
-#pragma unroll 4
-          for (int r = g8; r < M; r += kBRowGroups) {
-            const T cv = C[prow(r)];
-#pragma unroll
-            for (int a = 0; a < kBNB; ++a)
-              if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
-          }
-        }
-        b_group8_sum16(acc, g8);                // lane g holds W[2g], W[2g + 1]
-        if (col < NC) {
-          Wt[(2 * g8) * (kBCols + 1) + cc] = acc[0];
-          Wt[(2 * g8 + 1) * (kBCols + 1) + cc] = acc[1];
-        }
-      }
-      __syncthreads();
-      // phase B: W' = T^T W, one lane per column, in T (an FP32
-      // factorization keeps this chain off the slow FP64 pipe)
-      if (warp == 0 && t0 + lane < NC) {
-        T w[kBNB];
-#pragma unroll
-        for (int jj = 0; jj < kBNB; ++jj) {
-          if (jj < nbw) {
-            T t = Wt[jj * (kBCols + 1) + lane];
-#pragma unroll
-            for (int q = 0; q < jj; ++q) t = fma(-Gt[q + jj * kBNB], w[q], t);
-            w[jj] = taut[jj] * t;
-            Wt[jj * (kBCols + 1) + lane] = w[jj];
-          }
-        }
-      }
-      __syncthreads();
-      // phase C: C -= V W', the same lane layout as phase A
-      {
-        const int cc = kBGroupCols * warp + (lane >> 3);
-        const int col = t0 + cc;
-        if (col < NC) {
-          T *C = (col < NT) ? A + SLQR_IDX(k0, k0 + nbw + col, lda) : (T *)(Bcol + k0);
-          T w[kBNB];
-#pragma unroll
-          for (int a = 0; a < kBNB; ++a) w[a] = (a < nbw) ? Wt[a * (kBCols + 1) + cc] : T(0);
-#pragma unroll 4
-          for (int r = g8; r < M; r += kBRowGroups) {
-            const int pr = prow(r);
-            T cv = C[pr];
-#pragma unroll
-            for (int a = 0; a < kBNB; ++a)
-              if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
-            C[pr] = cv;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Back-substitution R x = (Q^T b)[0:n] of the FP64 path, column-oriented.
-__device__ void batch_solve_fp64(const double *A, int lda, int n, double *b, double *xs,
-                                 int *status_out) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += kThreads) xs[i] = b[i];
-  __syncthreads();
-  bool rank_def = false;
-  for (int i = n - 1; i >= 0; --i) {
-    const double d = A[SLQR_IDX(i, i, lda)];
-    if (tid == 0) xs[i] = (d != 0.0) ? xs[i] / d : 0.0;
-    if (d == 0.0) rank_def = true;
-    __syncthreads();
-    const double xi = xs[i];
-    for (int l = tid; l < i; l += kThreads) xs[l] = fma(-A[SLQR_IDX(l, i, lda)], xi, xs[l]);
-    __syncthreads();
-  }
-  for (int i = tid; i < n; i += kThreads) b[i] = xs[i];
-  if (tid == 0) *status_out = rank_def ? SLQR_ERANK : SLQR_OK;
-  __syncthreads();
-}
-
-constexpr size_t kBSmemBytes = BatchSmem<double>::kBytes;
-
-__global__ void __launch_bounds__(kThreads, 2)   // two CTAs per SM
-batch_factor_fp64_kernel(BatchParams bp) {
-  extern __shared__ __align__(16) char smraw[];
-  __shared__ int s_item;
-  __shared__ int s_status;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.counter, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= bp.count) break;
-    const int p = bp.order[item];
-    const BatchProblem pr = bp.probs[p];
-    if (pr.n > 0) {
-      batch_factor_core<double>(pr.A, pr.lda, pr.m, pr.n, pr.up, pr.b, nullptr, nullptr, smraw,
-                                pr.ntop);
-      if (pr.b) {
-        batch_solve_fp64(pr.A, pr.lda, pr.n, pr.b, (double *)smraw, &s_status);
-      } else if (threadIdx.x == 0) {
-        s_status = SLQR_OK;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0 && bp.status) bp.status[p] = s_status;
-    } else if (threadIdx.x == 0 && bp.status) {
-      bp.status[p] = SLQR_OK;
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
-// Mixed precision (SLQR_FP32): the factorization runs in FP32 on a scratch
-// copy of A (up, tau and G stored in FP64), and the LS solution is recovered by
-// iterative refinement of the augmented system [I A; A^T 0][r; x] = [b; 0]
-// (Bjorck): residuals f = b - r - A x and g = -A^T r in FP64 from the
-// original A, the correction through the FP32 QR:
-//   h = R^-T g,  d = Q^T f,  dx = R^-1 (d[0:n] - h),  dr = Q [h; d[n:m]].
-// This converges to the FP64 LS solution when kappa times the backward error
-// of the FP32 factorization (a modest multiple of u_fp32) is below 1, for
-// consistent and inconsistent right-hand sides alike.
-// --------------------------------------------------------------------------
-struct BatchMixedParams {
-  const BatchProblem *probs;
-  const int *order;
-  int count;
-  unsigned *counter;
-  int *status;
-  double *err;
-  float *af;            // per CTA: kBMaxRows * kBMaxRows floats
-  double *gt;           // per CTA: G (kMaxPanels * kBNB^2) + tau (kBMaxRows) + up (kBMaxRows)
-  int max_it;
-  double tol;
-};
-
-constexpr int kBMaxPanels = kBMaxRows / kBNB;
-// per-CTA global scratch of the mixed kernel: G of every panel, tau, up and
-// the column scales d_j of the equilibration
-constexpr size_t kBGtDoubles = (size_t)kBMaxPanels * kBNB * kBNB + 3 * kBMaxRows;
-
-// V(i, a) of panel p from the FP32 factorization (rows relative to k0 = p*kBNB)
-__device__ __forceinline__ float mixed_v(const float *Af, int m, const double *up, int k0,
-                                         int nbw, int i, int a) {
-  if (a >= nbw || i < a) return 0.f;
-  if (i == a) return (float)up[k0 + a];
-  return Af[SLQR_IDX(k0 + i, k0 + a, m)];
-}
-
-// y <- Q^T y (forward = true) or y <- Q y, panel by panel, FP32 arithmetic.
-// Per panel each thread loads the V entries of its rows (at most two: m <=
-// 512) once, all in flight, and keeps them in registers for both products:
-// w = V^T y (per-thread partials, a halving exchange over the warp, then the
-// 8 warp totals), w' = T^T w or T w on warp 0, then y -= V w'.  red holds
-// kBWarps * kBNB floats.
-constexpr int kBRowsPerThread = kBMaxRows / kThreads;
-static_assert(kBRowsPerThread * kThreads == kBMaxRows, "rows per thread");
-
-__device__ void mixed_apply_q(const float *Af, int m, int n, const double *G, const double *tau,
-                              const double *up, float *y, float *red, bool forward) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int K = num_reflectors(m, n);
-  const int np = num_panels(K, kBNB);
-  for (int s = 0; s < np; ++s) {
-    const int pnl = forward ? s : np - 1 - s;
-    const int k0 = pnl * kBNB;
-    const int nbw = min(kBNB, K - k0);
-    const int M = m - k0;
-    float vr[kBRowsPerThread][kBNB];
-    float yv[kBRowsPerThread];
-    float acc[kBNB];
-#pragma unroll
-    for (int a = 0; a < kBNB; ++a) acc[a] = 0.f;
-#pragma unroll
-    for (int t = 0; t < kBRowsPerThread; ++t) {
-      const int i = tid + t * kThreads;
-      const bool in = i < M;
-#pragma unroll
-      for (int a = 0; a < kBNB; ++a) {
-        float v = 0.f;
-        if (in && a < nbw && i >= a)
-          v = (i == a) ? (float)up[k0 + a] : Af[SLQR_IDX(k0 + i, k0 + a, m)];
-        vr[t][a] = v;
-      }
-      yv[t] = in ? y[k0 + i] : 0.f;
-#pragma unroll
-      for (int a = 0; a < kBNB; ++a) acc[a] = fmaf(vr[t][a], yv[t], acc[a]);
-    }
-    // halving exchange: lanes 2a, 2a + 1 end with the warp's total of acc[a]
-#pragma unroll
-    for (int h = 8, mask = 16; h >= 1; h >>= 1, mask >>= 1) {
-      const bool hi = (lane & mask) != 0;
-#pragma unroll
-      for (int i = 0; i < h; ++i) {
-        const float send = hi ? acc[i] : acc[i + h];
-        const float keep = hi ? acc[i + h] : acc[i];
-        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
-      }
-    }
-    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-    if ((lane & 1) == 0) red[warp * kBNB + (lane >> 1)] = acc[0];
-    __syncthreads();
-    // T^T w (forward) or T w, right-looking in FP32 on warp 0: lane j holds
-    // w_j and its column (forward) or row of G; at step q lane q's value is
-    // final and the lanes still open subtract its contribution
-    if (warp == 0) {
-      const double *Gp = G + (size_t)pnl * kBNB * kBNB;
-      const int j = lane;
-      const bool act = j < nbw;
-      float t = 0.f;
-      if (act) {
-#pragma unroll
-        for (int w8 = 0; w8 < kBWarps; ++w8) t += red[w8 * kBNB + j];
-      }
-      const float tj = act ? (float)tau[k0 + j] : 0.f;
-      float gl[kBNB];
-#pragma unroll
-      for (int q = 0; q < kBNB; ++q)
-        gl[q] = (act && q < nbw) ? (float)(forward ? Gp[q + j * kBNB] : Gp[j + q * kBNB]) : 0.f;
-      float wf = 0.f;
-#pragma unroll
-      for (int s2 = 0; s2 < kBNB; ++s2) {
-        const int q = forward ? s2 : kBNB - 1 - s2;
-        if (q < nbw) {                                 // uniform over the warp
-          const float fin = __shfl_sync(0xffffffffu, t * tj, q);
-          if (forward ? (j > q) : (j < q)) t = fmaf(-gl[q], fin, t);
-          if (j == q) wf = fin;
-        }
-      }
-      __syncwarp();
-      if (act) red[j] = wf;                           // (every lane has read red)
-    }
-    __syncthreads();
-    float wv[kBNB];
-#pragma unroll
-    for (int a = 0; a < kBNB; ++a) wv[a] = (a < nbw) ? red[a] : 0.f;
-#pragma unroll
-    for (int t = 0; t < kBRowsPerThread; ++t) {
-      const int i = tid + t * kThreads;
-      if (i < M) {
-        float v = yv[t];
-#pragma unroll
-        for (int a = 0; a < kBNB; ++a) v = fmaf(-vr[t][a], wv[a], v);
-        y[k0 + i] = v;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Triangular solves with R = triu(Af[0:n, 0:n]) in FP32, in blocks of 32
-// rows.  upper == true: R x = y (back); false: R^T x = y (forward).  y is
-// replaced; a zero diagonal gives x_i = 0 and returns true.  Per block, warp
-// 0 solves the 32 x 32 diagonal block with the block's entries of R in
-// registers (lane l = row; at each step one lane's x is final and is
-// broadcast), then every thread updates the rows not yet solved.
-__device__ bool mixed_trsv(const float *Af, int m, int n, float *y, bool upper) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  bool zero = false;
-  const int nblk = (n + 31) / 32;
-  for (int bi = 0; bi < nblk; ++bi) {
-    const int i0 = upper ? max(0, n - 32 * (bi + 1)) : 32 * bi;
-    const int nb = upper ? (n - 32 * bi) - i0 : min(32, n - i0);
-    if (warp == 0) {
-      const int i = i0 + lane;
-      const bool act = lane < nb;
-      float rv[32];
-#pragma unroll
-      for (int s = 0; s < 32; ++s) {
-        // upper: R[i, i0+s] for s > lane; lower: R^T[i, i0+s] = R[i0+s, i] for s < lane
-        const bool need = act && s < nb && (upper ? s > lane : s < lane);
-        rv[s] = need ? (upper ? Af[SLQR_IDX(i, i0 + s, m)] : Af[SLQR_IDX(i0 + s, i, m)]) : 0.f;
-      }
-      const float d = act ? Af[SLQR_IDX(i, i, m)] : 1.f;
-      float yl = act ? y[i] : 0.f;
-      if (__any_sync(0xffffffffu, act && d == 0.f)) zero = true;
-      float xl = 0.f;
-#pragma unroll
-      for (int s2 = 0; s2 < 32; ++s2) {
-        const int s = upper ? 31 - s2 : s2;
-        if (s < nb) {                                  // uniform over the warp
-          const float xs = __shfl_sync(0xffffffffu, (d != 0.f) ? yl / d : 0.f, s);
-          if (lane == s) xl = xs;
-          if (upper ? lane < s : lane > s) yl = fmaf(-rv[s], xs, yl);
-        }
-      }
-      if (act) y[i] = xl;
-    }
-    __syncthreads();
-    // rows not yet solved: upper -> [0, i0), lower -> [i0 + nb, n)
-    const int r0 = upper ? 0 : i0 + nb, r1 = upper ? i0 : n;
-    for (int l = r0 + tid; l < r1; l += kThreads) {
-      float v = y[l];
-#pragma unroll 8
-      for (int s = 0; s < nb; ++s)
-        v = fmaf(-(upper ? Af[SLQR_IDX(l, i0 + s, m)] : Af[SLQR_IDX(i0 + s, l, m)]), y[i0 + s], v);
-      y[l] = v;
-    }
-    __syncthreads();
-  }
-  return __syncthreads_or(zero);
-}
-
-__device__ double block_max_abs(double v, double *red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = fabs(v);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double r = 0.0;
-  for (int w = 0; w < kBWarps; ++w) r = fmax(r, red[w]);
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kThreads, 2)   // two CTAs per SM
-batch_factor_mixed_kernel(BatchMixedParams bp) {
-  extern __shared__ __align__(16) char smraw[];
-  __shared__ int s_item;
-  __shared__ double red[kBWarps];
-  float *Af = bp.af + (size_t)blockIdx.x * kBMaxRows * kBMaxRows;
-  double *G = bp.gt + (size_t)blockIdx.x * kBGtDoubles;
-  double *tau = G + (size_t)kBMaxPanels * kBNB * kBNB;
-  double *up = tau + kBMaxRows;
-  double *dcol = up + kBMaxRows;       // d_j = 2^-e_j: the FP32 copy is of A D
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(bp.counter, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= bp.count) break;
-    const int p = bp.order[item];
-    const BatchProblem pr = bp.probs[p];
-    const int m = pr.m, n = pr.n;
-    if (n == 0) {
-      if (tid == 0) {
-        if (bp.status) bp.status[p] = SLQR_OK;
-        if (bp.err) bp.err[p] = 0.0;
-      }
-      continue;
-    }
-    // column equilibration by exact powers of two (the largest entry of each
-    // column of A D in [1/2, 1): no FP32 overflow or underflow of products for
-    // any column scale), the FP32 working copy of A D (ld = m), then its FP32
-    // factorization; the refinement solves for y with x = D y
-    for (int j = warp; j < n; j += kBWarps) {
-      double mx = 0.0;
-      for (int i = lane; i < m; i += 32) mx = fmax(mx, fabs(pr.A[SLQR_IDX(i, j, pr.lda)]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) {
-        int ex = 0;
-        if (mx > 0.0 && isfinite(mx)) {
-          frexp(mx, &ex);
-          ex = max(-1000, min(1000, ex));
-        }
-        dcol[j] = ldexp(1.0, -ex);
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < m * n; idx += kThreads) {
-      int c = idx / m, r = idx - c * m;
-      Af[idx] = (float)(pr.A[SLQR_IDX(r, c, pr.lda)] * dcol[c]);
-    }
-    __syncthreads();
-    batch_factor_core<float>(Af, m, m, n, up, nullptr, G, tau, smraw, pr.ntop);
-    __syncthreads();
-    // refinement vectors in shared memory (the panel area is free now)
-    double *x = (double *)smraw;          // n
-    double *r = x + kBMaxRows;            // m
-    double *dx = r + kBMaxRows;           // n (FP64 copy of the correction)
-    float *f = (float *)(dx + kBMaxRows); // m   f, then d = Q^T f, then dr
-    float *g = f + kBMaxRows;             // n   g, then h
-    float *e = g + kBMaxRows;             // m
-    float *w = e + kBMaxRows;             // kBWarps * kBNB (apply_q reductions)
-    // r = 0, x = 0: the first sweep is the plain QR solve (see mixed.cu)
-    for (int i = tid; i < m; i += kThreads) r[i] = 0.0;
-    for (int i = tid; i < n; i += kThreads) x[i] = 0.0;
-    __syncthreads();
-    int status = SLQR_ENOCONV;
-    double err = 1.0, prev = 1e300;
-    for (int it = 0; it < bp.max_it; ++it) {
-      // f = b - r - A x (FP64), one thread per row
-      // (four partial sums: the dependent FP64 chain is a quarter as long)
-      for (int i = tid; i < m; i += kThreads) {
-        double a0 = pr.b[i] - r[i], a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int j = 0;
-        for (; j + 3 < n; j += 4) {
-          a0 = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], a0);
-          a1 = fma(-pr.A[SLQR_IDX(i, j + 1, pr.lda)], x[j + 1], a1);
-          a2 = fma(-pr.A[SLQR_IDX(i, j + 2, pr.lda)], x[j + 2], a2);
-          a3 = fma(-pr.A[SLQR_IDX(i, j + 3, pr.lda)], x[j + 3], a3);
-        }
-        for (; j < n; ++j) a0 = fma(-pr.A[SLQR_IDX(i, j, pr.lda)], x[j], a0);
-        f[i] = (float)((a0 + a1) + (a2 + a3));
-      }
-      // g = -D A^T r (FP64), one warp per column
-      for (int j = warp; j < n; j += kBWarps) {
-        double acc = 0.0;
-        for (int i = lane; i < m; i += 32) acc = fma(pr.A[SLQR_IDX(i, j, pr.lda)], r[i], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) g[j] = (float)(-acc * dcol[j]);
-      }
-      __syncthreads();
-      bool zero = mixed_trsv(Af, m, n, g, false);            // h = R^-T g (in g)
-      mixed_apply_q(Af, m, n, G, tau, up, f, w, true);        // d = Q^T f (in f)
-      for (int i = tid; i < m; i += kThreads) e[i] = (i < n) ? f[i] - g[i] : f[i];
-      __syncthreads();
-      zero |= mixed_trsv(Af, m, n, e, true);                 // dx = R^-1 (d1 - h) (in e[0:n])
-      for (int i = tid; i < n; i += kThreads) dx[i] = (double)e[i] * dcol[i];
-      for (int i = tid; i < m; i += kThreads) f[i] = (i < n) ? g[i] : f[i];   // [h; d2]
-      __syncthreads();
-      mixed_apply_q(Af, m, n, G, tau, up, f, w, false);       // dr = Q [h; d2] (in f)
-      double dmax = 0.0, xmax = 0.0;
-      for (int i = tid; i < n; i += kThreads) {
-        x[i] += dx[i];
-        // a non-finite entry (an FP32 overflow) counts as +inf: never "converged"
-        dmax = fmax(dmax, isfinite(dx[i]) ? fabs(dx[i]) : CUDART_INF);
-        xmax = fmax(xmax, isfinite(x[i]) ? fabs(x[i]) : CUDART_INF);
-      }
-      for (int i = tid; i < m; i += kThreads) r[i] += (double)f[i];
-      dmax = block_max_abs(dmax, red);
-      xmax = block_max_abs(xmax, red);
-      // an exact zero on the diagonal of R is a rank statement whatever the
-      // step looks like, so it is reported before the non-finite guard
-      if (zero) {
-        status = SLQR_ERANK;
-        err = (isfinite(dmax) && isfinite(xmax) && xmax > 0.0) ? dmax / xmax : CUDART_INF;
-        break;
-      }
-      if (!isfinite(dmax) || !isfinite(xmax)) {
-        status = SLQR_ENOCONV;
-        err = CUDART_INF;
-        break;
-      }
-      err = (xmax > 0.0) ? dmax / xmax : 0.0;
-      if (err <= bp.tol) { status = SLQR_OK; break; }
-      if (it >= 2 && err > 0.5 * prev) {        // no longer contracting: FP64 noise level
-        status = (err <= kBStallOk) ? SLQR_OK : SLQR_ENOCONV;
-        break;
-      }
-      prev = err;
-    }
-    for (int i = tid; i < n; i += kThreads) pr.b[i] = x[i];
-    if (tid == 0) {
-      if (bp.status) bp.status[p] = status;
-      if (bp.err) bp.err[p] = err;
-    }
-    __syncthreads();
-  }
-}
-
-constexpr size_t kBMixedSmemBytes = BatchSmem<float>::kBytes > 6 * kBMaxRows * sizeof(double)
-                                        ? BatchSmem<float>::kBytes
-                                        : 6 * kBMaxRows * sizeof(double);
+static const BatchSetting kBSettings[] = {{8, 32}, {8, 64}, {16, 16}, {16, 32}, {16, 64},
+                                          {32, 16}, {32, 32}, {32, 64}};
 
 slqr_status init_batch_attrs(slqr_ctx *ctx) {
-  cudaError_t e = cudaFuncSetAttribute(batch_factor_fp64_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kBSmemBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_factor_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kBMixedSmemBytes);
+  cudaError_t e = cudaSuccess;
+  for (const BatchSetting &s : kBSettings) {
+    BatchKernels k = batch_kernels(s.nb, s.tc);
+    if (!k.fp64 || !k.mixed) return fail(ctx, SLQR_ECUDA, "batch kernels (%d, %d) missing", s.nb, s.tc);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k.fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fp64);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k.mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)k.smem_mixed);
+  }
   if (e != cudaSuccess)
     return fail(ctx, SLQR_ECUDA, "cudaFuncSetAttribute(batch): %s", cudaGetErrorString(e));
   return SLQR_OK;
@@ -819,19 +97,27 @@ extern "C" int slqr_batch_max_rows(void) { return kBMaxRows; }
 
 namespace slqr {
 
-// The launch behind slqr_batch_factor and slqr_batch_factor_stacked (ntop:
-// NULL, or per problem the rows of its upper-triangular top block, 0 for a
-// dense problem).  The context mutex is held by the caller.
+// One persistent launch of a batch: the problems of the classes that share
+// one setting, at [begin, begin + count) of the order array.
+struct BatchGroup {
+  BatchSetting set;
+  int begin = 0, count = 0, grid = 0;
+  double cost = 0.0;
+};
+
 // A batch as the kernels see it: the problem table (in the order given), the
-// longest-first order, the grid and the algorithmic flops.
+// order (per group, longest first), the groups and the algorithmic flops.
 struct BatchSetup {
   std::vector<BatchProblem> probs;
   std::vector<int> order;
+  std::vector<BatchGroup> groups;
   bool mixed = false;
-  int grid = 0;
+  int max_grid = 0;
   double flops = 0.0;
   size_t table_bytes = 0, head = 0, af_bytes = 0, gt_bytes = 0;   // device layout
 };
+
+constexpr int kBMaxGroups = 64;   // work counters in the first 256 bytes of the layout
 
 // Validate the arguments and build the setup (no device work).
 static slqr_status batch_build(slqr_ctx *ctx, int count, const int *m, const int *n,
@@ -860,46 +146,84 @@ static slqr_status batch_build(slqr_ctx *ctx, int count, const int *m, const int
                       : 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0) +
               (b && b[i] ? 6.0 * m[i] * (double)n[i] : 0.0);
   }
-  bs.order.resize(count);
-  std::iota(bs.order.begin(), bs.order.end(), 0);
-  std::stable_sort(bs.order.begin(), bs.order.end(),
-                   [&](int a, int c) { return cost[a] > cost[c]; });
   bs.flops = 0.0;
   for (int i = 0; i < count; ++i) bs.flops += cost[i];
   bs.mixed = (prec == SLQR_FP32);
-  int per_sm = 0;
-  cudaError_t e;
-  if (bs.mixed)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_factor_mixed_kernel, kThreads,
-                                                      kBMixedSmemBytes);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_factor_fp64_kernel, kThreads,
-                                                      kBSmemBytes);
-  if (e != cudaSuccess || per_sm < 1)
-    return fail(ctx, SLQR_ECUDA, "batch occupancy: %s", cudaGetErrorString(e));
-  bs.grid = std::min(count, per_sm * ctx->num_sms);
-  // device layout: [counter 256 B][problem table][order][per-CTA scratch (mixed)]
+  // group the problems by the setting of their size class
+  std::vector<BatchSetting> cls_set(kBClasses);
+  for (int c = 0; c < kBClasses; ++c) cls_set[c] = batch_setting(prec, c);
+  std::vector<int> gidx(kBClasses, -1);            // class -> group
+  for (int c = 0; c < kBClasses; ++c) {
+    for (int c2 = 0; c2 < c; ++c2)
+      if (cls_set[c2] == cls_set[c]) { gidx[c] = gidx[c2]; break; }
+    if (gidx[c] < 0) {
+      gidx[c] = (int)bs.groups.size();
+      BatchGroup g;
+      g.set = cls_set[c];
+      bs.groups.push_back(g);
+    }
+  }
+  std::vector<std::vector<int>> members(bs.groups.size());
+  for (int i = 0; i < count; ++i) {
+    const int g = gidx[batch_class(m[i])];
+    members[g].push_back(i);
+    bs.groups[g].cost += cost[i];
+  }
+  // costliest group first; longest problem first inside each group
+  std::vector<int> gorder(bs.groups.size());
+  std::iota(gorder.begin(), gorder.end(), 0);
+  std::stable_sort(gorder.begin(), gorder.end(),
+                   [&](int a, int c) { return bs.groups[a].cost > bs.groups[c].cost; });
+  std::vector<BatchGroup> groups;
+  bs.order.clear();
+  for (int g : gorder) {
+    if (members[g].empty()) continue;
+    std::stable_sort(members[g].begin(), members[g].end(),
+                     [&](int a, int c) { return cost[a] > cost[c]; });
+    BatchGroup grp = bs.groups[g];
+    grp.begin = (int)bs.order.size();
+    grp.count = (int)members[g].size();
+    bs.order.insert(bs.order.end(), members[g].begin(), members[g].end());
+    BatchKernels k = batch_kernels(grp.set.nb, grp.set.tc);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, bs.mixed ? k.mixed : k.fp64, kThreads, bs.mixed ? k.smem_mixed : k.smem_fp64);
+    if (e != cudaSuccess || per_sm < 1)
+      return fail(ctx, SLQR_ECUDA, "batch occupancy: %s", cudaGetErrorString(e));
+    grp.grid = std::min(grp.count, per_sm * ctx->num_sms);
+    bs.max_grid = std::max(bs.max_grid, grp.grid);
+    groups.push_back(grp);
+  }
+  bs.groups = groups;
+  // device layout: [work counters 256 B][problem table][order][per-CTA scratch (mixed)]
   bs.table_bytes = align_up(sizeof(BatchProblem) * count, 256);
   bs.head = align_up(256 + bs.table_bytes + sizeof(int) * count, 256);
-  bs.af_bytes = bs.mixed ? (size_t)bs.grid * kBMaxRows * kBMaxRows * sizeof(float) : 0;
-  bs.gt_bytes = bs.mixed ? (size_t)bs.grid * kBGtDoubles * sizeof(double) : 0;
+  bs.af_bytes = bs.mixed ? (size_t)bs.max_grid * kBMaxRows * kBMaxRows * sizeof(float) : 0;
+  bs.gt_bytes = bs.mixed ? (size_t)bs.max_grid * kBGtDoubles * sizeof(double) : 0;
   return SLQR_OK;
 }
 
-// The kernel launch of a batch whose table and order are already at `base`.
-static void batch_kernel_launch(const BatchSetup &bs, char *base, int count, int *status,
-                                double *err, cudaStream_t s) {
-  unsigned *counter = (unsigned *)base;
+// The kernel launches of a batch whose table and order are already at `base`
+// (one per group, in order, each with its own work counter).
+static void batch_kernel_launch(const BatchSetup &bs, char *base, int *status, double *err,
+                                cudaStream_t s) {
+  unsigned *counters = (unsigned *)base;
   BatchProblem *d_probs = (BatchProblem *)(base + 256);
   int *d_order = (int *)(base + 256 + bs.table_bytes);
-  if (!bs.mixed) {
-    BatchParams bp{d_probs, d_order, count, counter, status};
-    batch_factor_fp64_kernel<<<bs.grid, kThreads, kBSmemBytes, s>>>(bp);
-  } else {
-    BatchMixedParams mp{d_probs, d_order, count, counter, status, err,
-                        (float *)(base + bs.head), (double *)(base + bs.head + bs.af_bytes),
-                        kBMaxRefine, kBRefineTol};
-    batch_factor_mixed_kernel<<<bs.grid, kThreads, kBMixedSmemBytes, s>>>(mp);
+  for (size_t gi = 0; gi < bs.groups.size(); ++gi) {
+    const BatchGroup &g = bs.groups[gi];
+    BatchKernels k = batch_kernels(g.set.nb, g.set.tc);
+    if (!bs.mixed) {
+      BatchParams bp{d_probs, d_order + g.begin, g.count, counters + gi, status};
+      void *args[] = {&bp};
+      cudaLaunchKernel(k.fp64, dim3(g.grid), dim3(kThreads), args, k.smem_fp64, s);
+    } else {
+      BatchMixedParams mp{d_probs, d_order + g.begin, g.count, counters + gi, status, err,
+                          (float *)(base + bs.head), (double *)(base + bs.head + bs.af_bytes),
+                          kBMaxRefine, kBRefineTol};
+      void *args[] = {&mp};
+      cudaLaunchKernel(k.mixed, dim3(g.grid), dim3(kThreads), args, k.smem_mixed, s);
+    }
   }
 }
 
@@ -930,8 +254,9 @@ slqr_status batch_launch(slqr_ctx *ctx, int count, const int *m, const int *n, c
                         cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
   int slot = prof_begin(ctx, s);
-  batch_kernel_launch(bs, base, count, status, err, s);
+  batch_kernel_launch(bs, base, status, err, s);
   prof_end(ctx, s, slot, kBatch, bs.flops);
+  ctx->launch_count += (long long)bs.groups.size() - 1;
   return check_launch(ctx, "batch_factor");
 }
 
@@ -942,6 +267,19 @@ slqr_status batch_factor_locked(slqr_ctx *ctx, int count, const int *m, const in
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   return batch_launch(ctx, count, m, n, ntop, A, lda, up, b, prec, status, err, stream);
+}
+
+// Generic scratch entries in (-1, 1) from a hash of the index (the timing does
+// not depend on the values, only on their being generic).
+__global__ void batch_tune_fill_kernel(double *A, size_t count, unsigned long long salt) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long h = (i + 1 + salt) * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 27;
+    A[i] = (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
 }
 
 }  // namespace slqr
@@ -974,6 +312,202 @@ extern "C" slqr_status slqr_batch_factor_stacked(slqr_ctx *ctx, int count, const
     m[i] = n[i] + m_eq[i];
   }
   return batch_launch(ctx, count, m.data(), n, n, A, lda, up, b, prec, status, err, stream);
+}
+
+extern "C" int slqr_batch_classes(void) { return kBClasses; }
+
+extern "C" int slqr_batch_class_rows(int m_class) {
+  return (m_class >= 0 && m_class < kBClasses) ? kBClassHi[m_class] : 0;
+}
+
+extern "C" slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_width,
+                                             int tile_cols) {
+  if (prec != SLQR_FP64 && prec != SLQR_FP32) return SLQR_EINVAL;
+  if (m_class < -1 || m_class >= kBClasses) return SLQR_EINVAL;
+  BatchSetting s;
+  if (panel_width != 0 || tile_cols != 0) {
+    bool ok = false;
+    for (const BatchSetting &v : kBSettings) ok |= (v.nb == panel_width && v.tc == tile_cols);
+    if (!ok) return SLQR_EINVAL;
+    s.nb = panel_width;
+    s.tc = tile_cols;
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (int c = 0; c < kBClasses; ++c)
+    if (m_class < 0 || c == m_class) g_batch_setting[prec == SLQR_FP32 ? 1 : 0][c] = s;
+  return SLQR_OK;
+}
+
+extern "C" slqr_status slqr_batch_get_tuning(int prec, int m_class, int *panel_width,
+                                             int *tile_cols) {
+  if ((prec != SLQR_FP64 && prec != SLQR_FP32) || m_class < 0 || m_class >= kBClasses)
+    return SLQR_EINVAL;
+  BatchSetting s = batch_setting(prec, m_class);
+  if (panel_width) *panel_width = s.nb;
+  if (tile_cols) *tile_cols = s.tc;
+  return SLQR_OK;
+}
+
+extern "C" slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, const int *m,
+                                           const int *n, int sample, int *panel_width,
+                                           int *tile_cols, double *ms_out) {
+  NvtxRange nvtx_range("slqr_batch_autotune");
+  if (!ctx) return SLQR_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (prec != SLQR_FP64 && prec != SLQR_FP32)
+    return fail(ctx, SLQR_EINVAL, "precision %d not available for batches", prec);
+  if (count < 0 || (count > 0 && (!m || !n)))
+    return fail(ctx, SLQR_EINVAL, "autotune: bad shape list (count=%d)", count);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  // the scratch batch: `sample` problems, every (count / sample)-th of the
+  // caller's shapes, or drawn from the default law (m ~ U{16..512},
+  // n ~ U{ceil(m/4)..m}, the 20,000-problem workload) with a fixed LCG
+  const int ns_ = sample > 0 ? sample : (count > 0 ? std::min(count, 3000) : 3000);
+  std::vector<int> mv, nv;
+  if (count > 0) {
+    for (int i = 0; i < ns_ && i < count; ++i) {
+      const int k = (int)((long long)i * count / std::min(ns_, count));
+      if (n[k] < 0 || m[k] < n[k] || m[k] > kBMaxRows)
+        return fail(ctx, SLQR_EINVAL, "autotune: problem %d: need %d >= m >= n >= 0", k, kBMaxRows);
+      if (n[k] == 0) continue;
+      mv.push_back(m[k]);
+      nv.push_back(n[k]);
+    }
+  } else {
+    unsigned long long r = 0x2545F4914F6CDD1Dull;
+    auto next = [&](int a, int b) {
+      r = r * 6364136223846793005ull + 1442695040888963407ull;
+      return a + (int)((r >> 33) % (unsigned long long)(b - a + 1));
+    };
+    for (int i = 0; i < ns_; ++i) {
+      mv.push_back(next(16, kBMaxRows));
+      nv.push_back(next((mv.back() + 3) / 4, mv.back()));
+    }
+  }
+  const int cnt = (int)mv.size();
+  if (cnt == 0) return fail(ctx, SLQR_EINVAL, "autotune: no problem with n > 0");
+  std::vector<int> ldv(mv);
+  size_t a_total = 0, b_total = 0, n_total = 0;
+  std::vector<double> cls_cost(kBClasses, 0.0);
+  for (int i = 0; i < cnt; ++i) {
+    a_total += (size_t)mv[i] * nv[i];
+    b_total += mv[i];
+    n_total += nv[i];
+    cls_cost[batch_class(mv[i])] += 2.0 * mv[i] * (double)nv[i] * nv[i];
+  }
+  const int pi = prec == SLQR_FP32 ? 1 : 0;
+  BatchSetting cur[kBClasses];
+  {
+    std::lock_guard<std::mutex> lk2(g_batch_mu);
+    for (int c = 0; c < kBClasses; ++c) cur[c] = g_batch_setting[pi][c];
+  }
+  const BatchSetting saved[kBClasses] = {cur[0], cur[1], cur[2], cur[3]};
+  auto apply = [&](const BatchSetting *set) {
+    std::lock_guard<std::mutex> lk2(g_batch_mu);
+    for (int c = 0; c < kBClasses; ++c) g_batch_setting[pi][c] = set[c];
+  };
+  double *A0 = nullptr, *Aw = nullptr, *B0 = nullptr, *Bw = nullptr, *UP = nullptr, *derr = nullptr;
+  int *dstat = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMalloc(&A0, a_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Aw, a_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&B0, b_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Bw, b_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&UP, n_total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dstat, cnt * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&derr, cnt * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<double *> Ap(cnt), Bp(cnt), Up(cnt);
+  {
+    size_t ao = 0, bo = 0, no = 0;
+    for (int i = 0; i < cnt; ++i) {
+      Ap[i] = Aw + ao;
+      Bp[i] = Bw + bo;
+      Up[i] = UP + no;
+      ao += (size_t)mv[i] * nv[i];
+      bo += mv[i];
+      no += nv[i];
+    }
+  }
+  if (e == cudaSuccess) {
+    batch_tune_fill_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A0, a_total, 0);
+    batch_tune_fill_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(B0, b_total, a_total);
+    e = cudaGetLastError();
+  }
+  slqr_status st = SLQR_OK;
+  // the sample batch under the settings now in the table: best of two runs
+  // after a warm-up
+  auto time_it = [&]() -> double {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && st == SLQR_OK && e == cudaSuccess; ++rep) {
+      cudaMemcpyAsync(Aw, A0, a_total * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(Bw, B0, b_total * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaEventRecord(e0, s);
+      st = batch_launch(ctx, cnt, mv.data(), nv.data(), nullptr, Ap.data(), ldv.data(), Up.data(),
+                        Bp.data(), prec, dstat, derr, s);
+      cudaEventRecord(e1, s);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    return tmin;
+  };
+  const double t_before = time_it();
+  double t_best = t_before;
+  // greedy coordinate search: the classes costliest first, each trying every
+  // setting with the others held, a change kept only when the whole sample
+  // batch gets faster (so a split into several launches must pay for itself)
+  std::vector<int> corder(kBClasses);
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(),
+                   [&](int a, int c) { return cls_cost[a] > cls_cost[c]; });
+  for (int c : corder) {
+    if (cls_cost[c] == 0.0) continue;
+    for (const BatchSetting &cand : kBSettings) {
+      if (st != SLQR_OK || e != cudaSuccess) break;
+      if (cand == cur[c]) continue;
+      BatchSetting trial[kBClasses] = {cur[0], cur[1], cur[2], cur[3]};
+      trial[c] = cand;
+      apply(trial);
+      const double t = time_it();
+      if (t < 0.99 * t_best) {              // a clear gain, not timing noise
+        t_best = t;
+        cur[c] = cand;
+      }
+    }
+    apply(cur);
+  }
+  cudaFree(A0);
+  cudaFree(Aw);
+  cudaFree(B0);
+  cudaFree(Bw);
+  cudaFree(UP);
+  cudaFree(dstat);
+  cudaFree(derr);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess || st != SLQR_OK) {
+    apply(saved);
+    if (st != SLQR_OK) return st;
+    cudaGetLastError();
+    return fail(ctx, SLQR_ENOMEM, "batch autotune: %s", cudaGetErrorString(e));
+  }
+  apply(cur);
+  for (int c = 0; c < kBClasses; ++c) {
+    if (panel_width) panel_width[c] = cur[c].nb;
+    if (tile_cols) tile_cols[c] = cur[c].tc;
+  }
+  if (ms_out) {
+    ms_out[0] = t_before;
+    ms_out[1] = t_best;
+  }
+  return SLQR_OK;
 }
 
 // --------------------------------------------------------------------------
@@ -1037,7 +571,7 @@ extern "C" slqr_status slqr_batch_plan_create(slqr_ctx *ctx, int count, const in
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(plan->dev, 0, 256, cs);
-    batch_kernel_launch(plan->bs, plan->dev, count, status, err, cs);
+    batch_kernel_launch(plan->bs, plan->dev, status, err, cs);
     e = cudaStreamEndCapture(cs, &plan->graph);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);

@@ -177,6 +177,8 @@ __global__ void init_kernel(double *__restrict__ r, int m, double *__restrict__ 
 // updates its own rows.  One barrier per panel instead of three launches.
 // --------------------------------------------------------------------------
 constexpr int kQvRows = 128;     // rows of f per CTA (more when m exceeds 128 per SM)
+constexpr int kQvRows64 = 64;    // the same for the FP64 application (GMRES-IR): twice the
+                                 // CTAs, half the FP64 arithmetic per CTA and panel
 
 // T of panel p (VT = float or double, ld nb + 1): column j solves U y = e_j by
 // back substitution with U = striu(G) + diag(1/tau), i.e. y_j = tau_j and
@@ -395,6 +397,9 @@ static size_t qvec_smem_bytes(int nb, int R) {
 template <typename VT>
 struct TrsvParams {
   const float *R;        // FP32 factorization; the solve runs in VT arithmetic
+  const VT *Rinv;        // NULL, or the inverses of R's 64 x 64 diagonal blocks
+                         // (diag_inv_kernel): each block is then one product
+  const int *zblk;       // with Rinv: per block, 1 when it has a zero diagonal
   VT *y;
   int *zero_flag;
   unsigned *bar;
@@ -444,11 +449,25 @@ trsv_coop_kernel(TrsvParams<VT> p) {
       Tu[c][r] = v;
     }
   };
-  if (one) load_diag(cta);
+  if (one && !p.Rinv) load_diag(cta);
   for (int step = 0; step < p.nblk; ++step) {
     const int b = UPPER ? p.nblk - 1 - step : step;
     const int b0 = b * 64, rows = min(64, p.n - b0);
-    if (b % p.P == cta) {
+    if (b % p.P == cta && p.Rinv) {
+      // x_b = Rinv_b c_b (UPPER) or Rinv_b^T c_b: thread (r, q) sums 16 terms
+      // of row r, the four partials of a row are added in a fixed order
+      if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : (VT)0;
+      __syncthreads();
+      const VT *Ri = p.Rinv + (size_t)b * 64 * 64;
+      const int r = tid & 63, q = tid >> 6;
+      VT acc = 0;
+      for (int c = q * 16; c < q * 16 + 16; ++c)
+        acc = fma_t(UPPER ? Ri[r + 64 * c] : Ri[c + 64 * r], xs[c], acc);
+      red[q][r] = acc;
+      __syncthreads();
+      if (tid < rows) p.y[b0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+      if (tid == 0 && p.zblk[b]) atomicExch(p.zero_flag, 1);
+    } else if (b % p.P == cta) {
       if (!one) load_diag(b);
       if (tid < 64) xs[tid] = (tid < rows) ? p.y[b0 + tid] : (VT)0;
       __syncthreads();
@@ -707,11 +726,44 @@ diag_range_kernel(const float *__restrict__ R, int lda, int n, double *__restric
   }
 }
 
+// Inverse of the upper-triangular 64 x 64 diagonal block b of the FP32 R, in
+// FP64 (one CTA per block, thread j builds column j right-looking: at step k
+// its y_k = acc_k / R_kk is final and is subtracted from the rows above).  An
+// exact zero R_kk gives y_k = 0, the substitution's x_k = 0, and marks the
+// block in zblk.  Rinv: [block][col][row], ld 64.
+__global__ void __launch_bounds__(64)
+diag_inv_kernel(const float *__restrict__ R, int lda, int n, double *__restrict__ Rinv,
+                int *__restrict__ zblk) {
+  __shared__ double Rs[64][65];
+  const int b = blockIdx.x, j = threadIdx.x, b0 = b * 64, rows = min(64, n - b0);
+  for (int c = 0; c < 64; ++c)
+    Rs[j][c] = (j < rows && c < rows && j <= c) ? (double)R[SLQR_IDX(b0 + j, b0 + c, lda)] : 0.0;
+  __syncthreads();
+  double acc[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) acc[i] = (i == j) ? 1.0 : 0.0;
+  bool zero = false;
+#pragma unroll
+  for (int k = 63; k >= 0; --k) {
+    const double d = Rs[k][k];
+    const double yk = (k < rows && d != 0.0) ? acc[k] / d : 0.0;
+    zero |= (k < rows && d == 0.0);
+    acc[k] = yk;
+#pragma unroll
+    for (int i = 0; i < k; ++i) acc[i] = fma(-Rs[i][k], yk, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 64; ++i) Rinv[(size_t)b * 4096 + (size_t)j * 64 + i] = acc[i];
+  if (j == 0) zblk[b] = zero ? 1 : 0;
+}
+
 template <bool UPPER, typename VT>
 static slqr_status trsv_vec(slqr_ctx *ctx, const float *R, int lda, int n, VT *y, int *zero_flag,
-                            unsigned *bar, unsigned &bar_base, cudaStream_t s) {
+                            unsigned *bar, unsigned &bar_base, cudaStream_t s,
+                            const VT *Rinv = nullptr, const int *zblk = nullptr) {
   TrsvParams<VT> tp;
-  tp.R = R; tp.y = y; tp.zero_flag = zero_flag; tp.bar = bar; tp.status = ctx->d_status;
+  tp.R = R; tp.Rinv = Rinv; tp.zblk = zblk;
+  tp.y = y; tp.zero_flag = zero_flag; tp.bar = bar; tp.status = ctx->d_status;
   tp.lda = lda; tp.n = n; tp.nblk = (n + 63) / 64;
   tp.P = std::min(tp.nblk, ctx->num_sms);
   tp.bar_base = bar_base;
@@ -740,9 +792,12 @@ struct MixedSolve {
   double *Tm64, *qpart64;
   unsigned *qbar;
   unsigned qbar_base = 0;
-  int qv_R, qv_P;
+  int qv_R, qv_P;                      // FP32 Q application: rows per CTA, CTAs
+  int qv_R64, qv_P64;                  // FP64 Q application
   // GMRES-IR: Krylov basis (restart + 1 vectors of m + n) and small buffers
   double *Vk = nullptr, *hdev = nullptr, *ydev = nullptr, *drange = nullptr;
+  double *Rinv = nullptr;              // FP64 inverses of R's diagonal blocks
+  int *zblk = nullptr;
   int restart = 0;
 };
 
@@ -752,17 +807,19 @@ static slqr_status apply_q_vec(MixedSolve &ms, VT *f, const VT *Tm, VT *qpart, b
   QvecParams<VT> qp;
   qp.A = ms.A32; qp.up = ms.up; qp.Tm = Tm; qp.f = f; qp.part = qpart; qp.bar = ms.qbar;
   qp.status = ms.ctx->d_status; qp.lda = ms.lda32; qp.m = ms.m; qp.K = ms.K; qp.nb = ms.nb;
-  qp.np = ms.np; qp.trans = trans ? 1 : 0; qp.R = ms.qv_R; qp.P = ms.qv_P;
+  const bool dbl = sizeof(VT) == sizeof(double);
+  const int R = dbl ? ms.qv_R64 : ms.qv_R, P = dbl ? ms.qv_P64 : ms.qv_P;
+  qp.np = ms.np; qp.trans = trans ? 1 : 0; qp.R = R; qp.P = P;
   qp.bar_base = ms.qbar_base;
   qp.spin = ms.ctx->spin_limit;
   void *args[] = {&qp};
-  cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel<VT>, dim3(ms.qv_P),
+  cudaError_t le = cudaLaunchCooperativeKernel((const void *)qvec_kernel<VT>, dim3(P),
                                                dim3(kThreads), args,
-                                               qvec_smem_bytes<VT>(ms.nb, ms.qv_R), ms.s);
+                                               qvec_smem_bytes<VT>(ms.nb, R), ms.s);
   ++ms.ctx->launch_count;
   if (le != cudaSuccess)
     return fail(ms.ctx, SLQR_ECUDA, "Q application: %s", cudaGetErrorString(le));
-  ms.qbar_base += (unsigned)ms.np * (unsigned)ms.qv_P;
+  ms.qbar_base += (unsigned)ms.np * (unsigned)P;
   return SLQR_OK;
 }
 
@@ -851,14 +908,15 @@ static slqr_status precondition64(MixedSolve &ms, double *w) {
   slqr_ctx *ctx = ms.ctx;
   double *ws = w, *wx = w + ms.m;
   slqr_status st = trsv_vec<false>(ctx, ms.A32, ms.lda32, ms.n, wx, ms.zero_flag, ms.qbar,
-                                   ms.qbar_base, ms.s);                 // h = R^-T g
+                                   ms.qbar_base, ms.s, (const double *)ms.Rinv,
+                                   ms.zblk);                            // h = R^-T g
   if (st != SLQR_OK) return st;
   st = apply_q_vec(ms, ws, ms.Tm64, ms.qpart64, true);                  // d = Q^T f
   if (st != SLQR_OK) return st;
   prec_mid_kernel<<<(ms.n + 255) / 256, 256, 0, ms.s>>>(ws, wx, ms.n);
   ++ctx->launch_count;
   st = trsv_vec<true>(ctx, ms.A32, ms.lda32, ms.n, wx, ms.zero_flag, ms.qbar, ms.qbar_base,
-                      ms.s);                                            // dx = R^-1 (d1 - h)
+                      ms.s, (const double *)ms.Rinv, ms.zblk);          // dx = R^-1 (d1 - h)
   if (st != SLQR_OK) return st;
   return apply_q_vec(ms, ws, ms.Tm64, ms.qpart64, false);               // Q [h; d2]
 }
@@ -918,7 +976,8 @@ static slqr_status gmres_ir(MixedSolve &ms, double tol, int max_iters, double in
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int k = 0;
-    bool inner_ok = false;
+    bool inner_ok = false, hopeless = false;
+    const int iters_left = max_iters - res->iters;
     for (int j = 0; j < k_max && res->iters < max_iters; ++j) {
       double *vj = ms.Vk + (size_t)j * N, *w = ms.Vk + (size_t)(j + 1) * N;
       aug_matvec(ms, vj, w);                                   // w = Aaug v_j
@@ -958,9 +1017,18 @@ static slqr_status gmres_ir(MixedSolve &ms, double tol, int max_iters, double in
       const double rel = std::fabs(gv[j + 1]) / beta;
       if (rel <= inner_tol) { inner_ok = true; break; }
       if (hnext <= 1e-300 * beta) { inner_ok = true; break; }   // invariant subspace: exact
+      // give up early when the residual's rate so far predicts far more
+      // iterations than the budget has left (the caller's fallback, if any,
+      // then starts at once): after 32 iterations, a geometric rate
+      // rel^(1/(j+1)) would need (j+1) log(inner_tol) / log(rel) iterations
+      if (j + 1 >= 32) {
+        const double need = (rel < 1.0) ? (j + 1) * std::log(inner_tol) / std::log(rel) : HUGE_VAL;
+        if (need > 2.0 * iters_left) { hopeless = true; break; }
+      }
       vec_scale_kernel<<<gblocks, 256, 0, s>>>(w, N, 1.0 / hnext);
       ++ctx->launch_count;
     }
+    if (hopeless) { res->err = HUGE_VAL; return SLQR_ENOCONV; }
     // y = H[0:k, 0:k]^-1 g[0:k] (upper triangular after the rotations)
     for (int q = k - 1; q >= 0; --q) {
       double t = gv[q];
@@ -1074,6 +1142,8 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
   // (a multiple of 64 rows: every slice starts 16-byte aligned for the vector loads)
   ms.qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
   ms.qv_P = (m + ms.qv_R - 1) / ms.qv_R;
+  ms.qv_R64 = std::max(kQvRows64, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
+  ms.qv_P64 = (m + ms.qv_R64 - 1) / ms.qv_R64;
   const size_t t_elems = (size_t)std::max(np, 1) * nb * (nb + 1);
   const size_t o_tm = take(t_elems * sizeof(float));
   const size_t o_qpart = take((size_t)2 * ms.qv_P * nb * sizeof(float));
@@ -1087,10 +1157,13 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
   int restart = o.gmres_restart > 0 ? o.gmres_restart : std::min(gm_iters, 200);
   restart = std::max(1, std::min(restart, kMaxKrylov));
   const size_t o_tm64 = use_gmres ? take(t_elems * sizeof(double)) : 0;
-  const size_t o_qpart64 = use_gmres ? take((size_t)2 * ms.qv_P * nb * sizeof(double)) : 0;
+  const size_t o_qpart64 = use_gmres ? take((size_t)2 * ms.qv_P64 * nb * sizeof(double)) : 0;
   const size_t o_vk = use_gmres ? take((size_t)(restart + 1) * N * sizeof(double)) : 0;
   const size_t o_h = use_gmres ? take((size_t)2 * (restart + 2) * sizeof(double)) : 0;
   const size_t o_y = use_gmres ? take((size_t)restart * sizeof(double)) : 0;
+  const int nblk64 = (n + 63) / 64;
+  const size_t o_rinv = use_gmres ? take((size_t)nblk64 * 4096 * sizeof(double)) : 0;
+  const size_t o_zblk = use_gmres ? take((size_t)nblk64 * sizeof(int)) : 0;
   const size_t o_dr = take(2 * sizeof(double));
   const size_t o_cs = take((size_t)n * sizeof(double));
   slqr_status st = ensure_workspace2(ctx, off);
@@ -1117,6 +1190,8 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     ms.Vk = (double *)(base + o_vk);
     ms.hdev = (double *)(base + o_h);
     ms.ydev = (double *)(base + o_y);
+    ms.Rinv = (double *)(base + o_rinv);
+    ms.zblk = (int *)(base + o_zblk);
     ms.restart = restart;
   }
   cudaError_t e = cudaFuncSetAttribute(qvec_kernel<float>,
@@ -1124,7 +1199,7 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
                                        (int)qvec_smem_bytes<float>(nb, ms.qv_R));
   if (e == cudaSuccess && use_gmres)
     e = cudaFuncSetAttribute(qvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)qvec_smem_bytes<double>(nb, ms.qv_R));
+                             (int)qvec_smem_bytes<double>(nb, ms.qv_R64));
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
 
   // the FP32 factorization, of A D
@@ -1171,6 +1246,10 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "GMRES-IR: %s", cudaGetErrorString(e));
     const double kappa_est = (dr[1] > 0.0) ? dr[0] / dr[1] : HUGE_VAL;
+    // the FP64 inverses of R's diagonal blocks, once for all the triangular
+    // solves of the preconditioner
+    diag_inv_kernel<<<nblk64, 64, 0, s>>>(ms.A32, ms.lda32, n, ms.Rinv, ms.zblk);
+    ++ctx->launch_count;
     info->kappa_est = kappa_est;
     const double noise = std::max(kStallOk, 100.0 * kappa_est * std::ldexp(1.0, -53));
     if (use_bjorck) {

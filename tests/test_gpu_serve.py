@@ -3,7 +3,7 @@ the oracle, resident factorizations under handles, HBM-budget admission, and
 the same result for a request alone and in a mix of concurrent requests.
 
 Tolerances as in tests/test_gpu_parity.py (LS forward-error bound
-1e3 * (kappa + kappa^2 ||r|| / (||A|| ||x||)) * eps against the FP64 oracle);
+64 (kappa + kappa^2 ||r|| / (||A|| ||x||)) u, u = 2^-53, against the FP64 oracle);
 refined FP32 results: 1e-10 relative to the oracle.
 """
 import numpy as np
@@ -29,7 +29,7 @@ def ls_bound(A, b):
     x, F, up, qtb, st = oracle.lstsq(A, b)
     kappa = np.linalg.cond(A)
     r = oracle.residual_norm(qtb, A.shape[1])
-    bound = 1e3 * (kappa + kappa ** 2 * r / (np.linalg.norm(A, 2) * np.linalg.norm(x))) * EPS
+    bound = 64.0 * (kappa + kappa ** 2 * r / (np.linalg.norm(A, 2) * np.linalg.norm(x))) * 2.0 ** -53
     return x, r, bound
 
 
