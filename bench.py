@@ -772,7 +772,8 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
                "autotune_s": tune_s,
                "autotune_sample_ms_before_after": list(tms),
                "tuned_settings": [{"m_max": abi.slqr_batch_class_rows(c), "panel_width": nb,
-                                   "tile_cols": tc} for c, (nb, tc) in enumerate(choice)]}
+                                   "tile_cols": tc, "resident": bool(rs)}
+                                  for c, (nb, tc, rs) in enumerate(choice)]}
         if prec == abi.SLQR_FP32:
             ev = err.cpu().numpy()
             rec["refine_err_max"] = float(ev[stv == 0].max()) if np.any(stv == 0) else None
@@ -848,6 +849,27 @@ def run_batch_workload(ctx, device, stream, barrier, count=BATCH_COUNT, reps=2, 
             abi.slqr_batch_plan_destroy(splan)
         small[mode] = {"median_ms": float(np.median(lat)), "min_ms": float(np.min(lat))}
     out["small_batch_256_call_latency"] = small
+    # the same small batch after the autotuner has seen its shapes (all in the
+    # class m <= 64, where the shared-memory-resident kernel is a candidate)
+    stt, choice, tms = abi.slqr_batch_autotune(ctx.ctx, abi.SLQR_FP64, sargs[0], sargs[1])
+    abi.check(ctx.ctx, stt, "slqr_batch_autotune (small batch)")
+    lat = []
+    for rep in range(21):
+        SA.copy_(SA0)
+        Sb.copy_(Sb0)
+        torch.cuda.synchronize()
+        t0 = _time.perf_counter()
+        abi.check(ctx.ctx, abi.slqr_batch_factor(ctx.ctx, *sargs, abi.SLQR_FP64, sstat.data_ptr(),
+                                                 None, stream.cuda_stream), "small batch")
+        torch.cuda.synchronize()
+        if rep:
+            lat.append((_time.perf_counter() - t0) * 1e3)
+    nb, tc, rs = choice[0]
+    out["small_batch_256_tuned"] = {"panel_width": nb, "tile_cols": tc, "resident": bool(rs),
+                                    "median_ms": float(np.median(lat)),
+                                    "tuner_sample_ms_before_after": list(tms),
+                                    "ok": int(np.sum(sstat.cpu().numpy() == 0))}
+    abi.slqr_batch_set_tuning(abi.SLQR_FP64, -1, 0, 0)
     del SA, Sb, SA0, Sb0
     # plain one-at-a-time FP64 GPU path on the first `serial` problems
     A_flat.copy_(A0)

@@ -299,7 +299,11 @@ int slqr_batch_max_rows(void);
  * (16, 16), (16, 32), (16, 64), (32, 16), (32, 32), (32, 64).  The setting is
  * chosen per precision (SLQR_FP64, SLQR_FP32) and per size class of the
  * problem's row count m: class 0 m <= 64, 1 m <= 128, 2 m <= 256, 3 m <= 512
- * (slqr_batch_class_rows gives the upper bounds); (16, 32) by default.  The
+ * (slqr_batch_class_rows gives the upper bounds); (16, 32) by default.  For
+ * SLQR_FP64 the classes 0 and 1 may instead take the shared-memory-resident
+ * kernel (`resident` = 1, with the pair (16, 32)): the whole problem and its b
+ * are copied into shared memory, factored and back-substituted there, and
+ * written back once.  The
  * problems of classes that share a setting run in one persistent launch; a
  * batch whose classes use different settings makes one launch per setting,
  * one after the other on the caller's stream.  Settings are process-wide:
@@ -307,8 +311,10 @@ int slqr_batch_max_rows(void);
  * the settings it was created with).
  *
  * slqr_batch_set_tuning  sets the pair of one class (m_class -1: every class);
- *                        (0, 0) restores the default.  SLQR_EINVAL for an
- *                        invalid precision, class or pair.
+ *                        (0, 0) restores the default; resident 1 selects the
+ *                        resident kernel (SLQR_FP64, class 0 or 1, pair
+ *                        (16, 32) or (0, 0)).  SLQR_EINVAL for an invalid
+ *                        precision, class, pair or resident request.
  * slqr_batch_get_tuning  reads it (HOST outputs, each may be NULL).
  * slqr_batch_autotune    tunes the settings of `prec` for a mixture of
  *                        shapes: count, m, n (HOST arrays) give the shapes of
@@ -319,22 +325,28 @@ int slqr_batch_max_rows(void);
  *                        solve) is timed (best of two runs after a warm-up)
  *                        under each candidate.  Greedy coordinate search: the
  *                        classes costliest first, each trying every valid
- *                        pair with the other classes held, a change kept only
+ *                        pair (and, for SLQR_FP64 classes 0 and 1, the
+ *                        resident kernel) with the other classes held, a
+ *                        change kept only
  *                        when the whole scratch batch runs at least 1% faster
  *                        (a split into several launches must pay for itself).
  *                        Synchronous; allocates and frees its scratch.  HOST
- *                        outputs, each may be NULL: panel widths and tile
- *                        widths per class (slqr_batch_classes() entries), and
+ *                        outputs, each may be NULL: panel widths, tile widths
+ *                        and resident flags per class (slqr_batch_classes()
+ *                        entries), and
  *                        ms[2] = the scratch batch's time before and after.
  *                        Errors: SLQR_EINVAL, SLQR_ENOMEM, SLQR_ECUDA; on
  *                        error the previous settings are kept.
  */
 int slqr_batch_classes(void);
 int slqr_batch_class_rows(int m_class);
-slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_width, int tile_cols);
-slqr_status slqr_batch_get_tuning(int prec, int m_class, int *panel_width, int *tile_cols);
+slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_width, int tile_cols,
+                                  int resident);
+slqr_status slqr_batch_get_tuning(int prec, int m_class, int *panel_width, int *tile_cols,
+                                  int *resident);
 slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, const int *m, const int *n,
-                                int sample, int *panel_width, int *tile_cols, double *ms);
+                                int sample, int *panel_width, int *tile_cols, int *resident,
+                                double *ms);
 
 /*
  * slqr_batch_factor for stacked SLSQP matrices A_i = [L_i^T; C_i]: problem i

@@ -99,12 +99,13 @@ SIGNATURES = [
     ("slqr_batch_max_rows", _c_int, []),
     ("slqr_batch_classes", _c_int, []),
     ("slqr_batch_class_rows", _c_int, [_c_int]),
-    ("slqr_batch_set_tuning", _c_int, [_c_int, _c_int, _c_int, _c_int]),
+    ("slqr_batch_set_tuning", _c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
     ("slqr_batch_get_tuning", _c_int, [_c_int, _c_int, ctypes.POINTER(_c_int),
-                                       ctypes.POINTER(_c_int)]),
+                                       ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     ("slqr_batch_autotune", _c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_int),
                                      ctypes.POINTER(_c_int), _c_int, ctypes.POINTER(_c_int),
-                                     ctypes.POINTER(_c_int), ctypes.POINTER(_dbl)]),
+                                     ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                     ctypes.POINTER(_dbl)]),
     ("slqr_batch_plan_create", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                         ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
                                         ctypes.POINTER(_c_int), ctypes.POINTER(_vp),
@@ -278,26 +279,29 @@ def slqr_batch_class_rows(m_class: int) -> int:
     return _lib.slqr_batch_class_rows(m_class)
 
 
-def slqr_batch_set_tuning(prec: int, m_class: int, panel_width: int, tile_cols: int) -> int:
-    return _lib.slqr_batch_set_tuning(prec, m_class, panel_width, tile_cols)
+def slqr_batch_set_tuning(prec: int, m_class: int, panel_width: int, tile_cols: int,
+                          resident: int = 0) -> int:
+    return _lib.slqr_batch_set_tuning(prec, m_class, panel_width, tile_cols, resident)
 
 
 def slqr_batch_get_tuning(prec: int, m_class: int):
-    """Returns (status, panel_width, tile_cols)."""
-    nb, tc = _c_int(), _c_int()
-    st = _lib.slqr_batch_get_tuning(prec, m_class, ctypes.byref(nb), ctypes.byref(tc))
-    return st, nb.value, tc.value
+    """Returns (status, panel_width, tile_cols, resident)."""
+    nb, tc, rs = _c_int(), _c_int(), _c_int()
+    st = _lib.slqr_batch_get_tuning(prec, m_class, ctypes.byref(nb), ctypes.byref(tc),
+                                    ctypes.byref(rs))
+    return st, nb.value, tc.value, rs.value
 
 
 def slqr_batch_autotune(ctx, prec: int, m_list=None, n_list=None, sample: int = 0):
-    """Returns (status, [(panel_width, tile_cols) per size class], (ms_before, ms_after))."""
+    """Returns (status, [(panel_width, tile_cols, resident) per size class],
+    (ms_before, ms_after))."""
     k = _lib.slqr_batch_classes()
-    nb, tc, ms = (_c_int * k)(), (_c_int * k)(), (_dbl * 2)()
+    nb, tc, rs, ms = (_c_int * k)(), (_c_int * k)(), (_c_int * k)(), (_dbl * 2)()
     count = len(m_list) if m_list is not None else 0
     m_arr = _int_array(m_list) if count else None
     n_arr = _int_array(n_list) if count else None
-    st = _lib.slqr_batch_autotune(ctx, prec, count, m_arr, n_arr, sample, nb, tc, ms)
-    return st, [(nb[i], tc[i]) for i in range(k)], (ms[0], ms[1])
+    st = _lib.slqr_batch_autotune(ctx, prec, count, m_arr, n_arr, sample, nb, tc, rs, ms)
+    return st, [(nb[i], tc[i], rs[i]) for i in range(k)], (ms[0], ms[1])
 
 
 BATCH_SETTINGS = [(8, 32), (8, 64), (16, 16), (16, 32), (16, 64), (32, 16), (32, 32), (32, 64)]

@@ -14,9 +14,10 @@
 // Settings.  The panel width NB and the tile width TC of the kernels are
 // chosen per size class of the problems (m <= 64, <= 128, <= 256, <= 512) and
 // per precision, the batch form of the paper's alpha/beta task sizes
-// (Section 4.1): slqr_batch_autotune times every valid setting on scratch
-// batches of each class and keeps the fastest; by default every class uses
-// NB = 16, TC = 32.  The problems of the classes that share a setting go into
+// (Section 4.1); for FP64 the classes m <= 64 and m <= 128 may also take the
+// shared-memory-resident kernel (the whole problem in shared memory).
+// slqr_batch_autotune searches them on a sample of the caller's shapes; by
+// default every class uses NB = 16, TC = 32.  The problems of the classes that share a setting go into
 // one persistent launch (with its own costliest-first order and work
 // counter); the launches of a batch follow each other on the caller's stream,
 // costliest group first.
@@ -38,8 +39,15 @@ BatchKernels batch_kernels_nb16(int tc) {
   }
 }
 
-// kernels of a setting (null pointers when not valid)
-static BatchKernels batch_kernels(int nb, int tc) {
+// kernels of a setting (null pointers when not valid); rm > 0: the
+// shared-memory-resident FP64 kernel for problems of at most rm rows
+static BatchKernels batch_kernels(int nb, int tc, int rm = 0) {
+  if (rm > 0) {
+    if (nb != 16 || tc != 32) return BatchKernels{};
+    if (rm == 64) return batch_resident_kernels_of<16, 32, 64>();
+    if (rm == 128) return batch_resident_kernels_of<16, 32, 128>();
+    return BatchKernels{};
+  }
   switch (nb) {
     case 8: return batch_kernels_nb8(tc);
     case 16: return batch_kernels_nb16(tc);
@@ -59,7 +67,8 @@ static int batch_class(int m) {
 
 struct BatchSetting {
   int nb = kBNBDefault, tc = kBTCDefault;
-  bool operator==(const BatchSetting &o) const { return nb == o.nb && tc == o.tc; }
+  int rm = 0;                   // > 0: the resident FP64 kernel for m <= rm
+  bool operator==(const BatchSetting &o) const { return nb == o.nb && tc == o.tc && rm == o.rm; }
 };
 // per precision (0: SLQR_FP64, 1: SLQR_FP32) and size class
 static BatchSetting g_batch_setting[2][kBClasses];
@@ -73,6 +82,13 @@ static BatchSetting batch_setting(int prec, int cls) {
 static const BatchSetting kBSettings[] = {{8, 32}, {8, 64}, {16, 16}, {16, 32}, {16, 64},
                                           {32, 16}, {32, 32}, {32, 64}};
 
+// the resident setting a size class may take (FP64 only): its row bound
+static BatchSetting resident_setting(int cls) {
+  BatchSetting s;
+  s.rm = (cls <= 1) ? kBClassHi[cls] : 0;
+  return s;
+}
+
 slqr_status init_batch_attrs(slqr_ctx *ctx) {
   cudaError_t e = cudaSuccess;
   for (const BatchSetting &s : kBSettings) {
@@ -83,6 +99,12 @@ slqr_status init_batch_attrs(slqr_ctx *ctx) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k.mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)k.smem_mixed);
+  }
+  for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+    const BatchSetting r = resident_setting(c);
+    BatchKernels k = batch_kernels(r.nb, r.tc, r.rm);
+    if (!k.fp64) return fail(ctx, SLQR_ECUDA, "resident batch kernel (%d rows) missing", r.rm);
+    e = cudaFuncSetAttribute(k.fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fp64);
   }
   if (e != cudaSuccess)
     return fail(ctx, SLQR_ECUDA, "cudaFuncSetAttribute(batch): %s", cudaGetErrorString(e));
@@ -184,7 +206,10 @@ static slqr_status batch_build(slqr_ctx *ctx, int count, const int *m, const int
     grp.begin = (int)bs.order.size();
     grp.count = (int)members[g].size();
     bs.order.insert(bs.order.end(), members[g].begin(), members[g].end());
-    BatchKernels k = batch_kernels(grp.set.nb, grp.set.tc);
+    BatchKernels k = batch_kernels(grp.set.nb, grp.set.tc, grp.set.rm);
+    if (bs.mixed ? !k.mixed : !k.fp64)
+      return fail(ctx, SLQR_EINVAL, "batch setting (%d, %d, resident %d) has no kernel here",
+                  grp.set.nb, grp.set.tc, grp.set.rm);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, bs.mixed ? k.mixed : k.fp64, kThreads, bs.mixed ? k.smem_mixed : k.smem_fp64);
@@ -212,7 +237,7 @@ static void batch_kernel_launch(const BatchSetup &bs, char *base, int *status, d
   int *d_order = (int *)(base + 256 + bs.table_bytes);
   for (size_t gi = 0; gi < bs.groups.size(); ++gi) {
     const BatchGroup &g = bs.groups[gi];
-    BatchKernels k = batch_kernels(g.set.nb, g.set.tc);
+    BatchKernels k = batch_kernels(g.set.nb, g.set.tc, g.set.rm);
     if (!bs.mixed) {
       BatchParams bp{d_probs, d_order + g.begin, g.count, counters + gi, status};
       void *args[] = {&bp};
@@ -321,11 +346,17 @@ extern "C" int slqr_batch_class_rows(int m_class) {
 }
 
 extern "C" slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_width,
-                                             int tile_cols) {
+                                             int tile_cols, int resident) {
   if (prec != SLQR_FP64 && prec != SLQR_FP32) return SLQR_EINVAL;
   if (m_class < -1 || m_class >= kBClasses) return SLQR_EINVAL;
   BatchSetting s;
-  if (panel_width != 0 || tile_cols != 0) {
+  if (resident) {
+    // the resident kernel: FP64, one size class of at most 128 rows, (16, 32)
+    if (prec != SLQR_FP64 || m_class < 0 || m_class > 1) return SLQR_EINVAL;
+    if (!((panel_width == 16 && tile_cols == 32) || (panel_width == 0 && tile_cols == 0)))
+      return SLQR_EINVAL;
+    s = resident_setting(m_class);
+  } else if (panel_width != 0 || tile_cols != 0) {
     bool ok = false;
     for (const BatchSetting &v : kBSettings) ok |= (v.nb == panel_width && v.tc == tile_cols);
     if (!ok) return SLQR_EINVAL;
@@ -339,18 +370,19 @@ extern "C" slqr_status slqr_batch_set_tuning(int prec, int m_class, int panel_wi
 }
 
 extern "C" slqr_status slqr_batch_get_tuning(int prec, int m_class, int *panel_width,
-                                             int *tile_cols) {
+                                             int *tile_cols, int *resident) {
   if ((prec != SLQR_FP64 && prec != SLQR_FP32) || m_class < 0 || m_class >= kBClasses)
     return SLQR_EINVAL;
   BatchSetting s = batch_setting(prec, m_class);
   if (panel_width) *panel_width = s.nb;
   if (tile_cols) *tile_cols = s.tc;
+  if (resident) *resident = s.rm > 0 ? 1 : 0;
   return SLQR_OK;
 }
 
 extern "C" slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, const int *m,
                                            const int *n, int sample, int *panel_width,
-                                           int *tile_cols, double *ms_out) {
+                                           int *tile_cols, int *resident, double *ms_out) {
   NvtxRange nvtx_range("slqr_batch_autotune");
   if (!ctx) return SLQR_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -468,7 +500,9 @@ extern "C" slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, c
                    [&](int a, int c) { return cls_cost[a] > cls_cost[c]; });
   for (int c : corder) {
     if (cls_cost[c] == 0.0) continue;
-    for (const BatchSetting &cand : kBSettings) {
+    std::vector<BatchSetting> cands(std::begin(kBSettings), std::end(kBSettings));
+    if (prec == SLQR_FP64 && c <= 1) cands.push_back(resident_setting(c));
+    for (const BatchSetting &cand : cands) {
       if (st != SLQR_OK || e != cudaSuccess) break;
       if (cand == cur[c]) continue;
       BatchSetting trial[kBClasses] = {cur[0], cur[1], cur[2], cur[3]};
@@ -502,6 +536,7 @@ extern "C" slqr_status slqr_batch_autotune(slqr_ctx *ctx, int prec, int count, c
   for (int c = 0; c < kBClasses; ++c) {
     if (panel_width) panel_width[c] = cur[c].nb;
     if (tile_cols) tile_cols[c] = cur[c].tc;
+    if (resident) resident[c] = cur[c].rm > 0 ? 1 : 0;
   }
   if (ms_out) {
     ms_out[0] = t_before;

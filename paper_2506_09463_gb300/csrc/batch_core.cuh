@@ -120,9 +120,11 @@ __device__ __forceinline__ double b_warp_sum(double v) {
 // mixed-precision path); the small per-panel quantities are double.
 __host__ __device__ constexpr size_t align_up_c(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <typename T, int NB, int TC>
+// PR: rows the panel slice holds (kBMaxRows, or the row bound of the
+// shared-memory-resident kernels)
+template <typename T, int NB, int TC, int PR = kBMaxRows>
 struct BatchSmem {
-  static constexpr int kPanel = NB * kBMaxRows;         // Ps[c][r]
+  static constexpr int kPanel = NB * PR;                // Ps[c][r]
   static constexpr int kW = NB * (TC + 1);              // Wt[a][col]
   static constexpr int kG = NB * NB;                    // G[q][j] (ld NB)
   // T copies of the panel's G and tau for W' = T^T W (phase B)
@@ -145,10 +147,13 @@ struct BatchSmem {
 // r of the panel is matrix row k0 + r for r < nbw, k0 + skip + r below, with
 // skip = ntop - k0 - nbw): the rows between are zero in every reflector and
 // untouched by the update.
-template <typename T, int NB, int TC>
+//
+// A and Bcol may point to global or to shared memory (the resident kernels
+// factor a shared-memory copy of the problem); PR is the panel's row capacity.
+template <typename T, int NB, int TC, int PR = kBMaxRows>
 __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, double *Bcol,
                                   double *G_out, double *tau_out, char *smraw, int ntop) {
-  using SM = BatchSmem<T, NB, TC>;
+  using SM = BatchSmem<T, NB, TC, PR>;
   using TL = BTile<NB, TC>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g8 = lane & (TL::RG - 1);          // this lane's row group in the tile phases
@@ -183,7 +188,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     for (int idx = tid; idx < NB * M; idx += kThreads) {
       int c = idx / M, r = idx - c * M;
       const bool zero = c >= nbw || (ntop > 0 && r < nbw && r > c);
-      Ps[c * kBMaxRows + r] = zero ? T(0) : A[SLQR_IDX(k0 + prow(r), k0 + c, lda)];
+      Ps[c * PR + r] = zero ? T(0) : A[SLQR_IDX(k0 + prow(r), k0 + c, lda)];
     }
     __syncthreads();
     // Per-column scale of the panel for the overflow-safe norm: 2^-E with E the
@@ -195,7 +200,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
       const int c = warp + kBWarps * t;
       if (c < nbw) {
         unsigned mx = 0;
-        for (int r = c + lane; r < M; r += 32) mx = max(mx, b_abs_hi(Ps[c * kBMaxRows + r]));
+        for (int r = c + lane; r < M; r += 32) mx = max(mx, b_abs_hi(Ps[c * PR + r]));
         mx = __reduce_max_sync(0xffffffffu, mx);
         if (lane == 0) {
           int E = (int)((mx >> 20) & 0x7ff) - 1023;
@@ -209,7 +214,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     }
     __syncthreads();
     for (int j = 0; j < nbw; ++j) {
-      const T *x = Ps + j * kBMaxRows;
+      const T *x = Ps + j * PR;
       // phase 1: warp w takes panel columns w, w + 8, ...
 #pragma unroll
       for (int t = 0; t < TL::NBW8; ++t) {
@@ -235,7 +240,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
             else misc[0] = sqrt((double)S) * sinv[j];
           }
         } else {
-          const T *col = Ps + c * kBMaxRows;
+          const T *col = Ps + c * PR;
           T acc = T(0), acc1 = T(0);                   // two chains
           int r = j + 1 + lane;
           for (; r + 32 < M; r += 64) {
@@ -263,7 +268,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         }
         if (tid < nbw) {
           const int c = tid;
-          const T pr_c = Ps[c * kBMaxRows + j];
+          const T pr_c = Ps[c * PR + j];
           if (c > j) sig[c] = defined ? (double)(-(upT * pr_c + (T)dots[c]) * tkT) : 0.0;
           else if (c < j) Gs[c + j * NB] = (double)(pr_c * upT + (T)dots[c]);
         }
@@ -279,7 +284,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         }
         if (tid < nbw) {
           const int c = tid;
-          const double pr_c = (double)Ps[c * kBMaxRows + j];
+          const double pr_c = (double)Ps[c * PR + j];
           // sigma_c = (up p_c + D_c) / b = -(up p_c + D_c) tau
           if (c > j) sig[c] = defined ? -(upk * pr_c + dots[c]) * tk : 0.0;
           else if (c < j) Gs[c + j * NB] = pr_c * upk + dots[c];
@@ -292,7 +297,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
         for (int t = 0; t < TL::NBW8; ++t) {
           const int c = warp + kBWarps * t;
           if (c > j && c < nbw) {
-            T *col = Ps + c * kBMaxRows;
+            T *col = Ps + c * PR;
             const T sg = (T)sig[c];
             for (int r = j + 1 + lane; r < M; r += 32) col[r] = fma(sg, x[r], col[r]);
             if (lane == 0) col[j] = fma(sg, upT, col[j]);
@@ -301,7 +306,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
       }
       __syncthreads();
       if (tid == 0) {
-        if (defined) Ps[j * kBMaxRows + j] = (T)cl;
+        if (defined) Ps[j * PR + j] = (T)cl;
         tau[j] = tk;
         ups[j] = upk;
       }
@@ -311,7 +316,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     // V (zero above the diagonal, up on it) for the trailing update
     for (int idx = tid; idx < nbw * M; idx += kThreads) {
       int c = idx / M, r = idx - c * M;
-      if (!(ntop > 0 && r < nbw && r > c)) A[SLQR_IDX(k0 + prow(r), k0 + c, lda)] = Ps[c * kBMaxRows + r];
+      if (!(ntop > 0 && r < nbw && r > c)) A[SLQR_IDX(k0 + prow(r), k0 + c, lda)] = Ps[c * PR + r];
     }
     if (tid < nbw) up_out[k0 + tid] = ups[tid];
     if (G_out) {
@@ -325,7 +330,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
     __syncthreads();
     for (int idx = tid; idx < NB * NB; idx += kThreads) {
       int c = idx / NB, r = idx - c * NB;
-      if (r <= c && r < M) Ps[c * kBMaxRows + r] = (r == c && c < nbw) ? (T)ups[c] : T(0);
+      if (r <= c && r < M) Ps[c * PR + r] = (r == c && c < nbw) ? (T)ups[c] : T(0);
       Gt[idx] = (T)Gs[idx];
     }
     if (tid < NB) taut[tid] = (T)tau[tid];
@@ -354,7 +359,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
             const T cv = C[prow(r)];
 #pragma unroll
             for (int a = 0; a < NB; ++a)
-              if (a < nbw) acc[a] = fma(Ps[a * kBMaxRows + r], cv, acc[a]);
+              if (a < nbw) acc[a] = fma(Ps[a * PR + r], cv, acc[a]);
           }
         }
         b_group_sum<T, NB, TL::RG>(acc, g8);    // lane g holds W[VPL g + i], i < VPL
@@ -395,7 +400,7 @@ __device__ void batch_factor_core(T *A, int lda, int m, int n, double *up_out, d
             T cv = C[pr];
 #pragma unroll
             for (int a = 0; a < NB; ++a)
-              if (a < nbw) cv = fma(-Ps[a * kBMaxRows + r], w[a], cv);
+              if (a < nbw) cv = fma(-Ps[a * PR + r], w[a], cv);
             C[pr] = cv;
           }
         }
@@ -454,6 +459,67 @@ batch_factor_fp64_kernel(BatchParams bp) {
       } else if (threadIdx.x == 0) {
         s_status = SLQR_OK;
       }
+      __syncthreads();
+      if (threadIdx.x == 0 && bp.status) bp.status[p] = s_status;
+    } else if (threadIdx.x == 0 && bp.status) {
+      bp.status[p] = SLQR_OK;
+    }
+  }
+}
+
+// Shared-memory-resident FP64 kernel for problems of at most RM rows: the
+// problem (A, ld m) and b are copied into shared memory once, factored and
+// back-substituted there by the same code, and written back once, so the
+// trailing updates and the solve never touch global memory.
+template <int NB, int TC, int RM>
+struct BatchResident {
+  static constexpr size_t kCore = align_up_c(BatchSmem<double, NB, TC, RM>::kBytes, 16);
+  static constexpr size_t kBytes = kCore + (size_t)(RM * RM + 2 * RM) * sizeof(double);
+};
+
+template <int NB, int TC, int RM>
+__global__ void __launch_bounds__(kThreads, RM <= 64 ? 2 : 1)
+batch_factor_resident_kernel(BatchParams bp) {
+  extern __shared__ __align__(16) char smraw[];
+  __shared__ int s_item;
+  __shared__ int s_status;
+  using RS = BatchResident<NB, TC, RM>;
+  double *As = (double *)(smraw + RS::kCore);      // [RM][RM], ld m
+  double *bs = As + RM * RM;                       // RM
+  double *xs = bs + RM;                            // RM (the solve's scratch)
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= bp.count) break;
+    const int p = bp.order[item];
+    const BatchProblem pr = bp.probs[p];
+    const int m = pr.m, n = pr.n;
+    if (n > 0) {
+      for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
+        const int c = idx / m, r = idx - c * m;
+        // (stacked: the strictly lower part of the top block is not read)
+        As[idx] = (pr.ntop > 0 && c < pr.ntop && r > c && r < pr.ntop) ? 0.0
+                                                                       : pr.A[SLQR_IDX(r, c, pr.lda)];
+      }
+      if (pr.b)
+        for (int i = threadIdx.x; i < m; i += kThreads) bs[i] = pr.b[i];
+      __syncthreads();
+      batch_factor_core<double, NB, TC, RM>(As, m, m, n, pr.up, pr.b ? bs : nullptr, nullptr,
+                                            nullptr, smraw, pr.ntop);
+      if (pr.b) {
+        batch_solve_fp64(As, m, n, bs, xs, &s_status);
+      } else if (threadIdx.x == 0) {
+        s_status = SLQR_OK;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
+        const int c = idx / m, r = idx - c * m;
+        if (!(pr.ntop > 0 && c < pr.ntop && r > c && r < pr.ntop)) pr.A[SLQR_IDX(r, c, pr.lda)] = As[idx];
+      }
+      if (pr.b)
+        for (int i = threadIdx.x; i < m; i += kThreads) pr.b[i] = bs[i];
       __syncthreads();
       if (threadIdx.x == 0 && bp.status) bp.status[p] = s_status;
     } else if (threadIdx.x == 0 && bp.status) {
@@ -822,7 +888,8 @@ constexpr size_t batch_mixed_smem_bytes() {
              : 6 * kBMaxRows * sizeof(double);
 }
 
-// The two persistent kernels of one setting and their dynamic shared memory.
+// The two persistent kernels of one setting and their dynamic shared memory
+// (the resident settings have an FP64 kernel only).
 struct BatchKernels {
   const void *fp64 = nullptr, *mixed = nullptr;
   size_t smem_fp64 = 0, smem_mixed = 0;
@@ -838,9 +905,17 @@ BatchKernels batch_kernels_of() {
   return k;
 }
 
-// The kernels of setting (nb, tc), instantiated in batch.cu (nb = 16),
-// batch_nb8.cu and batch_nb32.cu; null pointers for a setting that is not
-// valid (nb < 256 / tc).
+template <int NB, int TC, int RM>
+BatchKernels batch_resident_kernels_of() {
+  BatchKernels k;
+  k.fp64 = (const void *)batch_factor_resident_kernel<NB, TC, RM>;
+  k.smem_fp64 = BatchResident<NB, TC, RM>::kBytes;
+  return k;
+}
+
+// The kernels of setting (nb, tc), instantiated in batch.cu (nb = 16, and the
+// resident ones), batch_nb8.cu and batch_nb32.cu; null pointers for a setting
+// that is not valid (nb < 256 / tc).
 BatchKernels batch_kernels_nb8(int tc);
 BatchKernels batch_kernels_nb16(int tc);
 BatchKernels batch_kernels_nb32(int tc);

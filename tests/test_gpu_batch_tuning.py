@@ -81,7 +81,7 @@ def test_every_setting_matches_the_oracle(ctx, nb, tc, prec_name):
     prec = abi.SLQR_FP64 if prec_name == "fp64" else abi.SLQR_FP32
     assert abi.slqr_batch_set_tuning(prec, -1, nb, tc) == abi.SLQR_OK
     for c in range(abi.slqr_batch_classes()):
-        assert abi.slqr_batch_get_tuning(prec, c) == (abi.SLQR_OK, nb, tc)
+        assert abi.slqr_batch_get_tuning(prec, c) == (abi.SLQR_OK, nb, tc, 0)
     ms, ns = shapes(seed=90 + nb + tc)
     res = run(ctx, ms, ns, seed=91 + nb + tc, prec=prec)
     check_all(res, ms, ns, prec)
@@ -140,15 +140,56 @@ def test_autotune_keeps_a_valid_setting_per_class(ctx, prec_name):
     assert st == abi.SLQR_OK, abi.slqr_last_error(ctx.ctx)
     assert len(choice) == abi.slqr_batch_classes() == 4
     assert 0.0 < t_after <= t_before
-    for c, (nb, tc) in enumerate(choice):
-        assert (nb, tc) in SETTINGS
-        assert abi.slqr_batch_get_tuning(prec, c) == (abi.SLQR_OK, nb, tc)
+    for c, (nb, tc, rs) in enumerate(choice):
+        assert (nb, tc) in SETTINGS and (rs == 0 or (prec == abi.SLQR_FP64 and c <= 1))
+        assert abi.slqr_batch_get_tuning(prec, c) == (abi.SLQR_OK, nb, tc, rs)
     # and for the default shape law
     st, choice2, _ = abi.slqr_batch_autotune(ctx.ctx, prec, sample=300)
-    assert st == abi.SLQR_OK and all((nb, tc) in SETTINGS for nb, tc in choice2)
+    assert st == abi.SLQR_OK and all((nb, tc) in SETTINGS for nb, tc, _ in choice2)
     res = run(ctx, ms, ns, seed=100, prec=prec)
     check_all(res, ms, ns, prec)
     assert abi.slqr_batch_set_tuning(prec, -1, 0, 0) == abi.SLQR_OK
+
+
+def test_resident_kernel_for_the_small_classes(ctx):
+    """SLQR_FP64, classes m <= 64 and m <= 128 on the shared-memory-resident
+    kernel (the whole problem and b in shared memory), the other classes on
+    the default: every problem against the oracle; stacked problems too."""
+    from paper_2506_09463_gb300 import abi
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, 0, 0, 0, 1) == abi.SLQR_OK
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, 1, 16, 32, 1) == abi.SLQR_OK
+    assert abi.slqr_batch_get_tuning(abi.SLQR_FP64, 0) == (abi.SLQR_OK, 16, 32, 1)
+    assert abi.slqr_batch_get_tuning(abi.SLQR_FP64, 2) == (abi.SLQR_OK, 16, 32, 0)
+    ms, ns = shapes(seed=101, extra=150)
+    res = run(ctx, ms, ns, seed=102, prec=abi.SLQR_FP64)
+    check_all(res, ms, ns, abi.SLQR_FP64)
+    # stacked [L^T; C] problems of the resident classes
+    sn = [5, 30, 60, 90, 120]
+    smeq = [3, 30, 4, 30, 8]
+    Ah = [workloads.slsqp_stack(n_, q_, 200 + n_)[0] for n_, q_ in zip(sn, smeq)]
+    bh = [workloads.slsqp_stack(n_, q_, 200 + n_)[1] for n_, q_ in zip(sn, smeq)]
+    Ad = [torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t() for A in Ah]   # column-major
+    for A_, n_ in zip(Ad, sn):                   # the zero block is neither read nor written
+        il = torch.tril_indices(n_, n_, -1, device="cuda")
+        A_[il[0], il[1]] = float("nan")
+    bd = [torch.from_numpy(b.copy()).cuda() for b in bh]
+    up = [torch.empty(n_, dtype=torch.float64, device="cuda") for n_ in sn]
+    status = torch.full((len(sn),), 99, dtype=torch.int32, device="cuda")
+    st = abi.slqr_batch_factor_stacked(ctx.ctx, sn, smeq, [a.data_ptr() for a in Ad],
+                                       [n_ + q_ for n_, q_ in zip(sn, smeq)],
+                                       [u.data_ptr() for u in up], [b.data_ptr() for b in bd],
+                                       abi.SLQR_FP64, status.data_ptr(), None,
+                                       torch.cuda.current_stream().cuda_stream)
+    abi.check(ctx.ctx, st, "stacked batch")
+    assert ctx.sync() == 0 and np.all(status.cpu().numpy() == 0)
+    for A, b, A_, b_, n_ in zip(Ah, bh, Ad, bd, sn):
+        x_o = oracle.lstsq(A, b)[0]
+        il = torch.tril_indices(n_, n_, -1, device="cuda")
+        assert bool(torch.isnan(A_[il[0], il[1]]).all())
+        kappa = np.linalg.cond(A)
+        rel = np.linalg.norm(b_[:n_].cpu().numpy() - x_o) / np.linalg.norm(x_o)
+        assert rel <= 64.0 * (kappa + kappa ** 2) * U, rel
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, -1, 0, 0) == abi.SLQR_OK
 
 
 def test_set_tuning_rejects_invalid_settings():
@@ -158,4 +199,8 @@ def test_set_tuning_rejects_invalid_settings():
     assert abi.slqr_batch_set_tuning(abi.SLQR_TF32, 0, 16, 32) == abi.SLQR_EINVAL
     assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, 4, 16, 32) == abi.SLQR_EINVAL
     assert abi.slqr_batch_get_tuning(abi.SLQR_FP64, 4)[0] == abi.SLQR_EINVAL
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP32, 0, 16, 32, 1) == abi.SLQR_EINVAL  # FP64 only
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, 2, 16, 32, 1) == abi.SLQR_EINVAL  # m <= 128
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, -1, 16, 32, 1) == abi.SLQR_EINVAL
+    assert abi.slqr_batch_set_tuning(abi.SLQR_FP64, 0, 8, 32, 1) == abi.SLQR_EINVAL
     assert [abi.slqr_batch_class_rows(c) for c in range(5)] == [64, 128, 256, 512, 0]
