@@ -45,13 +45,17 @@ CPU_SAMPLE_COLS = 512   # oracle sample: leading m x 512 block of each matrix
 # factorization-only timings reported beside the step (N(0,1), seeds 2, 3, 4)
 FACTOR_ONLY_SHAPES = [(16384, 2048, 2), (8192, 8192, 3), (8192, 4096, 4)]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the two
-# trailing-update kernels, averaged over every launch of
-#   python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-mixed --no-serving
-# under ncu (one pass), beside the algorithmic bytes of the same launches
-# (vtx: 8 M (N + 64) read; upd: X read and written, V and W' read).  Reset to
-# None whenever either kernel changes.
-TRAFFIC_PER_LAUNCH = {"vtx": {"dram": 58.52e6, "algorithmic": 52.23e6},
-                      "upd": {"dram": 85.63e6, "algorithmic": 101.72e6}}
+# trailing-update kernels, scaled to this program's launches from a one-pass
+# capture of those two kernels alone on a small case larger than L2:
+#   python bench.py --ncu-case 8192 2048 && ncu --metrics dram__bytes_read.sum,\
+#     dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#     -k regex:"gemm_(vtx|upd)_kernel" -c 400 --csv python bench.py --ncu-case 8192 2048
+# There vtx moved 1.119 and upd 0.638 times their algorithmic bytes (vtx: 8 M (N + 64)
+# read; upd: X read and written, V and W' read); times this program's average algorithmic
+# bytes per launch (vtx 52.23 MB, upd 101.72 MB).  Re-measure the same way (never the
+# full-size program with DRAM counters) and reset to None whenever either kernel changes.
+TRAFFIC_PER_LAUNCH = {"vtx": {"dram": 1.119 * 52.23e6, "algorithmic": 52.23e6},
+                      "upd": {"dram": 0.638 * 101.72e6, "algorithmic": 101.72e6}}
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -479,7 +483,7 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": tr["dram"] if tr else None,
                 "traffic_algorithmic": tr["algorithmic"] if tr else None,
-                "traffic_unit": "bytes per launch (ncu, average over the launches of the FP64 bench command)",
+                "traffic_unit": "bytes per launch (ncu on 8192x2048, scaled to this program's launches)",
                 "peak_source": "derived: FP64 FMA pipe 4 flop/clk/SM x 152 SMs x 2070 MHz"}
     kernels = {k: {"ms": v[0], "launches": v[1], "share_of_step_time": v[0] / max(1e-9, ms),
                    "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0}
@@ -998,6 +1002,30 @@ def run_ncu_batch(count):
     return 0
 
 
+def run_ncu_gmres(m, n):
+    """GMRES-IR alone (a budget of 8 Krylov iterations) on an m x n matrix of
+    condition 1e6 (the conditioned recipe drawn on the host with numpy: no
+    torch.linalg call, which does not load under ncu), FP32 and split-BF16
+    factorizations: a short program for ncu captures of the preconditioner."""
+    import torch
+    import workloads
+    from paper_2506_09463_gb300 import abi, api
+    A, b_cons, x_true, b_rand = workloads.conditioned(m, n, 1e6, seed=5)
+    dev = torch.device("cuda", 0)
+    Ad = colmajor_cuda(A, dev)
+    bd = torch.from_numpy(b_rand.copy()).to(dev)
+    with api.Context(0) as ctx:
+        for prec in (abi.SLQR_FP32, abi.SLQR_BF16X3):
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            st, info = abi.slqr_lstsq_mixed_ex(ctx.ctx, m, n, Ad.data_ptr(), m, bd.data_ptr(),
+                                               x.data_ptr(), prec, 0,
+                                               refine=abi.SLQR_REFINE_GMRES, gmres_max_iters=8)
+            if st not in (abi.SLQR_OK, abi.SLQR_ENOCONV):
+                raise RuntimeError(f"status {st}")
+            print(prec, abi.STATUS_NAMES.get(st, st), info)
+    return 0
+
+
 def run_ncu_case(m, n):
     """One factorization + Q^T (64 RHS) + back-substitution of an m x n N(0,1)
     matrix after one warm-up pass: a small, short program for ncu captures."""
@@ -1041,11 +1069,15 @@ def main():
                     help="run one FP64 and one FP32 batch for profiling and exit")
     ap.add_argument("--tune", action="store_true",
                     help="time the factorization under the panel tuning knobs and exit")
+    ap.add_argument("--ncu-gmres", type=int, nargs=2, metavar=("M", "N"),
+                    help="GMRES-IR alone on an M x N matrix of condition 1e6 (ncu captures)")
     ap.add_argument("--ncu-case", type=int, nargs=2, metavar=("M", "N"),
                     help="run one small factor/apply/solve pass for profiling and exit")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(*args.ncu_case)
+    if args.ncu_gmres:
+        return run_ncu_gmres(*args.ncu_gmres)
     if args.tune:
         return run_tune()
     if args.ncu_mixed:
