@@ -470,6 +470,13 @@ def run_ours(args, rank, world, local_rank):
                    if not args.no_mixed else (None, None))
     serving = run_serving_workload(local_rank) if not args.no_serving else None
 
+    # ---- measured arithmetic peaks (diagnostic probes of the library) ----
+    peaks = {}
+    for name, kind in (("fp64_fma_tflops", abi.SLQR_PEAK_FP64_FMA),
+                       ("tf32_tensor_tflops", abi.SLQR_PEAK_TF32_TC)):
+        stp, v = abi.slqr_measure_peak(ctx.ctx, kind)
+        peaks[name] = v if stp == abi.SLQR_OK else None
+
     # ---- roofline of the dominant kernel (most device time in the timed region) ----
     # the dominant kernel is the family carrying most of the algorithmic flops
     # (the two trailing-update GEMMs carry equal shares; take the slower one);
@@ -484,7 +491,10 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": tr["dram"] if tr else None,
                 "traffic_algorithmic": tr["algorithmic"] if tr else None,
                 "traffic_unit": "bytes per launch (ncu on 8192x2048, scaled to this program's launches)",
-                "peak_source": "derived: FP64 FMA pipe 4 flop/clk/SM x 152 SMs x 2070 MHz"}
+                "peak_source": "derived: FP64 FMA pipe 4 flop/clk/SM x 152 SMs x 2070 MHz",
+                "peak_measured": peaks.get("fp64_fma_tflops"),
+                "frac_of_measured": (achieved / peaks["fp64_fma_tflops"]
+                                     if peaks.get("fp64_fma_tflops") else None)}
     kernels = {k: {"ms": v[0], "launches": v[1], "share_of_step_time": v[0] / max(1e-9, ms),
                    "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0}
                for k, v in prof.items()}
@@ -512,6 +522,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clk,
+        "peaks_measured": peaks,
         "gpu_launches": launches,
         "kernels": kernels,
         "factor_only": factor_only,
@@ -658,31 +669,37 @@ def single_problem_latency(ctx, device, stream, barrier, reps=50):
             "reps": reps}
 
 
-def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):
+def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=1000):
     """Poisson request streams of SLSQP-shaped LS subproblems [L^T; C]
     (n ~ log-U[50, 2000], m_eq ~ U{0..n/2}), FACTOR_SOLVE each, through
-    slqr_submit / slqr_poll; reports solves/s and p50/p99 latency per rate, in
-    FP64 and mixed (FP32 + refinement for m <= 512, FP64 above), each as a
-    dense request and as a stacked one (SLQR_STACKED: the structure-aware
-    factorization of [L^T; C])."""
+    slqr_submit / slqr_poll; reports solves/s and p50/p99 latency per rate
+    (`count` requests, so that p99 is a percentile of 1000 samples), in FP64
+    and in mixed precision (every request SLQR_FP32: the batched FP32 launch
+    for m <= 512, a mixed lane above, the FP64 fallback flagged), each as a
+    dense request and as a stacked one (SLQR_STACKED).  Every mixed-precision
+    solution is compared with the FP64 request's solution of the same problem
+    at the same rate."""
     import time
     import workloads
     from paper_2506_09463_gb300 import abi, api
     t_arr, ns, meqs, seeds = workloads.serving_stream(count, rate=1.0)
     problems = [workloads.slsqp_stack(int(ns[i]), int(meqs[i]), int(seeds[i])) for i in range(count)]
     gflop = sum(2.0 * (n + me) * n * n - 2.0 * n ** 3 / 3.0 for n, me in zip(ns, meqs)) / 1e9
-    out = {"requests": count, "mean_gflop_per_request": gflop / count,
+    out = {"requests_per_rate": count, "mean_gflop_per_request": gflop / count,
            "shapes": "[L^T; C], n ~ log-U[50,2000], m_eq ~ U{0..n/2}, Poisson arrivals"}
     modes = (("fp64", abi.SLQR_DENSE), ("mixed", abi.SLQR_DENSE),
              ("fp64_stacked", abi.SLQR_STACKED), ("mixed_stacked", abi.SLQR_STACKED))
+    x_fp64 = {}
     for mode, structure in modes:
         res_mode = {}
+        mixed = mode.startswith("mixed")
         for rate in rates:
             with api.Context(ctx_device) as sctx:
                 srv = api.Server(sctx)
-                # warm the loop (streams, pools, kernels) with one small request
-                A, b = problems[0]
-                srv.wait(srv.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b))
+                # warm the loop (streams, pools, lanes, kernels) with two requests
+                for A, b in (problems[0], workloads.slsqp_stack(700, 200, 1)):
+                    srv.wait(srv.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b,
+                                        prec=abi.SLQR_FP32 if mixed else abi.SLQR_FP64))
                 gaps = np.random.default_rng(int(rate)).exponential(1.0 / rate, size=count)
                 arrivals = np.cumsum(gaps) - gaps[0]
                 tickets = []
@@ -691,21 +708,31 @@ def run_serving_workload(ctx_device, rates=(100.0, 400.0, 1600.0), count=160):
                     while time.perf_counter() - t0 < arrivals[i]:
                         pass
                     A, b = problems[i]
-                    mixed = mode.startswith("mixed") and A.shape[0] <= 512
                     prec = abi.SLQR_FP32 if mixed else abi.SLQR_FP64
                     tickets.append(srv.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b, prec=prec,
                                               structure=structure))
-                lat, bad = [], 0
+                lat, bad, fallback, xs = [], 0, 0, []
                 for t in tickets:
-                    r, _ = srv.wait(t, timeout_s=600)
+                    r, x = srv.wait(t, timeout_s=600)
                     lat.append(r.latency_ms)
-                    bad += int(r.status != 0)
+                    bad += int(r.status not in (abi.SLQR_OK, abi.SLQR_FALLBACK))
+                    fallback += int(r.status == abi.SLQR_FALLBACK)
+                    xs.append(x)
                 wall = time.perf_counter() - t0
                 lat = np.array(lat)
-                res_mode[f"rate_{rate:g}"] = {
-                    "offered_req_per_s": rate, "solves_per_s": count / wall,
-                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                    "failed": bad, "gflops": gflop / wall}
+                rec = {"offered_req_per_s": rate, "solves_per_s": count / wall,
+                       "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)),
+                       "failed": bad, "fp64_fallbacks": fallback, "gflops": gflop / wall}
+                key = (structure, rate)
+                if not mixed:
+                    x_fp64[key] = xs
+                elif key in x_fp64:
+                    rel = [float(np.max(np.abs(a - c)) / np.max(np.abs(c)))
+                           for a, c in zip(xs, x_fp64[key])]
+                    rec["max_rel_diff_vs_fp64"] = max(rel)
+                    rec["over_1e-10_vs_fp64"] = int(sum(r_ > 1e-10 for r_ in rel))
+                res_mode[f"rate_{rate:g}"] = rec
         out[mode] = res_mode
     return out
 

@@ -452,6 +452,11 @@ slqr_status slqr_lstsq_mixed(slqr_ctx *ctx, int m, int n, const double *A, int l
  *                    (slqr_factor, slqr_apply_qt, slqr_solve_r on a copy of
  *                    A; m n + 2 m doubles more of device memory) and return
  *                    SLQR_FALLBACK; 0: return SLQR_ENOCONV
+ *   structure        SLQR_DENSE (0), or SLQR_STACKED: A = [L^T; C] with an
+ *                    upper-triangular top n x n block whose strictly lower
+ *                    part is zero (it is read: the FP64 residuals use all of
+ *                    A), factored with the structure of slqr_factor_stacked
+ *                    (its trailing updates on the FP32 FMA pipe)
  * Report (info may be NULL), HOST struct:
  *   method       how x was obtained: SLQR_REFINE_BJORCK, SLQR_REFINE_GMRES or
  *                SLQR_REFINE_FP64 (the fallback)
@@ -479,6 +484,7 @@ typedef struct {
   int gmres_restart;
   double gmres_tol;
   int fp64_fallback;
+  int structure;
 } slqr_mixed_opts;
 
 typedef struct {
@@ -512,10 +518,13 @@ slqr_status slqr_lstsq_mixed_ex(slqr_ctx *ctx, int m, int n, const double *A, in
  * Admission is in arrival order and by the context's HBM budget (bytes held
  * by resident factorizations and requests in flight); a request that cannot
  * fit waits until memory is freed, and one larger than the whole budget
- * fails with SLQR_EBUSY.  Admitted requests with m <= slqr_batch_max_rows()
- * of one precision share one persistent batched launch; larger ones run one
- * per stream on a pool of streams (FP64 factorization for either precision);
- * all of them overlap on the device.  Latency routing: while at most half of
+ * fails with SLQR_EBUSY.  Admitted FP64 requests with m <= slqr_batch_max_rows()
+ * share one persistent batched launch, and so do SLQR_FP32 FACTOR_SOLVE
+ * requests of that size; larger FP64 ones run one per stream on a pool of
+ * streams; every other mixed-precision request runs on a mixed lane (a helper
+ * thread with its own stream: the low-precision factorization and the
+ * automatic refinement of slqr_lstsq_mixed_ex with the FP64 fallback); all of
+ * them overlap on the device.  Latency routing: while at most half of
  * those streams are busy, a batch-sized request with m * n >= 60000 also runs
  * on a stream (its factorization is spread over many SMs instead of one CTA
  * of the batched launch).  Requests that arrive while others run are
@@ -523,10 +532,18 @@ slqr_status slqr_lstsq_mixed_ex(slqr_ctx *ctx, int m, int n, const double *A, in
  *
  * A, b and x are HOST pointers owned by the caller; they must stay valid
  * until slqr_poll reports the request done (A and b are copied in at
- * admission; x receives n doubles at completion).  prec: SLQR_FP64, or
- * SLQR_FP32 for FACTOR_SOLVE with m <= slqr_batch_max_rows() (FP32
- * factorization with FP64-residual refinement, see slqr_batch_factor, when
- * the request joins a batched launch; FP64 when it runs on a stream).
+ * admission; x receives n doubles at completion).  prec: SLQR_FP64,
+ * SLQR_FP32, SLQR_TF32 or SLQR_BF16X3.  A mixed-precision FACTOR_SOLVE of the
+ * batch size class in SLQR_FP32 joins the batched FP32 launch (refinement as
+ * in slqr_batch_factor); any other mixed-precision FACTOR_SOLVE is solved as
+ * by slqr_lstsq_mixed_ex in its automatic mode with fp64_fallback = 1
+ * (out->status SLQR_OK for a mixed-precision result, SLQR_FALLBACK when the
+ * FP64 solve answered).  A mixed-precision FACTOR keeps the library's FP64 copy
+ * of A and the low-precision factorization on the device under the handle
+ * (both counted in the HBM budget: m n doubles plus about m n floats); a
+ * SOLVE on it runs the refinement against that copy (SLQR_OK or
+ * SLQR_FALLBACK).  Stacked mixed-precision requests use the structure-aware
+ * low-precision factorization.
  * slqr_poll returns SLQR_PENDING until the request is done, then SLQR_OK with
  * *out filled (out->status is the request's own status) and forgets the
  * ticket; SLQR_ENOTFOUND for an unknown or already collected ticket.
@@ -543,7 +560,7 @@ typedef struct {
   const double *b;      /* host, m doubles (SOLVE, FACTOR_SOLVE) */
   double *x;            /* host, n doubles, written at completion */
   uint64_t handle;      /* SOLVE, RELEASE */
-  int prec;             /* SLQR_FP64 or SLQR_FP32 */
+  int prec;             /* SLQR_FP64, SLQR_FP32, SLQR_TF32 or SLQR_BF16X3 */
   int structure;        /* SLQR_DENSE, or SLQR_STACKED: A = [L^T; C] with an
                            upper-triangular top n x n block whose strictly lower
                            part is zero (factored as slqr_factor_stacked) */
@@ -553,11 +570,13 @@ typedef struct {
 #define SLQR_STACKED 1
 
 typedef struct {
-  int status;           /* SLQR_OK, SLQR_ERANK, SLQR_ENOCONV, SLQR_EBUSY, SLQR_ENOTFOUND, ... */
+  int status;           /* SLQR_OK, SLQR_FALLBACK, SLQR_ERANK, SLQR_ENOCONV, SLQR_EBUSY,
+                           SLQR_ENOTFOUND, ... */
   uint64_t handle;      /* FACTOR: the handle of the resident factorization */
-  double residual_norm; /* solves: ||b - A x|| (FP64: ||(Q^T b)[n:m]||) */
+  double residual_norm; /* solves: FP64 ||(Q^T b)[n:m]||; mixed precision ||b - A x||
+                           from the caller's arrays (NaN for a SOLVE, which has no A) */
   double latency_ms;    /* from slqr_submit to completion */
-  double err;           /* SLQR_FP32: last refinement step ||dx|| / ||x|| */
+  double err;           /* mixed precision: last refinement step ||dx|| / ||x|| */
 } slqr_result;
 
 slqr_status slqr_submit(slqr_ctx *ctx, const slqr_request *req, uint64_t *ticket);
@@ -618,6 +637,23 @@ int slqr_noalloc_max_cols(void);
 int slqr_profile(slqr_ctx *ctx, int enable);
 slqr_status slqr_profile_read(slqr_ctx *ctx, int kernel, double *ms, long long *launches,
                               double *flops);
+
+/*
+ * Measured arithmetic peaks of the device (a diagnostic for rooflines; no
+ * counterpart in the paper).  Synchronous: waits for the device, then times a
+ * probe kernel with CUDA events (best of three launches after a warm-up) and
+ * writes its rate in TFLOP/s to *tflops (HOST).
+ *   SLQR_PEAK_FP64_FMA  register-resident FP64 FMA chains on every SM (the FP64
+ *                       pipe that the FP64 factorization and update kernels use)
+ *   SLQR_PEAK_TF32_TC   tcgen05 kind::tf32 MMAs (M = 128, N = 64, K = 8, the
+ *                       shape of the TF32 trailing update) issued back to back by
+ *                       one CTA per SM on shared-memory operands
+ * Errors: SLQR_EINVAL (kind, NULL pointers), SLQR_ECUDA.  A probe's bounded
+ * wait that gives up records SLQR_ETIMEOUT in the status word (slqr_sync).
+ */
+#define SLQR_PEAK_FP64_FMA 0
+#define SLQR_PEAK_TF32_TC  1
+slqr_status slqr_measure_peak(slqr_ctx *ctx, int kind, double *tflops);
 
 /* Number of CUDA kernels this context has launched since it was created. */
 long long slqr_launch_count(slqr_ctx *ctx);

@@ -51,7 +51,8 @@ class SlqrRequest(ctypes.Structure):
 class SlqrMixedOpts(ctypes.Structure):
     _fields_ = [("refine", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
                 ("gmres_max_iters", ctypes.c_int), ("gmres_restart", ctypes.c_int),
-                ("gmres_tol", ctypes.c_double), ("fp64_fallback", ctypes.c_int)]
+                ("gmres_tol", ctypes.c_double), ("fp64_fallback", ctypes.c_int),
+                ("structure", ctypes.c_int)]
 
 
 class SlqrMixedInfo(ctypes.Structure):
@@ -91,6 +92,7 @@ SIGNATURES = [
     ("slqr_profile_read", _c_int, [_vp, _c_int, ctypes.POINTER(_dbl),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_dbl)]),
     ("slqr_launch_count", ctypes.c_longlong, [_vp]),
+    ("slqr_measure_peak", _c_int, [_vp, _c_int, ctypes.POINTER(_dbl)]),
     ("slqr_factor_noalloc", _c_int, [_c_int, _c_int, _vp, _c_int, _vp, _vp, _vp, _vp]),
     ("slqr_batch_factor", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                    ctypes.POINTER(_vp), ctypes.POINTER(_c_int),
@@ -245,6 +247,16 @@ def slqr_profile_read(ctx: int, kernel: int):
     return ms.value, n.value, fl.value
 
 
+SLQR_PEAK_FP64_FMA, SLQR_PEAK_TF32_TC = 0, 1
+
+
+def slqr_measure_peak(ctx, kind: int):
+    """Returns (status, TFLOP/s) of the device's FP64 FMA or TF32 tensor-core probe."""
+    v = _dbl()
+    st = _lib.slqr_measure_peak(ctx, kind, ctypes.byref(v))
+    return st, v.value
+
+
 def slqr_launch_count(ctx: int) -> int:
     return _lib.slqr_launch_count(ctx)
 
@@ -363,10 +375,10 @@ def slqr_lstsq_mixed(ctx, m, n, A, lda, b, x, prec, max_iter, tol, stream):
 
 def slqr_lstsq_mixed_ex(ctx, m, n, A, lda, b, x, prec, stream, refine=SLQR_REFINE_AUTO,
                         max_sweeps=0, tol=0.0, gmres_max_iters=0, gmres_restart=0,
-                        gmres_tol=0.0, fp64_fallback=0):
+                        gmres_tol=0.0, fp64_fallback=0, structure=0):
     """Returns (status, info) with info a dict of the SlqrMixedInfo fields."""
     opts = SlqrMixedOpts(refine, max_sweeps, tol, gmres_max_iters, gmres_restart, gmres_tol,
-                         fp64_fallback)
+                         fp64_fallback, structure)
     info = SlqrMixedInfo()
     st = _lib.slqr_lstsq_mixed_ex(ctx, m, n, A, lda, b, x, prec, ctypes.byref(opts),
                                   ctypes.byref(info), stream)

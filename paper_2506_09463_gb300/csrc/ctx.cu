@@ -1,6 +1,7 @@
 // ctx.cu -- context, workspace and status handling of the libslqr C ABI.
 #include "slqr_internal.cuh"
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <new>
@@ -252,6 +253,67 @@ extern "C" slqr_status slqr_set_spin_limit(slqr_ctx *ctx, unsigned polls) {
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   ctx->spin_limit = polls == 0 ? kSpinLimit : polls;
   return SLQR_OK;
+}
+
+namespace slqr {
+
+// FP64 FMA peak probe: register-resident DFMA chains, 8 independent ones per
+// thread (enough to cover the pipe's latency), 4 CTAs of 256 threads per SM.
+__global__ void __launch_bounds__(256)
+dfma_peak_kernel(double *out, int iters, double a, double b) {
+  double acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = fma(acc[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += acc[i];
+  if (s == 12345.678) out[0] = s;       // keeps the chains live; never true in practice
+}
+
+slqr_status measure_tf32_peak(slqr_ctx *ctx, double *tflops);
+
+static slqr_status measure_fp64_peak(slqr_ctx *ctx, double *tflops) {
+  const int iters = 1 << 14, threads = 256, grid = 4 * ctx->num_sms;
+  double *out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&out, sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, 0);
+    dfma_peak_kernel<<<grid, threads>>>(out, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, 0);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "FP64 peak probe: %s", cudaGetErrorString(e));
+  *tflops = 2.0 * 8.0 * iters * (double)threads * grid / (best * 1e-3) / 1e12;
+  return SLQR_OK;
+}
+
+}  // namespace slqr
+
+extern "C" slqr_status slqr_measure_peak(slqr_ctx *ctx, int kind, double *tflops) {
+  if (!ctx || !tflops) return SLQR_EINVAL;
+  NvtxRange nvtx_range("slqr_measure_peak");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "peak probe: %s", cudaGetErrorString(e));
+  if (kind == SLQR_PEAK_FP64_FMA) return measure_fp64_peak(ctx, tflops);
+  if (kind == SLQR_PEAK_TF32_TC) return measure_tf32_peak(ctx, tflops);
+  return fail(ctx, SLQR_EINVAL, "peak kind %d", kind);
 }
 
 extern "C" const char *slqr_last_error(slqr_ctx *ctx) {

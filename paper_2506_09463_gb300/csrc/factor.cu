@@ -1144,9 +1144,10 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
 }
 
 slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
-                       cudaStream_t stream) {
-  if (panel_width(m, n) == 32) return factor_impl<float, 32>(ctx, m, n, A, lda, up, wy, stream);
-  return factor_impl<float, 64>(ctx, m, n, A, lda, up, wy, stream);
+                       cudaStream_t stream, int ntop) {
+  if (panel_width(m, n) == 32)
+    return factor_impl<float, 32>(ctx, m, n, A, lda, up, wy, stream, ntop);
+  return factor_impl<float, 64>(ctx, m, n, A, lda, up, wy, stream, ntop);
 }
 
 

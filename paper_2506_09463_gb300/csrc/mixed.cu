@@ -1108,128 +1108,162 @@ static slqr_status fp64_fallback(slqr_ctx *ctx, int m, int n, const double *A, i
   return SLQR_OK;
 }
 
-static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A, int lda,
-                                    const double *b, double *x, int prec,
-                                    const slqr_mixed_opts &o, slqr_mixed_info *info,
-                                    cudaStream_t s) {
-  const int nb = panel_width(m, n);
-  const int K = num_reflectors(m, n);
-  const int np = num_panels(K, nb);
-  const bool use_gmres = o.refine != SLQR_REFINE_BJORCK;
-  const bool use_bjorck = o.refine != SLQR_REFINE_GMRES;
-  MixedSolve ms;
-  ms.ctx = ctx; ms.s = s; ms.m = m; ms.n = n; ms.lda = lda; ms.nb = nb; ms.K = K; ms.np = np;
-  ms.A = A; ms.b = b; ms.x = x;
-  ms.chunks = (n + kColChunk - 1) / kColChunk;
-  ms.ublocks = (n + 255) / 256;
-  // mixed-path buffers (a workspace of their own: the factorization uses ctx->ws)
+// Bytes of the persistent state of one low-precision factorization (kept by
+// the request loop for resident mixed-precision handles): the FP32 copy of
+// A D (columns padded to 128 bytes), up, the compact-WY store, the column
+// scales D and the explicit T of every panel.
+size_t mixed_state_bytes(int m, int n) {
+  const int nb = panel_width(m, n), K = num_reflectors(m, n), np = num_panels(K, nb);
+  const int lda32 = (m + 31) / 32 * 32;
+  size_t b = 0;
+  b += align_up((size_t)lda32 * n * sizeof(float), 256);
+  b += align_up((size_t)n * sizeof(double), 256);
+  b += align_up(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double), 256);
+  b += align_up((size_t)n * sizeof(double), 256);
+  b += align_up((size_t)std::max(np, 1) * nb * (nb + 1) * sizeof(float), 256);
+  return b;
+}
+
+static void mixed_state_carve(char *mem, int m, int n, int prec, MixedFactorState *fs) {
+  fs->m = m; fs->n = n; fs->prec = prec;
+  fs->nb = panel_width(m, n); fs->K = num_reflectors(m, n); fs->np = num_panels(fs->K, fs->nb);
+  fs->lda32 = (m + 31) / 32 * 32;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char *p = mem + off; off += align_up(bytes, 256); return p; };
+  fs->A32 = (float *)take((size_t)fs->lda32 * n * sizeof(float));
+  fs->up = (double *)take((size_t)n * sizeof(double));
+  fs->wy = (double *)take(wy_panel_doubles(fs->nb) * (size_t)std::max(fs->np, 1) * sizeof(double));
+  fs->colscale = (double *)take((size_t)n * sizeof(double));
+  fs->Tm32 = (float *)take((size_t)std::max(fs->np, 1) * fs->nb * (fs->nb + 1) * sizeof(float));
+}
+
+static size_t factor_scratch_bytes(int m, int n, int prec) {
+  const int lda32 = (m + 31) / 32 * 32;
+  return (prec == SLQR_BF16X3) ? 2 * align_up((size_t)lda32 * n * 2, 256) : 0;
+}
+
+// The low-precision factorization of A D into the state `fs` (memory carved
+// already); `scratch` holds the BF16 shadows of SLQR_BF16X3.
+static slqr_status factor_phase(slqr_ctx *ctx, const double *A, int lda, MixedFactorState &fs,
+                                char *scratch, cudaStream_t s) {
+  const int m = fs.m, n = fs.n, prec = fs.prec;
+  col_scale_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, fs.colscale);
+  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, fs.colscale, fs.A32, fs.lda32);
+  ctx->launch_count += 2;
+  ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
+  if (prec == SLQR_BF16X3) {
+    ctx->sh_hi = scratch;
+    ctx->sh_lo = scratch + align_up((size_t)fs.lda32 * n * 2, 256);
+    split_bf16_region(fs.A32, fs.lda32, 0, m, 0, n, ctx->sh_hi, ctx->sh_lo, ctx->num_sms, s);
+  }
+  slqr_status st = factor_f32(ctx, m, n, fs.A32, fs.lda32, fs.up, fs.wy, s, fs.ntop);
+  ctx->tc_mode = 0;
+  ctx->sh_hi = ctx->sh_lo = nullptr;
+  if (st != SLQR_OK) return st;
+  if (fs.np > 0) {
+    tmat_kernel<float><<<fs.np, 64, 0, s>>>(fs.wy, fs.nb, fs.K, fs.Tm32);
+    ++ctx->launch_count;
+  }
+  return check_launch(ctx, "mixed factorization");
+}
+
+// Layout of the refinement's scratch (carved from `base` when not NULL).
+static size_t refine_scratch(slqr_ctx *ctx, const MixedFactorState &fs, bool use_gmres,
+                             int restart, char *base, MixedSolve *ms) {
+  const int m = fs.m, n = fs.n, nb = fs.nb, np = fs.np;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t of = off; off = align_up(off + bytes, 256); return of; };
-  ms.lda32 = (m + 31) / 32 * 32;   // 128-byte aligned columns (TMA-friendly)
-  const size_t o_a32 = take((size_t)ms.lda32 * n * sizeof(float));
-  const size_t o_up = take((size_t)n * sizeof(double));
-  const size_t o_wy = take(wy_panel_doubles(nb) * (size_t)std::max(np, 1) * sizeof(double));
+  const int chunks = (n + kColChunk - 1) / kColChunk, ublocks = (n + 255) / 256;
+  const size_t N = (size_t)m + n;
+  const int max_blocks = std::max(ublocks, std::min(4 * ctx->num_sms, (int)((N + 255) / 256)));
+  const int qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
+  const int qv_P = (m + qv_R - 1) / qv_R;
+  const int qv_R64 = std::max(kQvRows64, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
+  const int qv_P64 = (m + qv_R64 - 1) / qv_R64;
+  const size_t t_elems = (size_t)std::max(np, 1) * nb * (nb + 1);
+  const int nblk64 = (n + 63) / 64;
   const size_t o_r = take((size_t)m * sizeof(double));
   const size_t o_f = take((size_t)m * sizeof(float));
   const size_t o_g = take((size_t)n * sizeof(float));
   const size_t o_e = take((size_t)m * sizeof(float));
-  const size_t o_part = take((size_t)ms.chunks * m * sizeof(double));
-  const size_t N = (size_t)m + n;
-  const int max_blocks = std::max(ms.ublocks, std::min(4 * ctx->num_sms, (int)((N + 255) / 256)));
+  const size_t o_part = take((size_t)chunks * m * sizeof(double));
   const size_t o_max = take((size_t)2 * max_blocks * sizeof(double));
   const size_t o_flag = take(sizeof(int));
-  // fused Q application: rows per CTA, explicit T per panel, partials, barrier
-  // (a multiple of 64 rows: every slice starts 16-byte aligned for the vector loads)
-  ms.qv_R = std::max(kQvRows, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
-  ms.qv_P = (m + ms.qv_R - 1) / ms.qv_R;
-  ms.qv_R64 = std::max(kQvRows64, ((m + ctx->num_sms - 1) / ctx->num_sms + 63) / 64 * 64);
-  ms.qv_P64 = (m + ms.qv_R64 - 1) / ms.qv_R64;
-  const size_t t_elems = (size_t)std::max(np, 1) * nb * (nb + 1);
-  const size_t o_tm = take(t_elems * sizeof(float));
-  const size_t o_qpart = take((size_t)2 * ms.qv_P * nb * sizeof(float));
+  const size_t o_qpart = take((size_t)2 * qv_P * nb * sizeof(float));
   const size_t o_bar = take(256);
-  // BF16 hi / lo shadows of the FP32 matrix (SLQR_BF16X3)
-  const size_t sh_bytes = (prec == SLQR_BF16X3) ? (size_t)ms.lda32 * n * 2 : 0;
-  const size_t o_shh = take(sh_bytes);
-  const size_t o_shl = take(sh_bytes);
-  // GMRES-IR: FP64 T and partials, the Krylov basis, the Hessenberg column
-  int gm_iters = o.gmres_max_iters > 0 ? o.gmres_max_iters : 300;
-  int restart = o.gmres_restart > 0 ? o.gmres_restart : std::min(gm_iters, 200);
-  restart = std::max(1, std::min(restart, kMaxKrylov));
+  const size_t o_dr = take(2 * sizeof(double));
   const size_t o_tm64 = use_gmres ? take(t_elems * sizeof(double)) : 0;
-  const size_t o_qpart64 = use_gmres ? take((size_t)2 * ms.qv_P64 * nb * sizeof(double)) : 0;
+  const size_t o_qpart64 = use_gmres ? take((size_t)2 * qv_P64 * nb * sizeof(double)) : 0;
   const size_t o_vk = use_gmres ? take((size_t)(restart + 1) * N * sizeof(double)) : 0;
   const size_t o_h = use_gmres ? take((size_t)2 * (restart + 2) * sizeof(double)) : 0;
   const size_t o_y = use_gmres ? take((size_t)restart * sizeof(double)) : 0;
-  const int nblk64 = (n + 63) / 64;
   const size_t o_rinv = use_gmres ? take((size_t)nblk64 * 4096 * sizeof(double)) : 0;
   const size_t o_zblk = use_gmres ? take((size_t)nblk64 * sizeof(int)) : 0;
-  const size_t o_dr = take(2 * sizeof(double));
-  const size_t o_cs = take((size_t)n * sizeof(double));
-  slqr_status st = ensure_workspace2(ctx, off);
-  if (st != SLQR_OK) return st;
-  char *base = (char *)ctx->ws2.ptr;
-  ms.A32 = (float *)(base + o_a32);
-  ms.up = (double *)(base + o_up);
-  ms.wy = (double *)(base + o_wy);
-  ms.r = (double *)(base + o_r);
-  ms.f32 = (float *)(base + o_f);
-  ms.g32 = (float *)(base + o_g);
-  ms.e32 = (float *)(base + o_e);
-  ms.part = (double *)(base + o_part);
-  ms.maxima = (double *)(base + o_max);
-  ms.zero_flag = (int *)(base + o_flag);
-  ms.Tm32 = (float *)(base + o_tm);
-  ms.qpart32 = (float *)(base + o_qpart);
-  ms.qbar = (unsigned *)(base + o_bar);
-  ms.drange = (double *)(base + o_dr);
-  ms.colscale = (double *)(base + o_cs);
-  if (use_gmres) {
-    ms.Tm64 = (double *)(base + o_tm64);
-    ms.qpart64 = (double *)(base + o_qpart64);
-    ms.Vk = (double *)(base + o_vk);
-    ms.hdev = (double *)(base + o_h);
-    ms.ydev = (double *)(base + o_y);
-    ms.Rinv = (double *)(base + o_rinv);
-    ms.zblk = (int *)(base + o_zblk);
-    ms.restart = restart;
-  }
-  cudaError_t e = cudaFuncSetAttribute(qvec_kernel<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)qvec_smem_bytes<float>(nb, ms.qv_R));
-  if (e == cudaSuccess && use_gmres)
-    e = cudaFuncSetAttribute(qvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)qvec_smem_bytes<double>(nb, ms.qv_R64));
-  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
-
-  // the FP32 factorization, of A D
-  col_scale_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, m, n, ms.colscale);
-  to_f32_kernel<<<4 * ctx->num_sms, 256, 0, s>>>(A, lda, m, n, ms.colscale, ms.A32, ms.lda32);
-  ctx->launch_count += 2;
-  ctx->tc_mode = (prec == SLQR_TF32) ? 1 : (prec == SLQR_BF16X3) ? 2 : 0;
-  if (prec == SLQR_BF16X3) {
-    ctx->sh_hi = base + o_shh;
-    ctx->sh_lo = base + o_shl;
-    split_bf16_region(ms.A32, ms.lda32, 0, m, 0, n, ctx->sh_hi, ctx->sh_lo, ctx->num_sms, s);
-  }
-  st = factor_f32(ctx, m, n, ms.A32, ms.lda32, ms.up, ms.wy, s);
-  ctx->tc_mode = 0;
-  ctx->sh_hi = ctx->sh_lo = nullptr;
-  if (st != SLQR_OK) return st;
-  if (np > 0) {
-    tmat_kernel<float><<<np, 64, 0, s>>>(ms.wy, nb, K, ms.Tm32);
-    ++ctx->launch_count;
+  if (base && ms) {
+    ms->ctx = ctx; ms->m = m; ms->n = n; ms->nb = nb; ms->K = fs.K; ms->np = np;
+    ms->lda32 = fs.lda32; ms->chunks = chunks; ms->ublocks = ublocks;
+    ms->A32 = fs.A32; ms->up = fs.up; ms->wy = fs.wy; ms->colscale = fs.colscale;
+    ms->Tm32 = fs.Tm32;
+    ms->qv_R = qv_R; ms->qv_P = qv_P; ms->qv_R64 = qv_R64; ms->qv_P64 = qv_P64;
+    ms->r = (double *)(base + o_r);
+    ms->f32 = (float *)(base + o_f);
+    ms->g32 = (float *)(base + o_g);
+    ms->e32 = (float *)(base + o_e);
+    ms->part = (double *)(base + o_part);
+    ms->maxima = (double *)(base + o_max);
+    ms->zero_flag = (int *)(base + o_flag);
+    ms->qpart32 = (float *)(base + o_qpart);
+    ms->qbar = (unsigned *)(base + o_bar);
+    ms->drange = (double *)(base + o_dr);
     if (use_gmres) {
-      tmat_kernel<double><<<np, 64, 0, s>>>(ms.wy, nb, K, ms.Tm64);
-      ++ctx->launch_count;
+      ms->Tm64 = (double *)(base + o_tm64);
+      ms->qpart64 = (double *)(base + o_qpart64);
+      ms->Vk = (double *)(base + o_vk);
+      ms->hdev = (double *)(base + o_h);
+      ms->ydev = (double *)(base + o_y);
+      ms->Rinv = (double *)(base + o_rinv);
+      ms->zblk = (int *)(base + o_zblk);
+      ms->restart = restart;
     }
   }
+  return off;
+}
+
+static int gmres_budget(const slqr_mixed_opts &o) {
+  return o.gmres_max_iters > 0 ? o.gmres_max_iters : 300;
+}
+static int gmres_restart_len(const slqr_mixed_opts &o) {
+  const int it = gmres_budget(o);
+  const int r = o.gmres_restart > 0 ? o.gmres_restart : std::min(it, 200);
+  return std::max(1, std::min(r, kMaxKrylov));
+}
+
+// The refinement of x for b with the low-precision factorization `fs` of the
+// FP64 matrix A (Bjorck sweeps, then or instead GMRES-IR, then the optional
+// FP64 fallback); `scratch` as laid out by refine_scratch.
+static slqr_status refine_phase(slqr_ctx *ctx, const MixedFactorState &fs, const double *A,
+                                int lda, const double *b, double *x, const slqr_mixed_opts &o,
+                                slqr_mixed_info *info, char *scratch, cudaStream_t s) {
+  const int m = fs.m, n = fs.n;
+  const bool use_gmres = o.refine != SLQR_REFINE_BJORCK;
+  const bool use_bjorck = o.refine != SLQR_REFINE_GMRES;
+  MixedSolve ms;
+  refine_scratch(ctx, fs, use_gmres, gmres_restart_len(o), scratch, &ms);
+  ms.s = s; ms.lda = lda; ms.A = A; ms.b = b; ms.x = x;
+  cudaError_t e = cudaFuncSetAttribute(qvec_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)qvec_smem_bytes<float>(fs.nb, ms.qv_R));
+  if (e == cudaSuccess && use_gmres)
+    e = cudaFuncSetAttribute(qvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)qvec_smem_bytes<double>(fs.nb, ms.qv_R64));
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "qvec attribute: %s", cudaGetErrorString(e));
   cudaMemsetAsync(ms.qbar, 0, 256, s);
   cudaMemsetAsync(ms.zero_flag, 0, sizeof(int), s);
+  slqr_status st;
   info->method = SLQR_REFINE_BJORCK;
   int status = SLQR_ENOCONV;
-  double e_cur = HUGE_VAL;
   if (use_bjorck) {
+    double e_cur = HUGE_VAL;
     status = bjorck(ms, o.max_sweeps, o.tol, &info->sweeps, &e_cur);
     info->err = e_cur;
   } else {
@@ -1237,9 +1271,13 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     ++ctx->launch_count;
   }
   if (status == SLQR_ENOCONV && use_gmres) {
+    if (fs.np > 0) {
+      tmat_kernel<double><<<fs.np, 64, 0, s>>>(fs.wy, fs.nb, fs.K, ms.Tm64);
+      ++ctx->launch_count;
+    }
     // condition estimate from the diagonal of R: the FP64 noise level that a
     // converged refinement stalls at is about kappa * u
-    diag_range_kernel<<<1, 256, 0, s>>>(ms.A32, ms.lda32, n, ms.drange);
+    diag_range_kernel<<<1, 256, 0, s>>>(fs.A32, fs.lda32, n, ms.drange);
     ++ctx->launch_count;
     double dr[2] = {0.0, 0.0};
     e = cudaMemcpyAsync(dr, ms.drange, sizeof(dr), cudaMemcpyDeviceToHost, s);
@@ -1248,7 +1286,7 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     const double kappa_est = (dr[1] > 0.0) ? dr[0] / dr[1] : HUGE_VAL;
     // the FP64 inverses of R's diagonal blocks, once for all the triangular
     // solves of the preconditioner
-    diag_inv_kernel<<<nblk64, 64, 0, s>>>(ms.A32, ms.lda32, n, ms.Rinv, ms.zblk);
+    diag_inv_kernel<<<(n + 63) / 64, 64, 0, s>>>(fs.A32, fs.lda32, n, ms.Rinv, ms.zblk);
     ++ctx->launch_count;
     info->kappa_est = kappa_est;
     const double noise = std::max(kStallOk, 100.0 * kappa_est * std::ldexp(1.0, -53));
@@ -1259,12 +1297,11 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     }
     GmresResult gr;
     const double inner_tol = o.gmres_tol > 0.0 ? o.gmres_tol : 1e-10;
-    status = gmres_ir(ms, o.tol, gm_iters, inner_tol, noise, &gr);
+    status = gmres_ir(ms, o.tol, gmres_budget(o), inner_tol, noise, &gr);
     info->method = SLQR_REFINE_GMRES;
     info->gmres_steps = gr.steps;
     info->gmres_iters = gr.iters;
     info->err = gr.err;
-    e_cur = gr.err;
   }
   st = check_launch(ctx, "lstsq_mixed");
   if (st != SLQR_OK) return st;
@@ -1288,6 +1325,54 @@ static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A
     fail(ctx, status, status == SLQR_ENOCONV ? "refinement did not reach its tolerance"
                                              : "R has an exact zero on its diagonal");
   return status;
+}
+
+static slqr_status lstsq_mixed_impl(slqr_ctx *ctx, int m, int n, const double *A, int lda,
+                                    const double *b, double *x, int prec,
+                                    const slqr_mixed_opts &o, slqr_mixed_info *info,
+                                    cudaStream_t s) {
+  // the state first, then the larger of the two phases' scratch, in one
+  // workspace of the context (the factorization itself uses ctx->ws)
+  const bool use_gmres = o.refine != SLQR_REFINE_BJORCK;
+  const size_t sbytes = align_up(mixed_state_bytes(m, n), 256);
+  MixedFactorState fs;
+  mixed_state_carve(nullptr, m, n, prec, &fs);     // sizes only
+  const size_t rbytes = refine_scratch(ctx, fs, use_gmres, gmres_restart_len(o), nullptr, nullptr);
+  const size_t fbytes = factor_scratch_bytes(m, n, prec);
+  slqr_status st = ensure_workspace2(ctx, sbytes + std::max(rbytes, fbytes));
+  if (st != SLQR_OK) return st;
+  char *base = (char *)ctx->ws2.ptr;
+  mixed_state_carve(base, m, n, prec, &fs);
+  fs.ntop = (o.structure == SLQR_STACKED) ? n : 0;
+  st = factor_phase(ctx, A, lda, fs, base + sbytes, s);
+  if (st != SLQR_OK) return st;
+  return refine_phase(ctx, fs, A, lda, b, x, o, info, base + sbytes, s);
+}
+
+// Internal entry points for the request loop (resident mixed factorizations).
+slqr_status mixed_factor_into(slqr_ctx *ctx, int m, int n, const double *A, int lda, int prec,
+                              int ntop, void *state_mem, MixedFactorState *fs, cudaStream_t s) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  slqr_status st = ensure_workspace2(ctx, std::max<size_t>(factor_scratch_bytes(m, n, prec), 256));
+  if (st != SLQR_OK) return st;
+  mixed_state_carve((char *)state_mem, m, n, prec, fs);
+  fs->ntop = ntop;
+  return factor_phase(ctx, A, lda, *fs, (char *)ctx->ws2.ptr, s);
+}
+
+slqr_status mixed_solve_with(slqr_ctx *ctx, const MixedFactorState &fs, const double *A, int lda,
+                             const double *b, double *x, const slqr_mixed_opts &o,
+                             slqr_mixed_info *info, cudaStream_t s) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  const bool use_gmres = o.refine != SLQR_REFINE_BJORCK;
+  const size_t rbytes = refine_scratch(ctx, fs, use_gmres, gmres_restart_len(o), nullptr, nullptr);
+  slqr_status st = ensure_workspace2(ctx, rbytes);
+  if (st != SLQR_OK) return st;
+  return refine_phase(ctx, fs, A, lda, b, x, o, info, (char *)ctx->ws2.ptr, s);
 }
 
 static slqr_status check_mixed_args(slqr_ctx *ctx, int m, int n, const double *A, int lda,
@@ -1340,6 +1425,8 @@ extern "C" slqr_status slqr_lstsq_mixed_ex(slqr_ctx *ctx, int m, int n, const do
     return fail(ctx, SLQR_EINVAL, "refine = %d is not a refinement method", o.refine);
   if (o.gmres_restart > kMaxKrylov)
     return fail(ctx, SLQR_EINVAL, "gmres_restart = %d above %d", o.gmres_restart, kMaxKrylov);
+  if (o.structure != SLQR_DENSE && o.structure != SLQR_STACKED)
+    return fail(ctx, SLQR_EINVAL, "structure = %d", o.structure);
   if (o.max_sweeps < 1) o.max_sweeps = 30;
   if (!(o.tol > 0.0)) o.tol = 1e-14;
   cudaError_t e = cudaSetDevice(ctx->device);

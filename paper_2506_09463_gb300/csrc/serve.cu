@@ -25,8 +25,18 @@
 //  * residency: a FACTOR request keeps its factorization (A in H12 form, up,
 //    compact-WY store) on the device under a handle until RELEASE; SOLVE
 //    requests reuse it (Q^T b, back-substitution);
-//  * completion is observed with CUDA events; the solution is copied into
-//    the caller's host buffer and the request's latency recorded.
+//  * mixed precision: FP32 requests of the batch size class join the batched
+//    FP32 launch; every other mixed-precision request (SLQR_FP32 with
+//    m > 512, SLQR_TF32, SLQR_BF16X3, and SOLVE on a mixed-precision handle)
+//    goes to a mixed lane: a helper thread with its own context and stream
+//    that runs the synchronous mixed-precision solve (low-precision
+//    factorization, refinement against the FP64 A, the FP64 fallback when the
+//    refinement fails, flagged as SLQR_FALLBACK).  A mixed FACTOR keeps the
+//    library's FP64 copy of A and the low-precision factorization resident
+//    (both counted in the HBM budget) for later SOLVE requests;
+//  * completion is observed with CUDA events (with a host flag for the mixed
+//    lanes); the solution is copied into the caller's host buffer and the
+//    request's latency recorded.
 #include "slqr_internal.cuh"
 
 #include <algorithm>
@@ -36,6 +46,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -47,6 +58,8 @@ using Clock = std::chrono::steady_clock;
 struct Resident {
   int m = 0, n = 0;
   bool stacked = false;          // [L^T; C] factorization (slqr_factor_stacked)
+  bool mixed = false;            // low-precision factorization: dA is the FP64 copy of A and
+  MixedFactorState fs;           //   fs the state of its factorization (mixed_factor_into)
   double *dA = nullptr, *dup = nullptr, *dwy = nullptr;
   size_t bytes = 0;
   cudaEvent_t ready = nullptr;   // the factorization is complete after this
@@ -64,11 +77,15 @@ struct Req {
   size_t bytes = 0;              // owned bytes (freed when done, unless resident)
   uint64_t handle = 0;           // SOLVE/RELEASE: the handle used; FACTOR: the one made
   bool small = false;
+  bool mixed = false;            // runs on a mixed lane
+  double *dx = nullptr;          // mixed lanes: the solution (n doubles)
+  MixedFactorState fs;           // mixed FACTOR: the state made (in the request's block)
 };
 
 struct Unit {                    // one launch sequence whose completion is watched
   std::vector<Req *> reqs;
   cudaEvent_t done = nullptr;
+  std::shared_ptr<std::atomic<int>> host_done;   // mixed lanes: set by the helper thread
   cudaStream_t stream = nullptr;
   int *d_status = nullptr;       // batch: per-problem status
   double *d_err = nullptr;
@@ -96,7 +113,27 @@ struct Server {
   cudaMemPool_t pool = nullptr;
   std::vector<Unit> inflight;
   std::vector<Req *> small_ready[2];              // admitted small requests, per precision
+  // mixed lanes: helper threads, each with a context, a stream and a job queue
+  struct Lane {
+    slqr_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread thread;
+    std::deque<std::pair<Req *, std::shared_ptr<std::atomic<int>>>> jobs;
+    int busy = 0;                                  // jobs queued or running (worker's view)
+  };
+  std::vector<Lane> lanes;
+  std::mutex lane_mu;
+  std::condition_variable lane_cv;
+  bool lanes_stopping = false;
 };
+
+// A request served on a mixed lane: every mixed-precision request except the
+// FP32 FACTOR_SOLVE of the batch size class, and SOLVE on a mixed handle.
+static bool is_mixed_lane(const slqr_request &r) {
+  if (r.kind != SLQR_REQ_FACTOR && r.kind != SLQR_REQ_FACTOR_SOLVE) return false;
+  if (r.prec == SLQR_FP64) return false;
+  return !(r.prec == SLQR_FP32 && r.kind == SLQR_REQ_FACTOR_SOLVE && r.m <= slqr_batch_max_rows());
+}
 
 static const size_t kAlign = 256;
 // Smallest m * n a batch-sized problem needs to be sent down the stream path
@@ -119,6 +156,13 @@ static void pool_free(double *p, cudaStream_t s) {
 }
 
 static size_t request_bytes(const slqr_request &r) {
+  if (is_mixed_lane(r)) {
+    // the FP64 copy of A, the low-precision state, b and x
+    size_t b = align_up((size_t)r.m * r.n * 8, kAlign) + align_up(mixed_state_bytes(r.m, r.n), kAlign);
+    if (r.kind == SLQR_REQ_FACTOR_SOLVE)
+      b += align_up((size_t)r.m * 8, kAlign) + align_up((size_t)r.n * 8, kAlign);
+    return b;
+  }
   switch (r.kind) {
     case SLQR_REQ_FACTOR:
     case SLQR_REQ_FACTOR_SOLVE: {
@@ -152,8 +196,13 @@ static void deliver_solution(Req &q, int m, int n) {
     return;
   }
   if (q.r.x) std::memcpy(q.r.x, hb.data(), sizeof(double) * n);
+  if (q.mixed) return;            // the mixed lane has set the residual norm
   double s = 0.0;
-  if (q.r.prec == SLQR_FP32) {
+  if (q.r.prec != SLQR_FP64 && !q.r.A) {
+    q.res.residual_norm = std::nan("");            // mixed SOLVE: A is not at hand
+    return;
+  }
+  if (q.r.prec != SLQR_FP64) {
     for (int i = 0; i < m; ++i) {
       double ri = q.r.b[i];
       for (int j = 0; j < n; ++j) ri -= q.r.A[(size_t)i + (size_t)j * q.r.lda] * hb[j];
@@ -163,6 +212,104 @@ static void deliver_solution(Req &q, int m, int n) {
     for (int i = n; i < m; ++i) s += hb[i] * hb[i];
   }
   q.res.residual_norm = std::sqrt(s);
+}
+
+// Body of one mixed-lane job (runs in the lane's helper thread): the
+// low-precision factorization and/or the refinement, synchronous on the lane's
+// stream; the solution ends in q.db[0:n] for deliver_solution.
+static void run_mixed_job(Server *S, Server::Lane &L, Req &q) {
+  const slqr_request &r = q.r;
+  slqr_mixed_opts o{};
+  o.fp64_fallback = 1;
+  slqr_mixed_info info{};
+  info.err = HUGE_VAL;
+  slqr_status st = SLQR_OK;
+  int m = r.m, n = r.n;
+  if (r.kind == SLQR_REQ_SOLVE) {
+    Resident *h = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      h = &S->handles[q.handle];     // kept alive by its user count
+    }
+    m = h->m;
+    n = h->n;
+    cudaStreamWaitEvent(L.stream, h->ready, 0);
+    st = mixed_solve_with(L.ctx, h->fs, h->dA, h->m, q.db, q.dx, o, &info, L.stream);
+  } else {
+    void *state = (char *)q.dA + align_up((size_t)m * n * 8, kAlign);
+    const int ntop = (r.structure == SLQR_STACKED) ? n : 0;
+    st = mixed_factor_into(L.ctx, m, n, q.dA, m, r.prec, ntop, state, &q.fs, L.stream);
+    if (st == SLQR_OK && r.kind == SLQR_REQ_FACTOR_SOLVE)
+      st = mixed_solve_with(L.ctx, q.fs, q.dA, m, q.db, q.dx, o, &info, L.stream);
+  }
+  const bool solved = q.db && (st == SLQR_OK || st == SLQR_FALLBACK || st == SLQR_ERANK);
+  if (solved)
+    cudaMemcpyAsync(q.db, q.dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, L.stream);
+  if (cudaStreamSynchronize(L.stream) != cudaSuccess) {
+    cudaGetLastError();
+    st = SLQR_ECUDA;
+  }
+  // ||b - A x|| from the caller's host arrays (here, not in the worker loop);
+  // a SOLVE request has no A at hand
+  double res = std::nan("");
+  if (solved && st != SLQR_ECUDA && r.A) {
+    std::vector<double> x(n);
+    if (cudaMemcpy(x.data(), q.dx, sizeof(double) * n, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      double acc = 0.0;
+      for (int i = 0; i < m; ++i) {
+        double ri = r.b[i];
+        for (int j = 0; j < n; ++j) ri -= r.A[(size_t)i + (size_t)j * r.lda] * x[j];
+        acc += ri * ri;
+      }
+      res = std::sqrt(acc);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  q.res.status = st;
+  q.res.err = info.err;
+  q.res.residual_norm = res;
+}
+
+static void lane_main(Server *S, int li) {
+  cudaSetDevice(S->device);
+  Server::Lane &L = S->lanes[li];
+  for (;;) {
+    std::pair<Req *, std::shared_ptr<std::atomic<int>>> job;
+    {
+      std::unique_lock<std::mutex> lk(S->lane_mu);
+      S->lane_cv.wait(lk, [&] { return S->lanes_stopping || !L.jobs.empty(); });
+      if (L.jobs.empty()) break;                   // stopping, nothing left
+      job = L.jobs.front();
+      L.jobs.pop_front();
+    }
+    run_mixed_job(S, L, *job.first);
+    job.second->store(1);
+  }
+}
+
+// Hand a request to the least busy mixed lane (its copies in are already
+// enqueued on that lane's stream).
+static void dispatch_mixed(Server *S, Req &q, int li) {
+  Unit u;
+  u.reqs.push_back(&q);
+  u.stream = S->lanes[li].stream;
+  u.host_done = std::make_shared<std::atomic<int>>(0);
+  S->lanes[li].busy++;
+  {
+    std::lock_guard<std::mutex> lk(S->lane_mu);
+    S->lanes[li].jobs.emplace_back(&q, u.host_done);
+  }
+  S->lane_cv.notify_all();
+  S->inflight.push_back(u);
+}
+
+static int least_busy_lane(Server *S) {
+  int best = 0;
+  for (int i = 1; i < (int)S->lanes.size(); ++i)
+    if (S->lanes[i].busy < S->lanes[best].busy) best = i;
+  return best;
 }
 
 // Admit pending requests in arrival order while the budget allows.
@@ -194,6 +341,30 @@ static void admit(Server *S) {
           S->pending.pop_front();
           continue;
         }
+      }
+      if (h->mixed) {
+        // b and x of a refinement with the resident low-precision factorization
+        const size_t bytes = align_up((size_t)h->m * 8, kAlign) + align_up((size_t)h->n * 8, kAlign);
+        if (budget && S->used_bytes + bytes > budget) break;
+        const int li = least_busy_lane(S);
+        cudaStream_t s = S->lanes[li].stream;
+        q.db = pool_alloc(S, bytes, s);
+        if (!q.db) break;
+        q.dx = (double *)((char *)q.db + align_up((size_t)h->m * 8, kAlign));
+        q.bytes = bytes;
+        q.mixed = true;
+        S->used_bytes += bytes;
+        cudaMemcpyAsync(q.db, r.b, sizeof(double) * h->m, cudaMemcpyHostToDevice, s);
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          h->users++;
+          q.handle = r.handle;
+          q.state = 1;
+          q.res.status = SLQR_OK;
+        }
+        dispatch_mixed(S, q, li);
+        S->pending.pop_front();
+        continue;
       }
       const size_t bytes = align_up((size_t)h->m * 8, kAlign);
       if (budget && S->used_bytes + bytes > budget) break;
@@ -237,11 +408,38 @@ static void admit(Server *S) {
       continue;
     }
     if (budget && S->used_bytes + bytes > budget) break;   // wait for memory to free up
+    if (is_mixed_lane(r)) {
+      const int li = least_busy_lane(S);
+      cudaStream_t s = S->lanes[li].stream;
+      char *blk = (char *)pool_alloc(S, bytes, s);
+      if (!blk) break;
+      const size_t a_b = align_up((size_t)r.m * r.n * 8, kAlign);
+      const size_t s_b = align_up(mixed_state_bytes(r.m, r.n), kAlign);
+      q.mixed = true;
+      q.dA = (double *)blk;
+      if (r.kind == SLQR_REQ_FACTOR_SOLVE) {
+        q.db = (double *)(blk + a_b + s_b);
+        q.dx = (double *)(blk + a_b + s_b + align_up((size_t)r.m * 8, kAlign));
+      }
+      q.bytes = bytes;
+      S->used_bytes += bytes;
+      cudaMemcpy2DAsync(q.dA, sizeof(double) * r.m, r.A, sizeof(double) * r.lda,
+                        sizeof(double) * r.m, r.n, cudaMemcpyHostToDevice, s);
+      if (q.db) cudaMemcpyAsync(q.db, r.b, sizeof(double) * r.m, cudaMemcpyHostToDevice, s);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        q.state = 1;
+        q.res.status = SLQR_OK;
+      }
+      dispatch_mixed(S, q, li);
+      S->pending.pop_front();
+      continue;
+    }
     bool small = (r.m <= slqr_batch_max_rows());
     if (small && (long long)r.m * r.n >= kRouteMN) {
       int busy = 0;                                  // units in flight on the stream pool
       for (const Unit &u : S->inflight)
-        if (u.stream != S->bstream[0] && u.stream != S->bstream[1]) ++busy;
+        if (!u.host_done && u.stream != S->bstream[0] && u.stream != S->bstream[1]) ++busy;
       if (2 * busy < S->nstreams) small = false;
     }
     const int pi = (r.prec == SLQR_FP32) ? 1 : 0;
@@ -338,10 +536,20 @@ static void launch_batches(Server *S) {
 static void retire(Server *S) {
   for (size_t ui = 0; ui < S->inflight.size();) {
     Unit &u = S->inflight[ui];
-    cudaError_t e = cudaEventQuery(u.done);
-    if (e == cudaErrorNotReady) {
-      ++ui;
-      continue;
+    cudaError_t e = cudaSuccess;
+    if (u.host_done) {
+      if (!u.host_done->load()) {
+        ++ui;
+        continue;
+      }
+      for (auto &ln : S->lanes)
+        if (ln.stream == u.stream) ln.busy--;
+    } else {
+      e = cudaEventQuery(u.done);
+      if (e == cudaErrorNotReady) {
+        ++ui;
+        continue;
+      }
     }
     std::vector<int> st_host;
     std::vector<double> err_host;
@@ -363,19 +571,23 @@ static void retire(Server *S) {
       q.res.status = status;
       if (r.kind == SLQR_REQ_SOLVE) {
         Resident &h = S->handles[q.handle];
-        if (status == SLQR_OK || status == SLQR_ERANK) deliver_solution(q, h.m, h.n);
+        if (status == SLQR_OK || status == SLQR_ERANK || status == SLQR_FALLBACK)
+          deliver_solution(q, h.m, h.n);
         pool_free(q.db, s);
         S->used_bytes -= q.bytes;
         h.users--;
       } else {
-        if (q.db && (status == SLQR_OK || status == SLQR_ERANK || status == SLQR_ENOCONV))
+        if (q.db && (status == SLQR_OK || status == SLQR_ERANK || status == SLQR_ENOCONV ||
+                     status == SLQR_FALLBACK))
           deliver_solution(q, r.m, r.n);
         if (r.kind == SLQR_REQ_FACTOR && status == SLQR_OK) {
           const uint64_t id = S->next_handle++;
           Resident h;
           h.m = r.m;
           h.n = r.n;
-          h.stacked = (r.structure == SLQR_STACKED);
+          h.mixed = q.mixed;
+          h.fs = q.fs;
+          h.stacked = (r.structure == SLQR_STACKED) && !q.mixed;
           h.dA = q.dA;
           h.dup = q.dup;
           h.dwy = q.small ? nullptr : q.dwy;   // the batched kernel keeps no WY store
@@ -395,7 +607,7 @@ static void retire(Server *S) {
       pool_free((double *)u.d_status, s);
       pool_free(u.d_err, s);
     }
-    cudaEventDestroy(u.done);
+    if (u.done) cudaEventDestroy(u.done);
     S->inflight.erase(S->inflight.begin() + ui);
   }
   // free released handles nobody uses any more
@@ -487,6 +699,22 @@ static slqr_status server_start(slqr_ctx *ctx) {
       return fail(ctx, SLQR_ECUDA, "server batch stream set-up failed");
     }
   }
+  const int nlanes = 4;
+  S->lanes.resize(nlanes);
+  for (int i = 0; i < nlanes; ++i) {
+    Server::Lane &L = S->lanes[i];
+    if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        slqr_create(&L.ctx, ctx->device, 0) != SLQR_OK) {
+      cudaGetLastError();
+      for (auto &l2 : S->lanes) {
+        if (l2.ctx) slqr_destroy(l2.ctx);
+        if (l2.stream) cudaStreamDestroy(l2.stream);
+      }
+      undo();
+      return fail(ctx, SLQR_ECUDA, "server mixed-lane set-up failed");
+    }
+  }
+  for (int i = 0; i < nlanes; ++i) S->lanes[i].thread = std::thread(lane_main, S, i);
   S->worker = std::thread(worker_main, S);
   ctx->server = S;
   return SLQR_OK;
@@ -501,6 +729,13 @@ void server_stop(slqr_ctx *ctx) {
   }
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  {
+    std::lock_guard<std::mutex> lk(S->lane_mu);
+    S->lanes_stopping = true;
+  }
+  S->lane_cv.notify_all();
+  for (auto &L : S->lanes)
+    if (L.thread.joinable()) L.thread.join();
   cudaSetDevice(S->device);
   cudaDeviceSynchronize();
   for (auto &kv : S->handles) {
@@ -513,6 +748,10 @@ void server_stop(slqr_ctx *ctx) {
   for (int pi = 0; pi < 2; ++pi) {
     slqr_destroy(S->bctx[pi]);
     cudaStreamDestroy(S->bstream[pi]);
+  }
+  for (auto &L : S->lanes) {
+    slqr_destroy(L.ctx);
+    cudaStreamDestroy(L.stream);
   }
   cudaMemPoolDestroy(S->pool);
   delete S;
@@ -533,11 +772,9 @@ extern "C" slqr_status slqr_submit(slqr_ctx *ctx, const slqr_request *req, uint6
         return fail(ctx, SLQR_EINVAL, "request: need m >= n >= 1, lda >= m, A");
       if (r.kind == SLQR_REQ_FACTOR_SOLVE && (!r.b || !r.x))
         return fail(ctx, SLQR_EINVAL, "request: FACTOR_SOLVE needs b and x");
-      if (r.prec != SLQR_FP64 && r.prec != SLQR_FP32)
+      if (r.prec != SLQR_FP64 && r.prec != SLQR_FP32 && r.prec != SLQR_TF32 &&
+          r.prec != SLQR_BF16X3)
         return fail(ctx, SLQR_EINVAL, "request: unknown precision %d", r.prec);
-      if (r.prec == SLQR_FP32 && (r.kind != SLQR_REQ_FACTOR_SOLVE || r.m > slqr_batch_max_rows()))
-        return fail(ctx, SLQR_EINVAL,
-                    "request: SLQR_FP32 serves FACTOR_SOLVE with m <= %d", slqr_batch_max_rows());
       if (r.m > slqr_max_rows()) return fail(ctx, SLQR_EINVAL, "request: m above slqr_max_rows()");
       if (r.structure != SLQR_DENSE && r.structure != SLQR_STACKED)
         return fail(ctx, SLQR_EINVAL, "request: unknown structure %d", r.structure);

@@ -227,9 +227,33 @@ slqr_status apply_panel_update(slqr_ctx *ctx, int m, int k0, int nbw, int nb,
                                cudaStream_t stream, int skip = 0);
 size_t panel_update_work_doubles(int m, int N, int nb, int num_sms);
 
+// Persistent state of one low-precision factorization of the mixed-precision
+// path (mixed.cu): the FP32 copy of A D, up, the compact-WY store, the column
+// scales D and the explicit T of every panel, in memory the caller owns
+// (mixed_state_bytes(m, n) bytes).  The request loop keeps one per resident
+// mixed-precision handle.
+struct MixedFactorState {
+  int m = 0, n = 0, prec = 0, nb = 0, K = 0, np = 0, lda32 = 0;
+  int ntop = 0;                        // > 0: stacked [L^T; C], top block of ntop rows
+  float *A32 = nullptr;
+  double *up = nullptr, *wy = nullptr, *colscale = nullptr;
+  float *Tm32 = nullptr;
+};
+size_t mixed_state_bytes(int m, int n);
+// Factor A (FP64, lda) in precision prec into state_mem; asynchronous on s.
+slqr_status mixed_factor_into(slqr_ctx *ctx, int m, int n, const double *A, int lda, int prec,
+                              int ntop, void *state_mem, MixedFactorState *fs, cudaStream_t s);
+// The refinement (and optional FP64 fallback) of x for b with that state and
+// the same FP64 A; synchronous, as slqr_lstsq_mixed_ex.
+slqr_status mixed_solve_with(slqr_ctx *ctx, const MixedFactorState &fs, const double *A, int lda,
+                             const double *b, double *x, const slqr_mixed_opts &o,
+                             slqr_mixed_info *info, cudaStream_t s);
+
 // FP32 factorization (up and the compact-WY store in FP64) used by the
 // mixed-precision driver.
+// ntop > 0: A = [L^T; C] with an upper-triangular top block of ntop rows (the
+// structure-aware factorization, as factor_impl).
 slqr_status factor_f32(slqr_ctx *ctx, int m, int n, float *A, int lda, double *up, double *wy,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int ntop = 0);
 
 }  // namespace slqr

@@ -317,9 +317,95 @@ int launch_vtx_tc(const float *A, int lda, const double *Vtop, int k0, int M, in
   return S + 1;
 }
 
+// TF32 tensor-core peak probe (slqr_measure_peak): one CTA per SM issues the
+// MMAs of upd_tc_kernel (M = 128, N = 64, K = 8 each; the same descriptors,
+// instruction descriptor and 64-column accumulator) back to back on operand
+// tiles filled by plain stores, `iters` times 8 MMAs (K = 64), then commits and
+// waits, bounded, for them.  2 * 128 * 64 * 64 flops per iteration.
+constexpr size_t kPeakSmem = (size_t)kUpBytesA + kUpBytesB + 1024;
+
+__global__ void __launch_bounds__(kTcThreads)
+tf32_peak_kernel(int iters, int *status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = base;
+  unsigned char *sB = base + kUpBytesA;
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_mma;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // operands: small generic values (their layout does not matter here)
+  float *fa = (float *)sA, *fb = (float *)sB;
+  for (int i = tid; i < (kUpBytesA + kUpBytesB) / 4; i += kTcThreads) {
+    const float v = 1.0f + (float)((i * 37) & 255) * (1.0f / 256.0f);
+    if (i < kUpBytesA / 4) fa[i] = v;
+    else fb[i - kUpBytesA / 4] = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&s_taddr)), "r"(kUpN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mma)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = s_taddr;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint64_t ad = sw128_desc(a0 + (k >> 2) * (kUpBytesA / 2) + (k & 3) * 32);
+        const uint64_t bd = sw128_desc(b0 + (k >> 2) * (kUpBytesB / 2) + (k & 3) * 32);
+        const uint32_t accum = (it > 0 || k > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                     :: "r"(taddr), "l"(ad), "l"(bd), "r"(kIdescTf32N64), "r"(accum) : "memory");
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&s_mma)) : "memory");
+    if (!mbar_wait(smem_u32(&s_mma), 0)) atomicCAS(status, 0, SLQR_ETIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kUpN));
+}
+
+slqr_status measure_tf32_peak(slqr_ctx *ctx, double *tflops) {
+  const int iters = 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, 0);
+    tf32_peak_kernel<<<ctx->num_sms, kTcThreads, kPeakSmem, 0>>>(iters, ctx->d_status);
+    cudaEventRecord(e1, 0);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);         // the first launch warms up
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "TF32 peak probe: %s", cudaGetErrorString(e));
+  const double flops = 2.0 * kTcTile * 64.0 * 64.0 * iters * ctx->num_sms;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  return SLQR_OK;
+}
+
 slqr_status init_tc_attrs(slqr_ctx *ctx) {
   cudaError_t e = cudaFuncSetAttribute(upd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kUpSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tf32_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPeakSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(vtx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kVxSmem);

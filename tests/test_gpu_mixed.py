@@ -278,3 +278,28 @@ def test_full_size_cells_8192x4096(ctx, kappa_name, prec_name):
     for j, (b, (x, st, info)) in enumerate(zip((b_cons, b_rand), results)):
         x_o = out["x"][:, j]
         assert_close(x, x_o, x_tol(Ah, b.cpu().numpy(), x_o, kappa, A2=1.0), (j, st, info))
+
+
+@pytest.mark.parametrize("prec_name", ["fp32", "tf32", "bf16x3"])
+def test_mixed_stacked_structure(ctx, prec_name):
+    """slqr_lstsq_mixed_ex with structure = SLQR_STACKED on an SLSQP matrix
+    [L^T; C]: the low-precision factorization skips the zero rows (the
+    structure of slqr_factor_stacked), the refinement uses all of A; the
+    solution matches the oracle's element by element."""
+    from paper_2506_09463_gb300 import abi
+    prec = {"fp32": abi.SLQR_FP32, "tf32": abi.SLQR_TF32, "bf16x3": abi.SLQR_BF16X3}[prec_name]
+    n, m_eq = 1100, 400
+    Ah, bh = workloads.slsqp_stack(n, m_eq, seed=61)
+    A = torch.from_numpy(np.ascontiguousarray(Ah.T)).cuda().t()
+    b = torch.from_numpy(bh.copy()).cuda()
+    m = n + m_eq
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, info = abi.slqr_lstsq_mixed_ex(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(), x.data_ptr(),
+                                       prec, torch.cuda.current_stream().cuda_stream,
+                                       fp64_fallback=1, structure=abi.SLQR_STACKED)
+    assert st in (abi.SLQR_OK, abi.SLQR_FALLBACK), (st, info)
+    x_o = oracle.lstsq(Ah, bh)[0]
+    assert_close(x.cpu().numpy(), x_o, x_tol(Ah, bh, x_o, np.linalg.cond(Ah)), info)
+    st, _ = abi.slqr_lstsq_mixed_ex(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(), x.data_ptr(),
+                                    prec, 0, structure=5)
+    assert st == abi.SLQR_EINVAL

@@ -143,3 +143,76 @@ def test_invalid_requests(server):
     req.kind = abi.SLQR_REQ_FACTOR_SOLVE
     req.m, req.n, req.lda = 3, 5, 3          # m < n
     assert abi.slqr_submit(server.ctx.ctx, req)[0] == abi.SLQR_EINVAL
+
+
+@pytest.mark.parametrize("prec_name", ["fp32", "tf32", "bf16x3"])
+def test_mixed_precision_large_requests(server, prec_name):
+    """FACTOR_SOLVE requests above the batch size class in every mixed
+    precision run on a mixed lane (low-precision factorization, refinement
+    against the FP64 A, FP64 fallback if it fails): the answer matches the
+    oracle within the refined-solution target and the status says how it was
+    obtained (SLQR_OK mixed, SLQR_FALLBACK FP64); dense and stacked."""
+    from paper_2506_09463_gb300 import abi
+    prec = {"fp32": abi.SLQR_FP32, "tf32": abi.SLQR_TF32, "bf16x3": abi.SLQR_BF16X3}[prec_name]
+    for (n, m_eq, structure) in [(600, 200, abi.SLQR_DENSE), (900, 300, abi.SLQR_STACKED)]:
+        A, b = slsqp_problem(n, m_eq, seed=n + 13)
+        res, x = server.wait(server.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b, prec=prec,
+                                           structure=structure))
+        assert res.status in (abi.SLQR_OK, abi.SLQR_FALLBACK), res.status
+        x_o, r_o, bound = ls_bound(A, b)
+        assert np.max(np.abs(x - x_o)) <= max(1e-10, bound) * np.max(np.abs(x_o))
+        assert abs(res.residual_norm - r_o) <= 1e-8 * max(1.0, r_o)
+        assert 0.0 <= res.err < 1e-9 or res.status == abi.SLQR_FALLBACK
+    assert abi.slqr_server_bytes_in_use(server.ctx.ctx) == 0
+
+
+def test_mixed_resident_factorization_solve_and_release(server):
+    """A mixed-precision FACTOR keeps the FP64 copy of A and the low-precision
+    factorization resident (counted in the bytes in use); SOLVE requests
+    refine against them; RELEASE frees them."""
+    from paper_2506_09463_gb300 import abi
+    for prec in (abi.SLQR_FP32, abi.SLQR_BF16X3):
+        n, m_eq = 700, 250
+        A, _ = slsqp_problem(n, m_eq, seed=41 + prec)
+        res, _ = server.wait(server.submit(abi.SLQR_REQ_FACTOR, A=A, prec=prec))
+        assert res.status == 0 and res.handle > 0
+        h = res.handle
+        m = A.shape[0]
+        assert abi.slqr_server_bytes_in_use(server.ctx.ctx) >= m * n * 8 + m * n * 4
+        rng = np.random.default_rng(prec)
+        for _ in range(2):
+            bb = rng.standard_normal(m)
+            r2, x = server.wait(server.submit(abi.SLQR_REQ_SOLVE, b=bb, handle=h, n=n))
+            assert r2.status in (abi.SLQR_OK, abi.SLQR_FALLBACK), r2.status
+            x_o, _, bound = ls_bound(A, bb)
+            assert np.max(np.abs(x - x_o)) <= max(1e-10, bound) * np.max(np.abs(x_o))
+        r3, _ = server.wait(server.submit(abi.SLQR_REQ_RELEASE, handle=h))
+        assert r3.status == 0
+        r4, _ = server.wait(server.submit(abi.SLQR_REQ_SOLVE, b=bb, handle=h, n=n))
+        assert r4.status == abi.SLQR_ENOTFOUND
+    assert abi.slqr_server_bytes_in_use(server.ctx.ctx) == 0
+
+
+def test_mixed_request_same_alone_and_in_the_mix(server):
+    """A mixed-precision request gives the same solution alone and while FP64
+    and mixed-precision requests of other sizes run around it (within the
+    refined-solution target)."""
+    from paper_2506_09463_gb300 import abi
+    A, b = slsqp_problem(800, 300, 77)
+    res, alone = server.wait(server.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b,
+                                           prec=abi.SLQR_FP32))
+    assert res.status == 0
+    t_arr, ns, meqs, seeds = workloads.serving_stream(30, rate=1e4, seed=98, n_hi=1200)
+    tickets, probe = [], None
+    for i in range(30):
+        Ai, bi = slsqp_problem(int(ns[i]), int(meqs[i]), int(seeds[i]))
+        tickets.append(server.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=Ai, b=bi,
+                                     prec=abi.SLQR_FP32 if i % 2 else abi.SLQR_FP64))
+        if i == 12:
+            probe = server.submit(abi.SLQR_REQ_FACTOR_SOLVE, A=A, b=b, prec=abi.SLQR_FP32)
+    res, x = server.wait(probe)
+    assert res.status == 0
+    assert np.max(np.abs(x - alone)) <= 1e-10 * np.max(np.abs(alone))
+    for t in tickets:
+        r, _ = server.wait(t)
+        assert r.status in (abi.SLQR_OK, abi.SLQR_FALLBACK)
