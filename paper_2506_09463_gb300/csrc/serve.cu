@@ -699,7 +699,7 @@ static slqr_status server_start(slqr_ctx *ctx) {
       return fail(ctx, SLQR_ECUDA, "server batch stream set-up failed");
     }
   }
-  const int nlanes = 4;
+  const int nlanes = 8;   // as many as the FP64 stream pool: a mixed solve is synchronous per lane
   S->lanes.resize(nlanes);
   for (int i = 0; i < nlanes; ++i) {
     Server::Lane &L = S->lanes[i];
