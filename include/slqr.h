@@ -160,6 +160,36 @@ slqr_status slqr_factor(slqr_ctx *ctx, int m, int n, double *A, int lda, double 
 void slqr_set_tuning(int panel_width, int panel_rows_min);
 
 /*
+ * Process-wide choice of the panel kernel (no counterpart in the paper):
+ *   ctas  0   chosen per panel: a thread-block cluster holds the panel when it
+ *             fits (FP32 panels of up to 16 x ~800 rows at width 64; FP64
+ *             panels of at most 1024 rows), else the cooperative panel
+ *        -1   always the cooperative panel (one grid-wide exchange of partial
+ *             sums through L2 per column)
+ *         1..16  a cluster of that many CTAs wherever the panel's rows fit
+ *             their shared memory, else the cooperative panel
+ * The cluster panel splits the panel's rows over the CTAs of one cluster,
+ * each slice in shared memory, and exchanges each column's partial sums
+ * through distributed shared memory with one cluster barrier per column.
+ * Both compute the same reflectors up to rounding order.  Set it while no
+ * call is in flight.  Errors: SLQR_EINVAL (ctas out of range).
+ */
+slqr_status slqr_set_panel_cluster(int ctas);
+int slqr_get_panel_cluster(void);
+
+/*
+ * Kernel of the cluster panel (a tuning and testing knob; same results up to
+ * rounding order):
+ *   0  chosen per panel: FP32 panels of width 64 with at most 512 rows per
+ *      CTA keep the panel in registers (16 warps, 4 columns each, R / 32
+ *      rows per lane), others hold it in shared memory with 16 warps
+ *   1  shared memory, 16 warps     2  shared memory, 8 warps
+ *   3  registers where that applies, else as 1
+ * Set it while no call is in flight.  Errors: SLQR_EINVAL (out of range).
+ */
+slqr_status slqr_set_panel_cluster_variant(int variant);
+
+/*
  * Autotuner of those knobs for one problem shape: times slqr_factor of a
  * generic m x n scratch matrix (allocated and freed here) under panel width
  * 32 and 64 and rows-per-CTA minimum 0 (by panel height), 64, 96, 128, 192 and

@@ -80,6 +80,9 @@ SIGNATURES = [
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
     ("slqr_set_tuning", None, [_c_int, _c_int]),
+    ("slqr_set_panel_cluster", _c_int, [_c_int]),
+    ("slqr_get_panel_cluster", _c_int, []),
+    ("slqr_set_panel_cluster_variant", _c_int, [_c_int]),
     ("slqr_autotune", _c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_dbl), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int)]),
     ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
@@ -198,6 +201,18 @@ def slqr_max_rows() -> int:
 
 def slqr_set_tuning(panel_width: int = 0, panel_rows_min: int = 0) -> None:
     _lib.slqr_set_tuning(panel_width, panel_rows_min)
+
+
+def slqr_set_panel_cluster(ctas: int = 0) -> int:
+    return _lib.slqr_set_panel_cluster(ctas)
+
+
+def slqr_get_panel_cluster() -> int:
+    return _lib.slqr_get_panel_cluster()
+
+
+def slqr_set_panel_cluster_variant(variant: int = 0) -> int:
+    return _lib.slqr_set_panel_cluster_variant(variant)
 
 
 def slqr_autotune(ctx, m, n):

@@ -795,6 +795,40 @@ static int rows_min_auto(int M, size_t elem) {
   return M < 1536 ? 64 : (M < 6144 ? 128 : 192);
 }
 
+// Panel by a thread-block cluster (panel_cluster.cu): 0 chosen per panel,
+// -1 never, 2..16 clusters of that many CTAs wherever the panel fits.
+static int g_panel_cluster = 0;
+
+// Automatic choice: the FP32 panel whenever it fits a cluster (its column
+// steps are latency-bound: an exchange through distributed shared memory
+// instead of polled records in L2).  FP64 panels stay cooperative: their
+// column steps carry the slow FP64 FMAs of a slice, which the cooperative
+// panel spreads over more SMs (on GB300 the 256 x 128 problem takes 1.56 ms
+// with it and 2.4 ms with a cluster of 4 to 16 CTAs).  At least
+// kClusterRowsMin rows per CTA.
+constexpr int kClusterRowsMin = 64;
+constexpr int kClusterMaxCtas = 16;
+
+int panel_cluster_ctas(slqr_ctx *ctx, bool f32, int nb, int M, int nbw) {
+  const int mode = g_panel_cluster;
+  if (mode < 0 || M <= 0) return 0;
+  const size_t elem = f32 ? sizeof(float) : sizeof(double);
+  const int rmax = cluster_panel_rows_max(ctx, nb, elem);
+  int ctas;
+  if (mode > 0) {
+    ctas = mode;
+  } else {
+    if (!f32) return 0;
+    ctas = std::min(kClusterMaxCtas, (M + kClusterRowsMin - 1) / kClusterRowsMin);
+  }
+  ctas = std::max(1, ctas);
+  const int R = std::max(nbw, (M + ctas - 1) / ctas);
+  if (R > rmax) return 0;
+  ctas = (M + R - 1) / R;                        // no CTA without rows
+  if (!cluster_panel_fits(ctx, f32, nb, ctas, R)) return 0;
+  return ctas;
+}
+
 int panel_width(int m, int n) {
   if (g_tune_nb == 32 || g_tune_nb == 64) return g_tune_nb;
   TuneEntry e;
@@ -1067,6 +1101,28 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     const int nbw = std::min(NB, K - k0);
     const int skip = skip_of(k0, nbw);
     const int M = m - k0 - skip;
+    // algorithmic flops of the panel: per column j a norm over M-j entries and,
+    // for each later panel column, a dot and an axpy over M-j entries
+    double pflops = 0.0;
+    for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
+    const int cs = panel_cluster_ctas(ctx, std::is_same<T, float>::value, NB, M, nbw);
+    if (cs > 0) {
+      ClusterPanelParams cp;
+      cp.A = A; cp.up = up; cp.wy = wy_store + (size_t)pnl * wy_panel_doubles(NB);
+      cp.m = m; cp.lda = lda; cp.k0 = k0; cp.nbw = nbw; cp.skip = skip; cp.stacked = ntop > 0;
+      cp.R = std::max(nbw, (M + cs - 1) / cs);
+      cp.status = ctx->d_status; cp.spin = ctx->spin_limit;
+      int slot = prof_begin(ctx, s);
+      slqr_status cst = launch_cluster_panel(ctx, std::is_same<T, float>::value, NB, cp, cs, s);
+      prof_end(ctx, s, slot, kPanel, pflops);
+      if (cst != SLQR_OK) return cst;
+      if constexpr (std::is_same<T, float>::value) {
+        if (ctx->tc_mode == 2)
+          split_bf16_region((const float *)A, lda, k0, m, k0, k0 + nbw, ctx->sh_hi, ctx->sh_lo,
+                            ctx->num_sms, s);
+      }
+      return SLQR_OK;                             // (no grid barrier used)
+    }
     const int R = panel_rows_per_cta(M, nbw, Pmax, max_rows_per_cta(NB, sizeof(T)), rmin,
                                      sizeof(T));
     if (R > max_rows_per_cta(NB, sizeof(T)))
@@ -1081,10 +1137,6 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     pp.spin = ctx->spin_limit;
     void *args[] = {&pp};
     size_t smem = panel_smem_bytes(NB, R, sizeof(T));
-    // algorithmic flops of the panel: per column j a norm over M-j entries and,
-    // for each later panel column, a dot and an axpy over M-j entries
-    double pflops = 0.0;
-    for (int j = 0; j < nbw; ++j) pflops += 2.0 * (M - j) * (1 + 2 * (nbw - 1 - j));
     int slot = prof_begin(ctx, s);
     cudaError_t le = cudaLaunchCooperativeKernel(panel_kernel_for<T, NB>(P), dim3(P),
                                                  dim3(kThreads), args, smem, s);
@@ -1164,6 +1216,20 @@ extern "C" void slqr_set_tuning(int panel_width, int panel_rows_min) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache.clear();
   }
+}
+
+extern "C" slqr_status slqr_set_panel_cluster(int ctas) {
+  if (!(ctas == 0 || ctas == -1 || (ctas >= 1 && ctas <= kClusterMaxCtas))) return SLQR_EINVAL;
+  g_panel_cluster = ctas;
+  return SLQR_OK;
+}
+
+extern "C" int slqr_get_panel_cluster(void) { return g_panel_cluster; }
+
+extern "C" slqr_status slqr_set_panel_cluster_variant(int variant) {
+  if (variant < 0 || variant > 3) return SLQR_EINVAL;
+  set_cluster_panel_variant(variant);
+  return SLQR_OK;
 }
 
 namespace slqr {

@@ -198,6 +198,40 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
 // Panel width used for an m x n factorization.
 int panel_width(int m, int n);
 
+// The panel factored by one thread-block cluster (panel_cluster.cu): the
+// panel's M = m - k0 - skip rows split over `ctas` CTAs of R rows each
+// (R >= nbw), each slice in shared memory, the per-column sums exchanged
+// through distributed shared memory.
+struct ClusterPanelParams {
+  void *A;             // T * (float or double), column-major, leading dimension lda
+  double *up;          // global up array
+  double *wy;          // this panel's compact-WY block (Vtop | G | tau)
+  int m, lda, k0, nbw;
+  int skip;            // rows skipped after the panel's top nbw rows (stacked [L^T; C])
+  int stacked;         // stacked [L^T; C]: the diagonal block's strict lower part is zero
+  int R;               // rows per CTA
+  int *status;         // device status word (SLQR_ETIMEOUT when a wait gives up)
+  unsigned spin;       // polls of a bounded wait before it gives up
+};
+size_t cluster_panel_smem_bytes(int nb, int R, size_t elem);
+// largest R for panel width nb and element size elem (0: no cluster panel)
+int cluster_panel_rows_max(const slqr_ctx *ctx, int nb, size_t elem);
+slqr_status init_cluster_attrs(slqr_ctx *ctx);
+// whether a cluster of `ctas` CTAs of R rows each can be resident on the device
+bool cluster_panel_fits(slqr_ctx *ctx, bool f32, int nb, int ctas, int R);
+// the register-resident FP32 panel of width 64 (panel_cluster_reg.cu): rows
+// per lane for R rows per CTA (0: too tall), its shared memory, its kernel
+int cluster_reg_rows_per_lane(int R);
+size_t cluster_reg_smem_bytes(int R);
+const void *cluster_reg_kernel(int rpl);
+int cluster_panel_variant();
+void set_cluster_panel_variant(int v);
+slqr_status launch_cluster_panel(slqr_ctx *ctx, bool f32, int nb, const ClusterPanelParams &pp,
+                                 int ctas, cudaStream_t stream);
+// Cluster size of the panel for a panel of M rows (0: the cooperative panel)
+// under the setting of slqr_set_panel_cluster.
+int panel_cluster_ctas(slqr_ctx *ctx, bool f32, int nb, int M, int nbw);
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------------------------
