@@ -165,7 +165,9 @@ void slqr_set_tuning(int panel_width, int panel_rows_min);
  *             fits (FP32 panels of up to 16 x ~800 rows at width 64; FP64
  *             panels of at most 1024 rows), else the cooperative panel
  *        -1   always the cooperative panel (one grid-wide exchange of partial
- *             sums through L2 per column)
+ *             sums through L2 per column); this also switches the Q
+ *             applications of the mixed-precision refinement to their
+ *             cooperative kernel
  *         1..16  a cluster of that many CTAs wherever the panel's rows fit
  *             their shared memory, else the cooperative panel
  * The cluster panel splits the panel's rows over the CTAs of one cluster,

@@ -1226,6 +1226,10 @@ extern "C" slqr_status slqr_set_panel_cluster(int ctas) {
 
 extern "C" int slqr_get_panel_cluster(void) { return g_panel_cluster; }
 
+namespace slqr {
+int panel_cluster_setting() { return g_panel_cluster; }
+}  // namespace slqr
+
 extern "C" slqr_status slqr_set_panel_cluster_variant(int variant) {
   if (variant < 0 || variant > 3) return SLQR_EINVAL;
   set_cluster_panel_variant(variant);

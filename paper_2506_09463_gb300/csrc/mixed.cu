@@ -804,6 +804,15 @@ struct MixedSolve {
 template <typename VT>
 static slqr_status apply_q_vec(MixedSolve &ms, VT *f, const VT *Tm, VT *qpart, bool trans) {
   if (ms.np == 0) return SLQR_OK;
+  // a cluster of CTAs (the exchange of each panel's partial sums through
+  // distributed shared memory) unless cluster kernels are switched off or
+  // the cluster does not fit
+  if (panel_cluster_setting() >= 0) {
+    slqr_status cst;
+    if (apply_q_cluster(ms.ctx, ms.A32, ms.lda32, ms.up, ms.m, ms.K, ms.nb, ms.np, Tm, f, trans,
+                        ms.s, &cst))
+      return cst;
+  }
   QvecParams<VT> qp;
   qp.A = ms.A32; qp.up = ms.up; qp.Tm = Tm; qp.f = f; qp.part = qpart; qp.bar = ms.qbar;
   qp.status = ms.ctx->d_status; qp.lda = ms.lda32; qp.m = ms.m; qp.K = ms.K; qp.nb = ms.nb;

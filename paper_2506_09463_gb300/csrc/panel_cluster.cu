@@ -16,22 +16,30 @@
 //    with the earlier ones).  The updated column j is computed by every warp
 //    from the old column and reflector j-1 (one FMA), so no warp waits for
 //    another within the pass; the warp that owns column j keeps the result in
-//    a column buffer (three, by j mod 3) and writes it into the slice during
-//    the next column's barrier;
+//    a column buffer (three, by j mod 3) and writes it into the slice while
+//    the next column's records travel;
 //  * the partial sums are reduced within each warp by shuffles (a butterfly:
-//    every lane ends with the same bits) and pushed into every CTA's receive
-//    buffer (st.shared::cluster, double-buffered by column parity); CTA 0
-//    pushes the pivot row the same way;
-//  * one hardware cluster barrier per column (arrive, then the writes nothing
-//    waits for, then wait), after which every warp sums the received records
-//    from its own shared memory in a fixed lane order: every warp of every
-//    CTA computes the same pivot and multipliers bit for bit, without a
-//    second barrier.  An FP32 panel keeps this chain on the FP32 pipe (a
-//    column whose scale is extreme for FP32 forms its pivot in FP64).
+//    every lane ends with the same bits) into a per-CTA record, which is
+//    pushed to every CTA of the cluster in 16-byte pieces with st.async
+//    (only the live entries); each store also counts its bytes on the
+//    receiver's mbarrier (double-buffered by column parity), so the receiver
+//    waits on its own barrier and no CTA waits for the others' stores to
+//    drain.  CTA 0 pushes the pivot row (updated first, at the start of the
+//    column step) entry by entry, counted on the same barriers;
+//  * every warp then sums the received records from its own shared memory in
+//    a fixed lane order: every warp of every CTA computes the same pivot and
+//    multipliers bit for bit.  An FP32 panel keeps this chain on the FP32
+//    pipe (a column whose scale is extreme for FP32 forms its pivot in FP64).
+//    The writes nothing waits for (the previous column's final copy into the
+//    slice, the R entries of the previous pivot row) run while the records
+//    travel.
 //
-// No spin-wait: the only waits are the cluster barriers, which every thread of
-// every CTA reaches on every path (no early exit).  All CTAs of a cluster are
-// co-scheduled by the hardware.
+// Waits are bounded: past the context's spin limit a wait records
+// SLQR_ETIMEOUT once and keeps waiting up to a fixed limit, so that no store
+// of the column is still in flight when the kernel moves on.  Every thread of
+// every CTA reaches every barrier (no early exit), and all CTAs of a cluster
+// are co-scheduled by the hardware.  FP32 panels of at most 16 x 512 rows use
+// the register-resident variant of panel_cluster_reg.cu instead.
 #include "cluster_common.cuh"
 
 #include <type_traits>

@@ -180,15 +180,11 @@ cluster_panel_reg_kernel(ClusterPanelParams p) {
     if (owner_j) pass(std::true_type{});
     else pass(std::false_type{});
     // ---- CTA 0: the pivot row, read out of the registers ----------------------
-    if (q == 0 && lane == (j & 31)) {
-      const int ij = j >> 5;
+    if (q == 0 && lane == (j & 31)) {      // (row j < 64: register row 0 or 1)
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
         const int c = warp + t * NW;
-        T w = v[t][0];
-#pragma unroll
-        for (int i = 1; i < RPL; ++i)
-          if (i == ij) w = v[t][i];
+        const T w = (j < 32) ? v[t][0] : v[t][1];
         if (c >= j && c < nbw) s_rec[buf][1][c] = w;
       }
     }

@@ -226,6 +226,18 @@ size_t cluster_reg_smem_bytes(int R);
 const void *cluster_reg_kernel(int rpl);
 int cluster_panel_variant();
 void set_cluster_panel_variant(int v);
+// the setting of slqr_set_panel_cluster (-1: no cluster kernels at all)
+int panel_cluster_setting();
+// Q^T f (trans) or Q f for one vector by a cluster of CTAs (qvec_cluster.cu),
+// for the FP32 factorization A32 with the explicit T of each panel (Tm);
+// false when the cluster does not fit (nothing launched), else *st is the
+// launch status.
+bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *up, int m, int K,
+                     int nb, int np, const float *Tm, float *f, bool trans, cudaStream_t s,
+                     slqr_status *st);
+bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *up, int m, int K,
+                     int nb, int np, const double *Tm, double *f, bool trans, cudaStream_t s,
+                     slqr_status *st);
 slqr_status launch_cluster_panel(slqr_ctx *ctx, bool f32, int nb, const ClusterPanelParams &pp,
                                  int ctas, cudaStream_t stream);
 // Cluster size of the panel for a panel of M rows (0: the cooperative panel)
