@@ -731,8 +731,9 @@ diag_range_kernel(const float *__restrict__ R, int lda, int n, double *__restric
 // its y_k = acc_k / R_kk is final and is subtracted from the rows above).  An
 // exact zero R_kk gives y_k = 0, the substitution's x_k = 0, and marks the
 // block in zblk.  Rinv: [block][col][row], ld 64.
+template <typename OT>
 __global__ void __launch_bounds__(64)
-diag_inv_kernel(const float *__restrict__ R, int lda, int n, double *__restrict__ Rinv,
+diag_inv_kernel(const float *__restrict__ R, int lda, int n, OT *__restrict__ Rinv,
                 int *__restrict__ zblk) {
   __shared__ double Rs[64][65];
   const int b = blockIdx.x, j = threadIdx.x, b0 = b * 64, rows = min(64, n - b0);
@@ -753,7 +754,7 @@ diag_inv_kernel(const float *__restrict__ R, int lda, int n, double *__restrict_
     for (int i = 0; i < k; ++i) acc[i] = fma(-Rs[i][k], yk, acc[i]);
   }
 #pragma unroll
-  for (int i = 0; i < 64; ++i) Rinv[(size_t)b * 4096 + (size_t)j * 64 + i] = acc[i];
+  for (int i = 0; i < 64; ++i) Rinv[(size_t)b * 4096 + (size_t)j * 64 + i] = (OT)acc[i];
   if (j == 0) zblk[b] = zero ? 1 : 0;
 }
 
@@ -761,6 +762,12 @@ template <bool UPPER, typename VT>
 static slqr_status trsv_vec(slqr_ctx *ctx, const float *R, int lda, int n, VT *y, int *zero_flag,
                             unsigned *bar, unsigned &bar_base, cudaStream_t s,
                             const VT *Rinv = nullptr, const int *zblk = nullptr) {
+  // a cluster of CTAs (the solved blocks pushed through distributed shared
+  // memory) unless cluster kernels are switched off or it does not apply
+  if (panel_cluster_setting() >= 0 && Rinv != nullptr) {
+    slqr_status cst;
+    if (trsv_cluster(ctx, UPPER, R, lda, n, Rinv, zblk, y, zero_flag, s, &cst)) return cst;
+  }
   TrsvParams<VT> tp;
   tp.R = R; tp.Rinv = Rinv; tp.zblk = zblk;
   tp.y = y; tp.zero_flag = zero_flag; tp.bar = bar; tp.status = ctx->d_status;
@@ -798,6 +805,8 @@ struct MixedSolve {
   double *Vk = nullptr, *hdev = nullptr, *ydev = nullptr, *drange = nullptr;
   double *Rinv = nullptr;              // FP64 inverses of R's diagonal blocks
   int *zblk = nullptr;
+  float *Rinv32 = nullptr;             // the same in FP32 (the Bjorck sweeps' solves)
+  int *zblk32 = nullptr;
   int restart = 0;
 };
 
@@ -857,6 +866,10 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
   cudaStream_t s = ms.s;
   const int m = ms.m, n = ms.n;
   init_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.r, m, ms.x, n);
+  // the inverses of R's diagonal blocks (computed in FP64, kept in FP32), once
+  // for all the sweeps' triangular solves
+  diag_inv_kernel<float><<<(n + 63) / 64, 64, 0, s>>>(ms.A32, ms.lda32, n, ms.Rinv32, ms.zblk32);
+  ctx->launch_count += 2;
   int it = 0, status = SLQR_ENOCONV;
   double e_cur = 1.0, e_prev = 1e300;
   slqr_status st;
@@ -867,13 +880,15 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
     resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, ms.colscale,
                                                          ms.g32);
     ctx->launch_count += 3;
-    st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
+    st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base, s,
+                         (const float *)ms.Rinv32, ms.zblk32);
     if (st != SLQR_OK) return st;                                       // h = R^-T g
     st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, true);            // d = Q^T f
     if (st != SLQR_OK) return st;
     form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.f32, ms.g32, m, n, ms.e32);
     ++ctx->launch_count;
-    st = trsv_vec<true>(ctx, ms.A32, ms.lda32, n, ms.e32, ms.zero_flag, ms.qbar, ms.qbar_base, s);
+    st = trsv_vec<true>(ctx, ms.A32, ms.lda32, n, ms.e32, ms.zero_flag, ms.qbar, ms.qbar_base, s,
+                        (const float *)ms.Rinv32, ms.zblk32);
     if (st != SLQR_OK) return st;                                       // dx = R^-1 (d1 - h)
     update_kernel<<<ms.ublocks, 256, 0, s>>>(ms.f32, ms.g32, ms.e32, ms.colscale, ms.x, n,
                                              ms.maxima);
@@ -1208,6 +1223,8 @@ static size_t refine_scratch(slqr_ctx *ctx, const MixedFactorState &fs, bool use
   const size_t o_y = use_gmres ? take((size_t)restart * sizeof(double)) : 0;
   const size_t o_rinv = use_gmres ? take((size_t)nblk64 * 4096 * sizeof(double)) : 0;
   const size_t o_zblk = use_gmres ? take((size_t)nblk64 * sizeof(int)) : 0;
+  const size_t o_rinv32 = take((size_t)nblk64 * 4096 * sizeof(float));
+  const size_t o_zblk32 = take((size_t)nblk64 * sizeof(int));
   if (base && ms) {
     ms->ctx = ctx; ms->m = m; ms->n = n; ms->nb = nb; ms->K = fs.K; ms->np = np;
     ms->lda32 = fs.lda32; ms->chunks = chunks; ms->ublocks = ublocks;
@@ -1224,6 +1241,8 @@ static size_t refine_scratch(slqr_ctx *ctx, const MixedFactorState &fs, bool use
     ms->qpart32 = (float *)(base + o_qpart);
     ms->qbar = (unsigned *)(base + o_bar);
     ms->drange = (double *)(base + o_dr);
+    ms->Rinv32 = (float *)(base + o_rinv32);
+    ms->zblk32 = (int *)(base + o_zblk32);
     if (use_gmres) {
       ms->Tm64 = (double *)(base + o_tm64);
       ms->qpart64 = (double *)(base + o_qpart64);
@@ -1295,7 +1314,7 @@ static slqr_status refine_phase(slqr_ctx *ctx, const MixedFactorState &fs, const
     const double kappa_est = (dr[1] > 0.0) ? dr[0] / dr[1] : HUGE_VAL;
     // the FP64 inverses of R's diagonal blocks, once for all the triangular
     // solves of the preconditioner
-    diag_inv_kernel<<<(n + 63) / 64, 64, 0, s>>>(fs.A32, fs.lda32, n, ms.Rinv, ms.zblk);
+    diag_inv_kernel<double><<<(n + 63) / 64, 64, 0, s>>>(fs.A32, fs.lda32, n, ms.Rinv, ms.zblk);
     ++ctx->launch_count;
     info->kappa_est = kappa_est;
     const double noise = std::max(kStallOk, 100.0 * kappa_est * std::ldexp(1.0, -53));

@@ -238,6 +238,14 @@ bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *u
 bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *up, int m, int K,
                      int nb, int np, const double *Tm, double *f, bool trans, cudaStream_t s,
                      slqr_status *st);
+// R y = c (upper) or R^T y = c for the FP32 R by a cluster of CTAs
+// (trsv_cluster.cu), with the inverses of R's 64 x 64 diagonal blocks; false
+// when it does not apply (n not a multiple of 64 or above 4096, alignment),
+// nothing launched, else *st is the launch status.
+bool trsv_cluster(slqr_ctx *ctx, bool upper, const float *R, int lda, int n, const float *Rinv,
+                  const int *zblk, float *y, int *zero_flag, cudaStream_t s, slqr_status *st);
+bool trsv_cluster(slqr_ctx *ctx, bool upper, const float *R, int lda, int n, const double *Rinv,
+                  const int *zblk, double *y, int *zero_flag, cudaStream_t s, slqr_status *st);
 slqr_status launch_cluster_panel(slqr_ctx *ctx, bool f32, int nb, const ClusterPanelParams &pp,
                                  int ctas, cudaStream_t stream);
 // Cluster size of the panel for a panel of M rows (0: the cooperative panel)
