@@ -601,42 +601,47 @@ gemm_vtx_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
 // T^{-1} = striu(G) + diag(1/tau):
 //   T^T w:  w'_j = tau_j (w_j - sum_{q<j} G[q,j] w'_q),  j = 0 .. nbw-1
 //   T w:    w'_j = tau_j (w_j - sum_{q>j} G[j,q] w'_q),  j = nbw-1 .. 0
-// with four lanes per column splitting the inner sum (FP64 arithmetic).
+// (in the storage precision: FP64 for the FP64 factorization, FP32 for the
+// FP32 one).
 template <typename T, int NB, bool TRANS, int COLS, bool CMAJOR = false>
 __global__ void __launch_bounds__(kThreads)
 tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy, int nbw,
           T *__restrict__ Wt) {
   static_assert(COLS * NB <= kThreads, "one entry needs at least one thread");
   constexpr int TPE = kThreads / (COLS * NB);   // threads per entry (split over s)
-  __shared__ double w[NB][COLS + 1];
-  __shared__ double part[TPE][COLS * NB];
-  __shared__ double G[NB * NB];                // striu(V^T V) of the panel (ld NB)
-  __shared__ double tau[NB];
+  // arithmetic in the storage precision: FP64 for the FP64 factorization,
+  // FP32 for the FP32 one (G and tau converted once per CTA), so that the
+  // substitution chain of an FP32 update stays off the FP64 pipe
+  using AT = T;
+  __shared__ AT w[NB][COLS + 1];
+  __shared__ AT part[TPE][COLS * NB];
+  __shared__ AT G[NB * NB];                    // striu(V^T V) of the panel (ld NB)
+  __shared__ AT tau[NB];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += kThreads) G[idx] = wy[(size_t)NB * NB + idx];
-  if (tid < NB) tau[tid] = wy[2 * (size_t)NB * NB + tid];
+  for (int idx = tid; idx < NB * NB; idx += kThreads) G[idx] = (AT)wy[(size_t)NB * NB + idx];
+  if (tid < NB) tau[tid] = (AT)wy[2 * (size_t)NB * NB + tid];
   const int c0 = blockIdx.x * COLS;
   {
     const int e = tid % (COLS * NB), h = tid / (COLS * NB);
     const int c = e / NB, a = e - c * NB;        // entry (column c0 + c, reflector a)
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    AT acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
     if (c0 + c < N) {
       const T *src = Wp + (size_t)(c0 + c) * NB + a;
       const size_t stride = (size_t)N * NB;
       int s = h;
       for (; s + 3 * TPE < S; s += 4 * TPE) {
-        acc0 += (double)src[(size_t)s * stride];
-        acc1 += (double)src[(size_t)(s + TPE) * stride];
-        acc2 += (double)src[(size_t)(s + 2 * TPE) * stride];
-        acc3 += (double)src[(size_t)(s + 3 * TPE) * stride];
+        acc0 += (AT)src[(size_t)s * stride];
+        acc1 += (AT)src[(size_t)(s + TPE) * stride];
+        acc2 += (AT)src[(size_t)(s + 2 * TPE) * stride];
+        acc3 += (AT)src[(size_t)(s + 3 * TPE) * stride];
       }
-      for (; s < S; s += TPE) acc0 += (double)src[(size_t)s * stride];
+      for (; s < S; s += TPE) acc0 += (AT)src[(size_t)s * stride];
     }
     part[h][e] = (acc0 + acc1) + (acc2 + acc3);
   }
   __syncthreads();
   if (tid < COLS * NB) {
-    double v = part[0][tid];
+    AT v = part[0][tid];
 #pragma unroll
     for (int h = 1; h < TPE; ++h) v += part[h][tid];
     const int c = tid / NB, a = tid - c * NB;
@@ -652,12 +657,12 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
   const int warp = tid >> 5, lane = tid & 31;
   if (warp < COLS) {
     const int c = warp;
-    double r0 = w[lane][c];
-    double r1 = (NB > 32) ? w[(lane + 32) & (NB - 1)][c] : 0.0;
+    AT r0 = w[lane][c];
+    AT r1 = (NB > 32) ? w[(lane + 32) & (NB - 1)][c] : AT(0);
     for (int s = 0; s < nbw; ++s) {
       const int j = TRANS ? s : nbw - 1 - s;
-      const double wj = __shfl_sync(0xffffffffu, (j < 32) ? r0 : r1, j & 31);
-      const double wpj = tau[j] * wj;
+      const AT wj = __shfl_sync(0xffffffffu, (j < 32) ? r0 : r1, j & 31);
+      const AT wpj = tau[j] * wj;
       if (TRANS) {
         if (lane > j) r0 = fma(-G[j + lane * NB], wpj, r0);
         if (NB > 32 && lane + 32 > j) r1 = fma(-G[j + ((lane + 32) & (NB - 1)) * NB], wpj, r1);
@@ -861,10 +866,14 @@ static void vtop_part_f32(const float *A, int lda, const double *Vtop, int k0, i
       A, lda, Vtop, k0, 64, rows, X, ldx, N, rows, Wp);
 }
 
+// lookahead: the update of the next panel's columns only (FP32: on the FMA
+// pipe, three short launches instead of the tensor-core chain, and no BF16
+// shadows to refresh: those columns are split again once they are factored)
 template <typename T, int NB, bool TRANS = true>
 static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, const T *A, int lda,
                                      const double *wy_panel, T *X, int ldx, int N, T *work,
-                                     size_t work_elems, cudaStream_t stream, int skip = 0) {
+                                     size_t work_elems, cudaStream_t stream, int skip = 0,
+                                     bool lookahead = false) {
   if (N <= 0) return SLQR_OK;
   const int M = m - k0 - skip;                     // rows of the panel (row map: panel_row)
   const int ntiles = (N + kBN - 1) / kBN;
@@ -882,11 +891,11 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   int slices = 0;
   bool tc = false;
   // tensor-core mode of an FP32 factorization (0 FMA, 1 TF32, 2 BF16 hi + lo)
-  const int mode = std::is_same<T, float>::value ? ctx->tc_mode : 0;
+  const int mode = (std::is_same<T, float>::value && !lookahead) ? ctx->tc_mode : 0;
   // BF16 mode: an update done on the FMA pipe refreshes the shadows it changed
   auto refresh_shadows = [&]() {
     if constexpr (std::is_same<T, float>::value) {
-      if (mode == 2 && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
+      if (ctx->tc_mode == 2 && !lookahead && ldx == lda && X >= A + (size_t)lda * (k0 + nbw)) {
         const int xcol0 = (int)((X - A) / lda);
         split_bf16_region((const float *)A, lda, k0, m, xcol0, xcol0 + N, ctx->sh_hi, ctx->sh_lo,
                           ctx->num_sms, stream);
@@ -1153,14 +1162,14 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     bar_base += 2u * (unsigned)P;                 // two grid barriers per panel
     return SLQR_OK;
   };
-  auto update = [&](int pnl, int c_begin, int c_end) -> slqr_status {
+  auto update = [&](int pnl, int c_begin, int c_end, bool lookahead) -> slqr_status {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     if (c_end <= c_begin) return SLQR_OK;
     return panel_update_impl<T, NB>(ctx, m, k0, nbw, A, lda,
                                  wy_store + (size_t)pnl * wy_panel_doubles(NB),
                                  A + (size_t)c_begin * lda, lda, c_end - c_begin, work,
-                                 work_doubles, stream, skip_of(k0, nbw));
+                                 work_doubles, stream, skip_of(k0, nbw), lookahead);
   };
   // order the auxiliary stream after everything already on the caller's stream
   e = cudaEventRecord(ctx->ev_start, stream);
@@ -1174,7 +1183,7 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     const int c0 = k0 + nbw;                       // first trailing column
     if (pnl + 1 < np) {
       const int next_w = std::min(NB, K - (k0 + NB));
-      st = update(pnl, c0, c0 + next_w);           // columns of panel p+1
+      st = update(pnl, c0, c0 + next_w, true);     // columns of panel p+1
       if (st != SLQR_OK) return st;
       e = cudaEventRecord(ctx->ev_ready, stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ctx->ev_ready, 0);
@@ -1183,12 +1192,12 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
       if (st != SLQR_OK) return st;
       e = cudaEventRecord(ctx->ev_panel, aux);
       if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
-      st = update(pnl, c0 + next_w, n);            // the rest, concurrently with the panel
+      st = update(pnl, c0 + next_w, n, false);     // the rest, concurrently with the panel
       if (st != SLQR_OK) return st;
       e = cudaStreamWaitEvent(stream, ctx->ev_panel, 0);
       if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
     } else {
-      st = update(pnl, c0, n);
+      st = update(pnl, c0, n, false);
       if (st != SLQR_OK) return st;
     }
   }

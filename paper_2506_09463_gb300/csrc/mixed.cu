@@ -870,6 +870,10 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
   // for all the sweeps' triangular solves
   diag_inv_kernel<float><<<(n + 63) / 64, 64, 0, s>>>(ms.A32, ms.lda32, n, ms.Rinv32, ms.zblk32);
   ctx->launch_count += 2;
+  // the two solves of a sweep that do not depend on each other run at once
+  // when both are cluster kernels (their size limits)
+  const bool overlap = panel_cluster_setting() >= 0 && n % 64 == 0 && n <= 4096 && m <= 8192 &&
+                       m % 4 == 0 && ms.lda32 % 4 == 0;
   int it = 0, status = SLQR_ENOCONV;
   double e_cur = 1.0, e_prev = 1e300;
   slqr_status st;
@@ -880,11 +884,27 @@ static slqr_status bjorck(MixedSolve &ms, int max_iter, double tol, int *it_out,
     resid_g_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(ms.A, ms.lda, m, n, ms.r, ms.colscale,
                                                          ms.g32);
     ctx->launch_count += 3;
-    st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base, s,
-                         (const float *)ms.Rinv32, ms.zblk32);
-    if (st != SLQR_OK) return st;                                       // h = R^-T g
-    st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, true);            // d = Q^T f
-    if (st != SLQR_OK) return st;
+    if (overlap) {
+      // h = R^-T g on the auxiliary stream while d = Q^T f runs here: both
+      // are clusters of 16 CTAs and share no buffer or barrier counter
+      cudaError_t oe = cudaEventRecord(ctx->ev_ready, s);
+      if (oe == cudaSuccess) oe = cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_ready, 0);
+      if (oe != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(oe));
+      st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base,
+                           ctx->aux_stream, (const float *)ms.Rinv32, ms.zblk32);
+      if (st != SLQR_OK) return st;                                     // h = R^-T g
+      st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, true);          // d = Q^T f
+      if (st != SLQR_OK) return st;
+      oe = cudaEventRecord(ctx->ev_panel, ctx->aux_stream);
+      if (oe == cudaSuccess) oe = cudaStreamWaitEvent(s, ctx->ev_panel, 0);
+      if (oe != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(oe));
+    } else {
+      st = trsv_vec<false>(ctx, ms.A32, ms.lda32, n, ms.g32, ms.zero_flag, ms.qbar, ms.qbar_base,
+                           s, (const float *)ms.Rinv32, ms.zblk32);
+      if (st != SLQR_OK) return st;                                     // h = R^-T g
+      st = apply_q_vec(ms, ms.f32, ms.Tm32, ms.qpart32, true);          // d = Q^T f
+      if (st != SLQR_OK) return st;
+    }
     form_e_kernel<<<(m + 255) / 256, 256, 0, s>>>(ms.f32, ms.g32, m, n, ms.e32);
     ++ctx->launch_count;
     st = trsv_vec<true>(ctx, ms.A32, ms.lda32, n, ms.e32, ms.zero_flag, ms.qbar, ms.qbar_base, s,
