@@ -62,6 +62,9 @@ typedef int slqr_status;
 #define SLQR_EBUSY     (-6)  /* over the HBM budget of the context */
 #define SLQR_ENOTFOUND (-7)  /* unknown ticket or handle */
 #define SLQR_ENOCONV   (-8)  /* iterative refinement did not reach its tolerance */
+#define SLQR_ECHECK    (-9)  /* checked build (SLQR_CHECKED): a device bounds or
+                                invariant check failed (the access was skipped), or
+                                a workspace guard zone was overwritten */
 #define SLQR_FALLBACK    2   /* slqr_lstsq_mixed_ex: the mixed-precision refinement
                                 failed and x comes from the opt-in FP64 solve */
 
@@ -207,6 +210,21 @@ slqr_status slqr_set_panel_cluster_variant(int variant);
  */
 slqr_status slqr_autotune(slqr_ctx *ctx, int m, int n, double *best_ms, int *best_panel_width,
                           int *best_rows_min);
+
+/*
+ * The checked build (compiled with -DSLQR_CHECKED into libslqr_checked.so,
+ * a stand-in for a memory checker): every workspace is filled with NaN bytes
+ * (0xFF) each time an entry point takes it and is followed by a guard zone
+ * whose pattern slqr_sync verifies; the cluster kernels check their launch
+ * invariants and the indices they compute at run time, and a failed check
+ * records SLQR_ECHECK in the status word and skips the access (nothing
+ * traps).  slqr_is_checked returns 1 in that build, 0 otherwise.
+ * slqr_check_selftest runs a kernel whose index check must fail on purpose
+ * (the out-of-range access is skipped) and returns the status word it read:
+ * SLQR_ECHECK in the checked build; SLQR_EINVAL in a normal build.
+ */
+int slqr_is_checked(void);
+slqr_status slqr_check_selftest(slqr_ctx *ctx);
 
 /* Largest m that slqr_factor accepts (the panel is held in shared memory). */
 int slqr_max_rows(void);

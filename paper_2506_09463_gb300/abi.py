@@ -16,7 +16,8 @@ import os
 
 from . import build as _build
 
-LIB_PATH = _build.LIB_PATH
+# SLQR_CHECKED=1 loads the checked build (build(checked=True)) instead
+LIB_PATH = _build.LIB_PATH_CHECKED if os.environ.get("SLQR_CHECKED") == "1" else _build.LIB_PATH
 
 SLQR_OK = 0
 SLQR_PENDING = 1
@@ -29,7 +30,7 @@ SLQR_EBUSY = -6
 SLQR_ENOTFOUND = -7
 
 STATUS_NAMES = {
-    -8: "SLQR_ENOCONV", 2: "SLQR_FALLBACK",
+    -8: "SLQR_ENOCONV", 2: "SLQR_FALLBACK", -9: "SLQR_ECHECK",
     SLQR_OK: "SLQR_OK", SLQR_PENDING: "SLQR_PENDING", SLQR_EINVAL: "SLQR_EINVAL",
     SLQR_ENOMEM: "SLQR_ENOMEM", SLQR_ECUDA: "SLQR_ECUDA", SLQR_ETIMEOUT: "SLQR_ETIMEOUT",
     SLQR_ERANK: "SLQR_ERANK", SLQR_EBUSY: "SLQR_EBUSY", SLQR_ENOTFOUND: "SLQR_ENOTFOUND",
@@ -37,6 +38,7 @@ STATUS_NAMES = {
 
 SLQR_ENOCONV = -8
 SLQR_FALLBACK = 2
+SLQR_ECHECK = -9
 SLQR_REFINE_AUTO, SLQR_REFINE_BJORCK, SLQR_REFINE_GMRES, SLQR_REFINE_FP64 = 0, 1, 2, 3
 SLQR_REQ_FACTOR, SLQR_REQ_SOLVE, SLQR_REQ_FACTOR_SOLVE, SLQR_REQ_RELEASE = 1, 2, 3, 4
 
@@ -76,6 +78,8 @@ SIGNATURES = [
     ("slqr_sync", _c_int, [_vp, _vp]),
     ("slqr_check_bounded_wait", _c_int, [_vp, ctypes.c_uint, _vp]),
     ("slqr_set_spin_limit", _c_int, [_vp, ctypes.c_uint]),
+    ("slqr_is_checked", _c_int, []),
+    ("slqr_check_selftest", _c_int, [_vp]),
     ("slqr_panel_width", _c_int, [_c_int, _c_int]),
     ("slqr_wy_size", _c_size, [_c_int, _c_int]),
     ("slqr_max_rows", _c_int, []),
@@ -148,7 +152,7 @@ SLQR_STACKED = 1
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"libslqr.so not built ({LIB_PATH} missing); run "
+            f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH} missing); run "
             "`python -m paper_2506_09463_gb300.build` first")
     lib = ctypes.CDLL(LIB_PATH)
     for name, res, args in SIGNATURES:
@@ -201,6 +205,14 @@ def slqr_max_rows() -> int:
 
 def slqr_set_tuning(panel_width: int = 0, panel_rows_min: int = 0) -> None:
     _lib.slqr_set_tuning(panel_width, panel_rows_min)
+
+
+def slqr_is_checked() -> bool:
+    return bool(_lib.slqr_is_checked())
+
+
+def slqr_check_selftest(ctx: int) -> int:
+    return _lib.slqr_check_selftest(ctx)
 
 
 def slqr_set_panel_cluster(ctas: int = 0) -> int:

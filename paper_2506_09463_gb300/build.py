@@ -4,7 +4,7 @@ Each .cu file under csrc/ is compiled in parallel to an object file, then
 linked into ``paper_2506_09463_gb300/lib/libslqr.so``.  An object is rebuilt
 when its source or any header is newer.  No cmake, one -gencode.
 
-    python -m paper_2506_09463_gb300.build [--force]
+    python -m paper_2506_09463_gb300.build [--force] [--checked]
 """
 from __future__ import annotations
 
@@ -21,6 +21,11 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libslqr.so")
+# the checked build (-DSLQR_CHECKED: NaN-poisoned workspaces with guard zones,
+# device bounds and invariant checks that record SLQR_ECHECK and skip the
+# access); loaded by the binding when SLQR_CHECKED=1
+OBJ_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_PATH_CHECKED = os.path.join(LIB_DIR, "libslqr_checked.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -44,8 +49,11 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    obj_dir = OBJ_DIR_CHECKED if checked else OBJ_DIR
+    lib_path = LIB_PATH_CHECKED if checked else LIB_PATH
+    flags = NVCC_FLAGS + (["-DSLQR_CHECKED"] if checked else [])
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = _headers()
@@ -53,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     objs = []
     for src in sources:
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append((src, obj))
@@ -61,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(job):
         src, obj = job
         tmp = obj + f".tmp{os.getpid()}"
-        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", tmp]
+        cmd = [nvcc, *flags, "-c", src, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -73,17 +81,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             for src in ex.map(compile_one, jobs):
                 if verbose:
                     print("compiled", os.path.relpath(src, ROOT))
-    if force or jobs or _stale(LIB_PATH, objs):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB_PATH)
+        os.replace(tmp, lib_path)
         if verbose:
-            print("linked", os.path.relpath(LIB_PATH, ROOT))
-    return LIB_PATH
+            print("linked", os.path.relpath(lib_path, ROOT))
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

@@ -1,6 +1,8 @@
 // ctx.cu -- context, workspace and status handling of the libslqr C ABI.
 #include "slqr_internal.cuh"
 
+#include <vector>
+
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -28,11 +30,60 @@ slqr_status check_launch(slqr_ctx *ctx, const char *what) {
 
 static slqr_status grow(slqr_ctx *ctx, Workspace &ws, size_t bytes);
 
+#ifdef SLQR_CHECKED
+// Checked build: every workspace is followed by a guard zone of this byte
+// pattern, and its contents are NaN bytes (0xFF) each time an entry point
+// takes it, so that a read of anything not written first shows up as NaN
+// in the results and a write past the end shows up at the next check.
+constexpr size_t kGuardBytes = 64 * 1024;
+constexpr unsigned char kGuardByte = 0xA5;
+
+static slqr_status check_guard(slqr_ctx *ctx, const Workspace &ws) {
+  if (!ws.ptr) return SLQR_OK;
+  std::vector<unsigned char> g(kGuardBytes);
+  cudaError_t e = cudaMemcpy(g.data(), (char *)ws.ptr + ws.bytes, kGuardBytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "guard zone: %s", cudaGetErrorString(e));
+  for (size_t i = 0; i < kGuardBytes; ++i)
+    if (g[i] != kGuardByte)
+      return fail(ctx, SLQR_ECHECK, "workspace guard zone overwritten at byte %zu past the end", i);
+  return SLQR_OK;
+}
+
+static slqr_status poison(slqr_ctx *ctx, Workspace &ws) {
+  cudaError_t e = cudaDeviceSynchronize();             // (work still using it)
+  if (e == cudaSuccess) e = cudaMemset(ws.ptr, 0xFF, ws.bytes);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "poison: %s", cudaGetErrorString(e));
+  return SLQR_OK;
+}
+#endif
+
 slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes) { return grow(ctx, ctx->ws, bytes); }
 slqr_status ensure_workspace2(slqr_ctx *ctx, size_t bytes) { return grow(ctx, ctx->ws2, bytes); }
 
+slqr_status check_workspaces(slqr_ctx *ctx) {
+#ifdef SLQR_CHECKED
+  slqr_status st = check_guard(ctx, ctx->ws);
+  if (st == SLQR_OK) st = check_guard(ctx, ctx->ws2);
+  return st;
+#else
+  (void)ctx;
+  return SLQR_OK;
+#endif
+}
+
 static slqr_status grow(slqr_ctx *ctx, Workspace &ws, size_t bytes) {
+#ifdef SLQR_CHECKED
+  if (bytes <= ws.bytes) {
+    slqr_status st = check_guard(ctx, ws);
+    return st == SLQR_OK ? poison(ctx, ws) : st;
+  }
+  if (ws.ptr) {
+    slqr_status st = check_guard(ctx, ws);
+    if (st != SLQR_OK) return st;
+  }
+#else
   if (bytes <= ws.bytes) return SLQR_OK;
+#endif
   bytes = align_up(bytes, (size_t)1 << 20);
   if (ctx->hbm_budget && bytes > ctx->hbm_budget)
     return fail(ctx, SLQR_EBUSY, "workspace of %zu bytes exceeds the HBM budget %zu", bytes,
@@ -45,14 +96,24 @@ static slqr_status grow(slqr_ctx *ctx, Workspace &ws, size_t bytes) {
     ws.bytes = 0;
   }
   void *p = nullptr;
+#ifdef SLQR_CHECKED
+  cudaError_t e = cudaMalloc(&p, bytes + kGuardBytes);
+#else
   cudaError_t e = cudaMalloc(&p, bytes);
+#endif
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, SLQR_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   }
   ws.ptr = p;
   ws.bytes = bytes;
+#ifdef SLQR_CHECKED
+  e = cudaMemset((char *)p + bytes, kGuardByte, kGuardBytes);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "guard zone: %s", cudaGetErrorString(e));
+  return poison(ctx, ws);
+#else
   return SLQR_OK;
+#endif
 }
 
 static cudaEvent_t take_event(slqr_ctx *ctx) {
@@ -335,6 +396,48 @@ extern "C" slqr_status slqr_sync(slqr_ctx *ctx, void *stream) {
   if (st != 0) {
     if (st == SLQR_ERANK) fail(ctx, st, "R has an exact zero on its diagonal");
     else if (st == SLQR_ETIMEOUT) fail(ctx, st, "a bounded device wait gave up");
+    else if (st == SLQR_ECHECK) fail(ctx, st, "a device bounds or invariant check failed");
+  }
+  if (st == 0) {
+    const slqr_status g = check_workspaces(ctx);        // (checked build only)
+    if (g != SLQR_OK) return g;
   }
   return st;
+}
+
+// The checked build's self test: an index one past a 64-entry buffer, which
+// the check must catch (the access is skipped).
+__global__ void check_selftest_kernel(double *buf, int n, int *status) {
+  const int i = threadIdx.x;                           // 0 .. n (one past the end)
+  if (slqr_check(i < n, status)) buf[i] = (double)i;
+}
+
+extern "C" int slqr_is_checked(void) {
+#ifdef SLQR_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" slqr_status slqr_check_selftest(slqr_ctx *ctx) {
+  if (!ctx) return SLQR_EINVAL;
+#ifndef SLQR_CHECKED
+  return SLQR_EINVAL;
+#else
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  double *buf = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&buf, 64 * sizeof(double));
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "selftest: %s", cudaGetErrorString(e));
+  check_selftest_kernel<<<1, 65>>>(buf, 64, ctx->d_status);
+  e = cudaDeviceSynchronize();
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "selftest: %s", cudaGetErrorString(e));
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "selftest: %s", cudaGetErrorString(e));
+  return st;
+#endif
 }

@@ -193,7 +193,8 @@ panel_kernel(PanelParams p) {
   for (int idx = tid; idx < nbw * R; idx += kThreads) {
     int c = idx / R, r = idx - c * R;
     // (stacked: the strictly lower part of the diagonal block is zero, not read)
-    const bool zero = r >= RO || (p.stacked && row0 + r < nbw && row0 + r > c);
+    const bool zero = r >= RO || (p.stacked && row0 + r < nbw && row0 + r > c) ||
+                      !slqr_check(panel_row(p.k0, nbw, p.skip, row0 + r) < p.m, p.status);
     Ps[c * R + r] =
         zero ? T(0) : A[SLQR_IDX(panel_row(p.k0, nbw, p.skip, row0 + r), p.k0 + c, lda)];
   }

@@ -37,8 +37,9 @@
 // Waits are bounded: past the context's spin limit a wait records
 // SLQR_ETIMEOUT once and keeps waiting up to a fixed limit, so that no store
 // of the column is still in flight when the kernel moves on.  Every thread of
-// every CTA reaches every barrier (no early exit), and all CTAs of a cluster
-// are co-scheduled by the hardware.  FP32 panels of at most 16 x 512 rows use
+// every CTA reaches every barrier (the checked build's launch-invariant check
+// returns from every CTA at once, before the first barrier), and all CTAs of
+// a cluster are co-scheduled by the hardware.  FP32 panels of at most 16 x 512 rows use
 // the register-resident variant of panel_cluster_reg.cu instead.
 #include "cluster_common.cuh"
 
@@ -81,6 +82,11 @@ cluster_panel_kernel(ClusterPanelParams p) {
   const int nbw = p.nbw;
   T *A = (T *)p.A;
   const int lda = p.lda;
+  // checked build: the launch's invariants (uniform: every CTA returns here
+  // together, before any barrier)
+  if (!slqr_check(CS <= kClMaxCtas && R >= nbw && nbw >= 1 && nbw <= NB &&
+                      p.m - p.k0 - p.skip <= CS * R && lda >= p.m, p.status))
+    return;
 
   for (int idx = tid; idx < NB * R; idx += NT) {
     const int c = idx / R, r = idx - c * R;

@@ -66,6 +66,11 @@ cluster_panel_reg_kernel(ClusterPanelParams p) {
   const int nbw = p.nbw;
   T *A = (T *)p.A;
   const int lda = p.lda;
+  // checked build: the launch's invariants (the same in every CTA, so every
+  // CTA returns here together, before any barrier)
+  if (!slqr_check(CS <= kClMaxCtas && R >= nbw && R <= RP && nbw >= 1 && nbw <= NB &&
+                      p.m - p.k0 - p.skip <= CS * R && lda >= p.m, p.status))
+    return;
 
   // ---- the slice into registers --------------------------------------------
   T v[CPW][RPL];

@@ -35,7 +35,8 @@
 //
 // Waits are bounded as in the cluster panel: past the context's spin limit a
 // wait records SLQR_ETIMEOUT and keeps waiting up to a fixed limit.  Every
-// thread reaches every barrier (no early exit).
+// thread reaches every barrier (the checked build's launch-invariant check
+// returns from every CTA at once, before the first barrier).
 #include "cluster_common.cuh"
 
 namespace slqr {
@@ -86,6 +87,11 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
   const int r0 = q * R, r1 = min(p.m, r0 + R);
   const float *A = p.A;
   const size_t lda = (size_t)p.lda;
+  // checked build: the launch's invariants (uniform: every CTA returns here
+  // together, before any barrier)
+  if (!slqr_check(CS <= kClMaxCtas && R <= RP && (long long)CS * R >= p.m && p.lda >= p.m &&
+                      (!TMA || (R % 64 == 0 && p.lda % 4 == 0 && p.m % 4 == 0)), p.status))
+    return;
 
   for (int r = tid; r < 2 * RP; r += NT) fs[r] = r < r1 - r0 ? p.f[r0 + r] : VT(0);
   // (TMA: every entry of Vs is finite before the first copy lands; entries
@@ -223,7 +229,7 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
       const int rr = lane + 32 * i;
-      const VT fv = fs[off + rr];                         // (zero past the slice)
+      const VT fv = slqr_check(off + rr < 2 * RP, p.status) ? fs[off + rr] : VT(0);   // (zero past the slice)
 #pragma unroll
       for (int t = 0; t < CPW; ++t) acc[t] = fma_t((VT)vr[t][i], fv, acc[t]);
     }
@@ -296,7 +302,7 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
       VT v = VT(0);
 #pragma unroll
       for (int w = 0; w < NW; ++w) v += sp[w * RP + rr];
-      fs[off + rr] -= v;
+      if (slqr_check(rr < RP && off + rr < 2 * RP, p.status)) fs[off + rr] -= v;
     }
     load_up(s + 1);                                       // (read after the barrier)
     __syncthreads();

@@ -104,6 +104,9 @@ slqr_status fail(slqr_ctx *ctx, slqr_status st, const char *fmt, ...);
 // Make sure the workspace holds at least `bytes`; returns SLQR_OK or an error.
 slqr_status ensure_workspace(slqr_ctx *ctx, size_t bytes);
 slqr_status ensure_workspace2(slqr_ctx *ctx, size_t bytes);
+// Checked build: verify the workspaces' guard zones (SLQR_ECHECK when one was
+// overwritten); SLQR_OK otherwise and in the normal build.
+slqr_status check_workspaces(slqr_ctx *ctx);
 
 // Check the last launch; returns SLQR_OK or SLQR_ECUDA with the message set.
 slqr_status check_launch(slqr_ctx *ctx, const char *what);
@@ -168,6 +171,18 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 __device__ __forceinline__ void record_status(int *status, int code) {
   atomicCAS(status, kStatusOk, code);
 }
+
+// Checked build (SLQR_CHECKED): a condition that must hold for an access or
+// a launch; when it fails the first failure is recorded as SLQR_ECHECK and
+// the caller skips the access.  Normal build: always true, no code.
+#ifdef SLQR_CHECKED
+__device__ __forceinline__ bool slqr_check(bool ok, int *status) {
+  if (!ok) atomicCAS(status, kStatusOk, SLQR_ECHECK);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool slqr_check(bool ok, int *) { return true; }
+#endif
 
 // Arrive at a grid barrier (a monotonic arrival counter) and wait, bounded by
 // `limit` polls, until it reaches `target`.  Returns false after recording

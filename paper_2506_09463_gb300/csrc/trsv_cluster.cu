@@ -22,7 +22,8 @@
 //           pushes it to every CTA.
 //
 // Waits are bounded as in the other cluster kernels.  Every thread reaches
-// every barrier (no early exit).
+// every barrier (the checked build's launch-invariant check returns from
+// every CTA at once, before the first barrier).
 #include "cluster_common.cuh"
 
 namespace slqr {
@@ -72,6 +73,11 @@ trsv_cluster_kernel(TrsvClusterParams<VT> p) {
   auto owner = [&](int b) { return b % CS; };
   auto slot = [&](int b) { return b / CS; };                     // its place in cs
   const int nloc = (nblk - q + CS - 1) / CS;                     // blocks of this CTA
+  // checked build: the launch's invariants (uniform: every CTA returns here
+  // together, before any barrier)
+  if (!slqr_check(CS <= kClMaxCtas && nblk >= 1 && nblk <= kTsBlocks && n == 64 * nblk &&
+                      (nblk + CS - 1) / CS <= kTsLocal && p.lda >= n, p.status))
+    return;
 
   // this CTA's blocks of the right-hand side
   for (int idx = tid; idx < kTsLocal * 64; idx += NT) {
