@@ -425,9 +425,15 @@ bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *u
   return qvec_cluster_launch<float>(ctx, pp, nb, s, st);
 }
 
+// The FP64 application (the GMRES-IR preconditioner) stays on the cooperative
+// kernel for panels of more than 256 rows per CTA: its arithmetic runs on the
+// FP64 pipe, which 16 SMs make the bound (on GB300, 8192 x 4096: 2x slower
+// than the cooperative kernel's 128 CTAs), and its slices no longer fit
+// shared memory for the TMA copies.
 bool apply_q_cluster(slqr_ctx *ctx, const float *A32, int lda32, const double *up, int m, int K,
                      int nb, int np, const double *Tm, double *f, bool trans, cudaStream_t s,
                      slqr_status *st) {
+  if (m > 16 * 256) return false;
   QvecClusterParams<double> pp;
   pp.A = A32; pp.up = up; pp.Tm = Tm; pp.f = f; pp.status = ctx->d_status; pp.lda = lda32;
   pp.m = m; pp.K = K; pp.np = np; pp.trans = trans ? 1 : 0; pp.R = 0; pp.spin = ctx->spin_limit;
