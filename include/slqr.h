@@ -195,6 +195,22 @@ int slqr_get_panel_cluster(void);
 slqr_status slqr_set_panel_cluster_variant(int variant);
 
 /*
+ * Look-ahead update of the FP32 factorization (the mixed-precision path):
+ * after each panel of width 64, the next panel's columns X (rows k0 .. m-1)
+ * become X - V T^T V^T X (the compact-WY form of the panel's reflectors,
+ * Alg. 2 applied by blocks) before the next panel is factored.
+ *   1  (default) one cooperative kernel: slices of V and X staged in shared
+ *      memory, V^T X reduced in a fixed order, T^T W, X -= V W' (two bounded
+ *      grid barriers; SLQR_ETIMEOUT if one gives up); it applies to dense
+ *      matrices with at most 256 * (number of SMs) rows
+ *   0  three tiled launches (V^T X partials, T^T W, X -= V W')
+ * Same results up to rounding order.  A process-wide tuning and testing
+ * knob: set it while no call is in flight.  Errors: SLQR_EINVAL (not 0 or 1).
+ */
+slqr_status slqr_set_fused_lookahead(int enable);
+int slqr_get_fused_lookahead(void);
+
+/*
  * Autotuner of those knobs for one problem shape: times slqr_factor of a
  * generic m x n scratch matrix (allocated and freed here) under panel width
  * 32 and 64 and rows-per-CTA minimum 0 (by panel height), 64, 96, 128, 192 and

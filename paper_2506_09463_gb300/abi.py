@@ -87,6 +87,8 @@ SIGNATURES = [
     ("slqr_set_panel_cluster", _c_int, [_c_int]),
     ("slqr_get_panel_cluster", _c_int, []),
     ("slqr_set_panel_cluster_variant", _c_int, [_c_int]),
+    ("slqr_set_fused_lookahead", _c_int, [_c_int]),
+    ("slqr_get_fused_lookahead", _c_int, []),
     ("slqr_autotune", _c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_dbl), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int)]),
     ("slqr_factor", _c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _vp]),
@@ -225,6 +227,14 @@ def slqr_get_panel_cluster() -> int:
 
 def slqr_set_panel_cluster_variant(variant: int = 0) -> int:
     return _lib.slqr_set_panel_cluster_variant(variant)
+
+
+def slqr_set_fused_lookahead(enable: int = 1) -> int:
+    return _lib.slqr_set_fused_lookahead(enable)
+
+
+def slqr_get_fused_lookahead() -> int:
+    return _lib.slqr_get_fused_lookahead()
 
 
 def slqr_autotune(ctx, m, n):

@@ -240,7 +240,7 @@ extern "C" slqr_status slqr_create(slqr_ctx **out, int device, size_t hbm_budget
   ctx->smem_optin = (size_t)optin;
   if (init_kernel_attrs(ctx) != SLQR_OK || init_batch_attrs(ctx) != SLQR_OK ||
       init_tc_attrs(ctx) != SLQR_OK || init_bf16_attrs(ctx) != SLQR_OK ||
-      init_cluster_attrs(ctx) != SLQR_OK) {
+      init_cluster_attrs(ctx) != SLQR_OK || init_lookahead_attrs(ctx) != SLQR_OK) {
     cudaEventDestroy(ctx->ev_start);
     cudaEventDestroy(ctx->ev_ready);
     cudaEventDestroy(ctx->ev_panel);

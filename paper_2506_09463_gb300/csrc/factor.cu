@@ -616,10 +616,26 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
   using AT = T;
   __shared__ AT w[NB][COLS + 1];
   __shared__ AT part[TPE][COLS * NB];
-  __shared__ AT G[NB * NB];                    // striu(V^T V) of the panel (ld NB)
+  // striu(V^T V) of the panel, row-major with row stride NB + 1: the
+  // substitution reads a row (TRANS) or a column of it across the lanes, and
+  // both are conflict-free in this layout (the store is column-major)
+  constexpr int GLD = NB + 1;
+  __shared__ AT G[NB * GLD];
   __shared__ AT tau[NB];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += kThreads) G[idx] = (AT)wy[(size_t)NB * NB + idx];
+  {
+    // all loads of G issued before the first store (one round trip to L2)
+    constexpr int GPER = NB * NB / kThreads;
+    static_assert(GPER * kThreads == NB * NB, "G splits evenly over the threads");
+    double gv[GPER];
+#pragma unroll
+    for (int u = 0; u < GPER; ++u) gv[u] = wy[(size_t)NB * NB + tid + u * kThreads];
+#pragma unroll
+    for (int u = 0; u < GPER; ++u) {
+      const int idx = tid + u * kThreads, r = idx % NB, c = idx / NB;
+      G[r * GLD + c] = (AT)gv[u];
+    }
+  }
   if (tid < NB) tau[tid] = (AT)wy[2 * (size_t)NB * NB + tid];
   const int c0 = blockIdx.x * COLS;
   {
@@ -665,11 +681,11 @@ tw_kernel(const T *__restrict__ Wp, int S, int N, const double *__restrict__ wy,
       const AT wj = __shfl_sync(0xffffffffu, (j < 32) ? r0 : r1, j & 31);
       const AT wpj = tau[j] * wj;
       if (TRANS) {
-        if (lane > j) r0 = fma(-G[j + lane * NB], wpj, r0);
-        if (NB > 32 && lane + 32 > j) r1 = fma(-G[j + ((lane + 32) & (NB - 1)) * NB], wpj, r1);
+        if (lane > j) r0 = fma(-G[j * GLD + lane], wpj, r0);
+        if (NB > 32 && lane + 32 > j) r1 = fma(-G[j * GLD + ((lane + 32) & (NB - 1))], wpj, r1);
       } else {
-        if (lane < j) r0 = fma(-G[lane + j * NB], wpj, r0);
-        if (NB > 32 && lane + 32 < j) r1 = fma(-G[lane + 32 + j * NB], wpj, r1);
+        if (lane < j) r0 = fma(-G[lane * GLD + j], wpj, r0);
+        if (NB > 32 && lane + 32 < j) r1 = fma(-G[(lane + 32) * GLD + j], wpj, r1);
       }
       if (lane == (j & 31)) {
         if (j < 32) r0 = wpj;
@@ -1101,9 +1117,9 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   if (np == 0) return SLQR_OK;
 
   // Look-ahead: after panel p, the columns of panel p+1 are updated first;
-  // panel p+1 is then factored on the auxiliary stream while the rest of the
-  // trailing update of panel p runs on the caller's stream (the GPU form of
-  // running the critical path T_{i,i} early).
+  // panel p+1 is then factored while the rest of the trailing update of
+  // panel p runs on the other stream (the GPU form of running the critical
+  // path T_{i,i} early).
   cudaStream_t aux = ctx->aux_stream;
   unsigned bar_base = 0;
   auto launch_panel = [&](int pnl, cudaStream_t s) -> slqr_status {
@@ -1163,14 +1179,27 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
     bar_base += 2u * (unsigned)P;                 // two grid barriers per panel
     return SLQR_OK;
   };
-  auto update = [&](int pnl, int c_begin, int c_end, bool lookahead) -> slqr_status {
+  // the fused look-ahead kernel's grid barriers count on their own counter
+  // (bar[32], another cache line than the panels' bar[0])
+  unsigned la_base = 0;
+  auto update = [&](int pnl, int c_begin, int c_end, bool lookahead,
+                    cudaStream_t us) -> slqr_status {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     if (c_end <= c_begin) return SLQR_OK;
+    if constexpr (std::is_same<T, float>::value && NB == 64) {
+      slqr_status lst = SLQR_OK;
+      if (lookahead && ntop == 0 &&
+          lookahead_update_f32(ctx, m, k0, nbw, A, lda,
+                               wy_store + (size_t)pnl * wy_panel_doubles(NB), c_begin,
+                               c_end - c_begin, work, work_doubles, bar + 32, la_base, us,
+                               &lst))
+        return lst;
+    }
     return panel_update_impl<T, NB>(ctx, m, k0, nbw, A, lda,
                                  wy_store + (size_t)pnl * wy_panel_doubles(NB),
                                  A + (size_t)c_begin * lda, lda, c_end - c_begin, work,
-                                 work_doubles, stream, skip_of(k0, nbw), lookahead);
+                                 work_doubles, us, skip_of(k0, nbw), lookahead);
   };
   // order the auxiliary stream after everything already on the caller's stream
   e = cudaEventRecord(ctx->ev_start, stream);
@@ -1178,27 +1207,45 @@ static slqr_status factor_impl(slqr_ctx *ctx, int m, int n, T *A, int lda, doubl
   if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
   st = launch_panel(0, stream);
   if (st != SLQR_OK) return st;
+  // FP64: the panels on the auxiliary stream, the updates (the longer chain)
+  // back to back on the caller's stream.  FP32: the panels (the longer chain)
+  // right behind the look-ahead on the caller's stream, so that a panel is
+  // never queued behind the first kernel of the rest of the update and has
+  // its SMs before the update fills the GPU, and the rest of each update on
+  // the auxiliary stream.
+  constexpr bool kPanelsOnCaller = std::is_same<T, float>::value;
   for (int pnl = 0; pnl < np; ++pnl) {
     const int k0 = pnl * NB;
     const int nbw = std::min(NB, K - k0);
     const int c0 = k0 + nbw;                       // first trailing column
     if (pnl + 1 < np) {
       const int next_w = std::min(NB, K - (k0 + NB));
-      st = update(pnl, c0, c0 + next_w, true);     // columns of panel p+1
+      st = update(pnl, c0, c0 + next_w, true, stream);   // columns of panel p+1
       if (st != SLQR_OK) return st;
       e = cudaEventRecord(ctx->ev_ready, stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ctx->ev_ready, 0);
       if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
-      st = launch_panel(pnl + 1, aux);
-      if (st != SLQR_OK) return st;
-      e = cudaEventRecord(ctx->ev_panel, aux);
-      if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
-      st = update(pnl, c0 + next_w, n, false);     // the rest, concurrently with the panel
-      if (st != SLQR_OK) return st;
-      e = cudaStreamWaitEvent(stream, ctx->ev_panel, 0);
+      if (kPanelsOnCaller) {
+        // rest of the update of panel p (aux) || panel p+1 (caller's stream)
+        st = update(pnl, c0 + next_w, n, false, aux);
+        if (st != SLQR_OK) return st;
+        e = cudaEventRecord(ctx->ev_panel, aux);
+        if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+        st = launch_panel(pnl + 1, stream);
+        if (st != SLQR_OK) return st;
+        e = cudaStreamWaitEvent(stream, ctx->ev_panel, 0);
+      } else {
+        st = launch_panel(pnl + 1, aux);
+        if (st != SLQR_OK) return st;
+        e = cudaEventRecord(ctx->ev_panel, aux);
+        if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
+        st = update(pnl, c0 + next_w, n, false, stream);  // concurrently with the panel
+        if (st != SLQR_OK) return st;
+        e = cudaStreamWaitEvent(stream, ctx->ev_panel, 0);
+      }
       if (e != cudaSuccess) return fail(ctx, SLQR_ECUDA, "event: %s", cudaGetErrorString(e));
     } else {
-      st = update(pnl, c0, n, false);
+      st = update(pnl, c0, n, false, stream);
       if (st != SLQR_OK) return st;
     }
   }

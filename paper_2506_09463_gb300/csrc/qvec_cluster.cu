@@ -21,9 +21,10 @@
 //   push    the CTA's partials go to every CTA (st.async, 16-byte pieces,
 //           counted on the receiver's mbarrier, double-buffered by panel
 //           parity);
-//   W'      warps 0-1 wait for the records, sum them in a fixed order (the
-//           same bits in every CTA) and form W' = T^T W (or T W) with the
-//           panel's T, fetched into shared memory during the dot;
+//   W'      warps 0-1 wait for the records and sum them in a fixed order
+//           (the same bits in every CTA); then every thread takes part in
+//           W' = T^T W (or T W) with the panel's T, fetched into shared
+//           memory during the dot (eight threads per entry);
 //   update  f -= V W' from the same registers: each warp's part of every row
 //           through shared memory, the 16 parts of a row added in a fixed
 //           order.
@@ -247,7 +248,7 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
       st_async16(cluster_addr(&s_recv[buf][q][c], dest), &s_rec[buf][c],
                  cluster_addr(&s_mbar[buf], dest));
     }
-    // ---- warps 0-1: the sums over the cluster, then W' ---------------------------
+    // ---- warps 0-1: the sums over the cluster ------------------------------------
     if (warp < 2) {
       bool got = false;
       if (s_ok) got = mbar_wait_bounded(&s_mbar[buf], (unsigned)(s >> 1) & 1u, p.spin, p.status,
@@ -268,19 +269,30 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
           for (int r = 0; r < w; ++r) a[r] += a[r + w];
         s_w[tid] = a[0];
       }
-      asm volatile("bar.sync 1, 64;" ::: "memory");     // warps 0-1 only
-      if (tid < NB) {
-        const int j = tid;
-        VT v = VT(0);
-        if (j < nbw) {
+    }
+    __syncthreads();
+    // ---- W' = T^T W (or T W): eight threads per entry j, thread l of the
+    // eight taking the terms qq = l, l + 8, ..; the eight parts summed by a
+    // butterfly in a fixed order -----------------------------------------------
+    {
+      constexpr int TPJ = NT / NB;                      // threads per entry (8)
+      static_assert(TPJ * NB == NT && (TPJ & (TPJ - 1)) == 0, "threads per entry");
+      const int j = tid / TPJ, l = tid % TPJ;
+      VT v = VT(0);
+      if (j < nbw) {
+#pragma unroll
+        for (int i = 0; i < NB / TPJ; ++i) {
+          const int qq = l + TPJ * i;
           if (p.trans) {
-            for (int qq = 0; qq <= j; ++qq) v = fma_t(Ts[qq + j * (NB + 1)], s_w[qq], v);
+            if (qq <= j) v = fma_t(Ts[qq + j * (NB + 1)], s_w[qq], v);
           } else {
-            for (int qq = j; qq < nbw; ++qq) v = fma_t(Ts[j + qq * (NB + 1)], s_w[qq], v);
+            if (qq >= j && qq < nbw) v = fma_t(Ts[j + qq * (NB + 1)], s_w[qq], v);
           }
         }
-        s_wt[j] = v;
       }
+#pragma unroll
+      for (int w = TPJ / 2; w > 0; w >>= 1) v += __shfl_xor_sync(0xffffffffu, v, w);
+      if (l == 0) s_wt[j] = v;
     }
     __syncthreads();
     // ---- update: f -= V W' on the slice: each warp its columns' part of every

@@ -267,6 +267,17 @@ slqr_status launch_cluster_panel(slqr_ctx *ctx, bool f32, int nb, const ClusterP
 // under the setting of slqr_set_panel_cluster.
 int panel_cluster_ctas(slqr_ctx *ctx, bool f32, int nb, int M, int nbw);
 
+// Look-ahead update of the next panel's columns (at most 64) of an FP32
+// factorization with panels of width 64, in one cooperative launch
+// (lookahead.cu): false when it does not apply (setting off, rows per CTA
+// above its limit, workspace) or the launch was refused, nothing launched;
+// else *st = SLQR_OK and bar_base advanced past its two grid barriers.
+bool lookahead_update_f32(slqr_ctx *ctx, int m, int k0, int nbw, float *A, int lda,
+                          const double *wy_panel, int cb, int N, float *work, size_t work_elems,
+                          unsigned *bar, unsigned &bar_base, cudaStream_t stream,
+                          slqr_status *st);
+slqr_status init_lookahead_attrs(slqr_ctx *ctx);
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------------------------

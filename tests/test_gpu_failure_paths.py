@@ -106,8 +106,8 @@ def test_panel_waits_give_up_under_a_short_spin_limit():
 
 
 def test_mixed_solve_reports_a_wait_that_gave_up():
-    """The mixed-precision solve's cooperative kernels (panel, Q application,
-    triangular solves) under a spin limit of 2 polls: the call returns
+    """The mixed-precision solve's cooperative kernels (panel, look-ahead
+    update, Q application, triangular solves) under a spin limit of 2 polls: the call returns
     SLQR_ETIMEOUT, never a result; with the default limit it solves again."""
     from paper_2506_09463_gb300 import abi, api
     m, n = 2000, 600
