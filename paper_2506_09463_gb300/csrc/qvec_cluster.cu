@@ -31,7 +31,8 @@
 // Where shared memory allows, the next panel's slice comes into shared memory
 // by TMA bulk copies (one per column, counted on an mbarrier) while the
 // current panel is processed, and moves to registers at the start of its
-// step.  The slice of V in registers limits a CTA to 512 rows (m <= 8192 with
+// step.  The copies are issued by the warps that would otherwise wait for the
+// exchange.  The slice of V in registers limits a CTA to 512 rows (m <= 8192 with
 // 16 CTAs); taller problems keep the cooperative kernel.
 //
 // Waits are bounded as in the cluster panel: past the context's spin limit a
@@ -136,23 +137,25 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
     const int k0 = panel_of(step) * NB;
     s_upf[tid] = k0 + tid < p.K ? (float)p.up[k0 + tid] : 0.f;
   };
-  // TMA: warp 0 announces the bytes and copies each column of a panel's slice
+  // TMA: threads [t0, t0 + nth) (whole warps) copy each column of a panel's
+  // slice, the first of them announcing the bytes
   auto rows_of = [&](int step, int *lo_, int *rows_) {
     const int k0 = panel_of(step) * NB;
     *lo_ = max(r0, k0);
     *rows_ = max(0, r1 - *lo_);
   };
-  auto tma_issue = [&](int step) {
-    if (!TMA || step >= p.np || warp != 0) return;
+  auto tma_issue = [&](int step, int t0, int nth) {
+    if (!TMA || step >= p.np || tid < t0 || tid >= t0 + nth) return;
     const int pnl = panel_of(step), k0 = pnl * NB, nbw = min(NB, p.K - k0);
     int lo, rows;
     rows_of(step, &lo, &rows);
     const unsigned bytes = (unsigned)rows * 4u;         // (rows % 4 == 0)
-    if (lane == 0) mbar_expect(&s_vbar, bytes * (unsigned)nbw);
-    __syncwarp();
+    if (tid == t0) mbar_expect(&s_vbar, bytes * (unsigned)nbw);
+    if (nth == 32) __syncwarp();
+    else asm volatile("bar.sync 2, %0;" ::"r"(nth) : "memory");
     if (bytes == 0) return;
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_vbar);
-    for (int c = lane; c < nbw; c += 32) {
+    for (int c = tid - t0; c < nbw; c += nth) {
       const float *src = A + (size_t)lo + (size_t)(k0 + c) * lda;
       const unsigned dst = (unsigned)__cvta_generic_to_shared(Vs + (size_t)c * RP);
       asm volatile(
@@ -162,7 +165,7 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
   };
   if (TMA) {
     __syncthreads();                                    // (the barrier's init before its use)
-    tma_issue(0);
+    tma_issue(0, 0, 32);
   } else {
     prefetch(0);
   }
@@ -208,7 +211,6 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
         }
       }
       __syncthreads();                                    // every thread is done with Vs
-      tma_issue(s + 1);                                   // the next panel's slice, in flight
     } else {
 #pragma unroll
       for (int t = 0; t < CPW; ++t) {
@@ -248,7 +250,10 @@ qvec_cluster_kernel(QvecClusterParams<VT> p) {
       st_async16(cluster_addr(&s_recv[buf][q][c], dest), &s_rec[buf][c],
                  cluster_addr(&s_mbar[buf], dest));
     }
-    // ---- warps 0-1: the sums over the cluster ------------------------------------
+    // ---- warps 2-15 start the next panel's copies (an issuing warp can stall
+    // until the copy engine accepts them) while warps 0-1 wait for the
+    // cluster's records and sum them ----------------------------------------------
+    tma_issue(s + 1, 64, NT - 64);
     if (warp < 2) {
       bool got = false;
       if (s_ok) got = mbar_wait_bounded(&s_mbar[buf], (unsigned)(s >> 1) & 1u, p.spin, p.status,
