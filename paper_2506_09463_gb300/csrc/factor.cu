@@ -776,6 +776,150 @@ gemm_upd_kernel(const T *__restrict__ A, int lda, const double *__restrict__ Vto
   }
 }
 
+// FP32 forms of the two products for panels of width 64.  The FP64 kernels
+// above read one value per shared-memory load, which leaves the FP32 pipe
+// waiting on shared memory (8 loads per 16 FMAs, at about twice the FMA
+// time); these read four values per 16-byte load and stage each tile with
+// every global load issued before the first store.  Each output sums its
+// terms in the same order as the FP64-form kernels, so results are
+// identical.
+constexpr int kF32Ld = kBK + 4;   // row stride of a staged chunk (= 4 mod 32)
+
+// W_part[s][c][a] = sum_{i in slice s} V(i, a) X(i, c), chunks of kBK rows
+// staged [column][row]; thread (tx, ty) owns a = tx + 16 i, c = ty + 16 j and
+// reads four consecutive rows of each with one load (V: 16 distinct addresses
+// per half-warp, two wavefronts; X: two, one wavefront).
+__global__ void __launch_bounds__(kThreads, 3)
+gemm_vtx_f32_kernel(const float *__restrict__ A, int lda, const double *__restrict__ Vtop,
+                    int k0, int nbw, int M, const float *__restrict__ X, int ldx, int N, int RS,
+                    float *__restrict__ Wp, int skip) {
+  constexpr int NB = 64;
+  __shared__ __align__(16) float Vs[NB * kF32Ld];
+  __shared__ __align__(16) float Xs[kBN * kF32Ld];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int c0 = blockIdx.x * kBN;
+  const int s = blockIdx.y;
+  const int i_begin = s * RS, i_end = min(M, i_begin + RS);
+  constexpr int PER = NB * kBK / kThreads;     // entries of V (and of X) per thread: 8
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int i0 = i_begin; i0 < i_end; i0 += kBK) {
+    float vv[PER], xv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * kThreads, a = idx / kBK, kk = idx % kBK;
+      const int i = i0 + kk, cc = c0 + a;
+      vv[u] = (i < i_end) ? v_at<float>(A, lda, Vtop, NB, k0, nbw, i, a, skip) : 0.f;
+      xv[u] = (i < i_end && cc < N) ? X[SLQR_IDX(panel_row(k0, nbw, skip, i), cc, ldx)] : 0.f;
+    }
+    __syncthreads();                           // the previous chunk has been read
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * kThreads, a = idx / kBK, kk = idx % kBK;
+      Vs[a * kF32Ld + kk] = vv[u];
+      Xs[a * kF32Ld + kk] = xv[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 4) {
+      float4 va[4], xc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        va[i] = *reinterpret_cast<const float4 *>(Vs + (tx + 16 * i) * kF32Ld + kk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        xc[j] = *reinterpret_cast<const float4 *>(Xs + (ty + 16 * j) * kF32Ld + kk);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] = fmaf(va[i].x, xc[j].x, acc[i][j]);
+          acc[i][j] = fmaf(va[i].y, xc[j].y, acc[i][j]);
+          acc[i][j] = fmaf(va[i].z, xc[j].z, acc[i][j]);
+          acc[i][j] = fmaf(va[i].w, xc[j].w, acc[i][j]);
+        }
+    }
+  }
+  float *out = Wp + (size_t)s * N * NB;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int cc = c0 + ty + 16 * j;
+    if (cc < N) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[(size_t)cc * NB + tx + 16 * i] = acc[i][j];
+    }
+  }
+}
+
+// X(i, c) -= sum_a V(i, a) W'[a][c] on a kBM x kBN tile; thread (tx, ty) owns
+// rows 4 tx .. 4 tx + 3 and columns 4 ty .. 4 ty + 3 and reads each with one
+// 16-byte load per reflector; X is read and written four rows at a time where
+// the row map and the alignment allow (vec).
+__global__ void __launch_bounds__(kThreads)
+gemm_upd_f32_kernel(const float *__restrict__ A, int lda, const double *__restrict__ Vtop,
+                    int k0, int nbw, int M, float *__restrict__ X, int ldx, int N,
+                    const float *__restrict__ Wt, int skip, int vec) {
+  constexpr int NB = 64;
+  __shared__ __align__(16) float Vs[NB * kBM];   // [a][row]
+  __shared__ __align__(16) float Ws[NB * kBN];   // [a][column]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * kBM, c0 = blockIdx.y * kBN;
+  {
+    constexpr int PER = NB * kBM / kThreads;    // 16
+    float vv[PER], wv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * kThreads, a = idx / kBM, ii = idx % kBM;
+      const int i = i0 + ii;
+      vv[u] = (i < M) ? v_at<float>(A, lda, Vtop, NB, k0, nbw, i, a, skip) : 0.f;
+      wv[u] = (c0 + ii < N) ? Wt[(size_t)a * N + c0 + ii] : 0.f;   // (kBN == kBM)
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * kThreads;
+      Vs[idx] = vv[u];
+      Ws[idx] = wv[u];
+    }
+  }
+  __syncthreads();
+  float acc[4][4];                              // [row p][column q]
+#pragma unroll
+  for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[pp][q] = 0.f;
+#pragma unroll 4
+  for (int a = 0; a < nbw; ++a) {
+    const float4 v = *reinterpret_cast<const float4 *>(Vs + a * kBM + 4 * tx);
+    const float4 w = *reinterpret_cast<const float4 *>(Ws + a * kBN + 4 * ty);
+    const float vr[4] = {v.x, v.y, v.z, v.w}, wr[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[pp][q] = fmaf(vr[pp], wr[q], acc[pp][q]);
+  }
+  const int ib = i0 + 4 * tx;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cc = c0 + 4 * ty + q;
+    if (cc >= N) continue;
+    if (vec && ib + 3 < M && (ib >= nbw || ib + 3 < nbw)) {
+      float4 *dst = reinterpret_cast<float4 *>(X + SLQR_IDX(panel_row(k0, nbw, skip, ib), cc, ldx));
+      float4 x = *dst;
+      x.x -= acc[0][q]; x.y -= acc[1][q]; x.z -= acc[2][q]; x.w -= acc[3][q];
+      *dst = x;
+    } else {
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) {
+        const int i = ib + pp;
+        if (i < M) X[SLQR_IDX(panel_row(k0, nbw, skip, i), cc, ldx)] -= acc[pp][q];
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------
@@ -879,8 +1023,8 @@ size_t panel_update_work_doubles(int m, int N, int nb, int num_sms) {
 // remaining rows.
 static void vtop_part_f32(const float *A, int lda, const double *Vtop, int k0, int rows,
                           const float *X, int ldx, int N, float *Wp, cudaStream_t stream) {
-  gemm_vtx_kernel<float, 64, false><<<dim3((N + kBN - 1) / kBN, 1), kThreads, 0, stream>>>(
-      A, lda, Vtop, k0, 64, rows, X, ldx, N, rows, Wp);
+  gemm_vtx_f32_kernel<<<dim3((N + kBN - 1) / kBN, 1), kThreads, 0, stream>>>(
+      A, lda, Vtop, k0, 64, rows, X, ldx, N, rows, Wp, 0);
 }
 
 // lookahead: the update of the next panel's columns only (FP32: on the FMA
@@ -919,6 +1063,27 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
       }
     }
   };
+  // the FMA-pipe products (FP32 panels of width 64: the 16-byte-load forms)
+  auto launch_vtx_fma = [&](int S_, int RS_) {
+    if constexpr (std::is_same<T, float>::value && NB == 64)
+      gemm_vtx_f32_kernel<<<dim3(ntiles, S_), kThreads, 0, stream>>>(A, lda, Vtop, k0, nbw, M, X,
+                                                                      ldx, N, RS_, Wp, skip);
+    else
+      gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, S_), kThreads, 0, stream>>>(
+          A, lda, Vtop, k0, nbw, M, X, ldx, N, RS_, Wp, skip);
+  };
+  auto launch_upd_fma = [&](const T *Wt_) {
+    if constexpr (std::is_same<T, float>::value && NB == 64) {
+      const int vec = (ldx % 4 == 0 && ((uintptr_t)X & 15) == 0 && k0 % 4 == 0 && skip % 4 == 0 &&
+                       nbw % 4 == 0) ? 1 : 0;
+      gemm_upd_f32_kernel<<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, 0, stream>>>(
+          A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt_, skip, vec);
+    } else {
+      gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads,
+                               (size_t)NB * (kBM + kBN) * sizeof(T), stream>>>(
+          A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt_, skip);
+    }
+  };
   if constexpr (std::is_same<T, float>::value && NB == 64) {
     // tensor-core path: both products on the tensor cores for a full panel
     // whose X lies in A (the factorization); W'^T and a row-major V follow
@@ -943,9 +1108,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
           launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
           prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
           slot = prof_begin(ctx, stream);
-          gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads,
-                                   (size_t)NB * (kBM + kBN) * sizeof(T), stream>>>(
-              A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt);
+          launch_upd_fma(Wt);
           refresh_shadows();
           prof_end(ctx, stream, slot, kUpd, gemm_flops);
           return check_launch(ctx, "trailing update");
@@ -955,15 +1118,13 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
   }
   if (slices == 0) {
     slices = Seff;
-    gemm_vtx_kernel<T, NB, false><<<dim3(ntiles, Seff), kThreads, 0, stream>>>(
-        A, lda, Vtop, k0, nbw, M, X, ldx, N, RS, Wp, skip);
+    launch_vtx_fma(Seff, RS);
   }
   prof_end(ctx, stream, slot, kVtx, gemm_flops);
   slot = prof_begin(ctx, stream);
   if (tc) launch_tw<T, NB, TRANS, true>(Wp, slices, N, wy_panel, nbw, Wt, stream);
   else launch_tw<T, NB, TRANS>(Wp, slices, N, wy_panel, nbw, Wt, stream);
   prof_end(ctx, stream, slot, kTw, (double)nbw * nbw * N);
-  size_t smem = (size_t)NB * (kBM + kBN) * sizeof(T);
   slot = prof_begin(ctx, stream);
   bool done = false;
   if constexpr (std::is_same<T, float>::value) {
@@ -981,8 +1142,7 @@ static slqr_status panel_update_impl(slqr_ctx *ctx, int m, int k0, int nbw, cons
     }
   }
   if (!done) {
-    gemm_upd_kernel<T, NB><<<dim3((M + kBM - 1) / kBM, ntiles), kThreads, smem, stream>>>(
-        A, lda, Vtop, k0, nbw, M, X, ldx, N, Wt, skip);
+    launch_upd_fma(Wt);
     refresh_shadows();
   }
   prof_end(ctx, stream, slot, kUpd, gemm_flops);
