@@ -564,6 +564,14 @@ def run_mixed_workload(ctx, device, stream, barrier, inputs):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flops = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + (4.0 * m * n - 2.0 * n * n) + n * n
     precs = (("fp32", abi.SLQR_FP32), ("tf32", abi.SLQR_TF32), ("bf16x3", abi.SLQR_BF16X3))
+    # one untimed solve per precision first: the first call of a precision
+    # loads its kernels and builds its tensor maps and workspaces (1-2 ms)
+    A0, _, _, b0 = inputs[MIXED_KAPPAS[0]]
+    for _, prec in precs:
+        x = torch.zeros(n, dtype=torch.float64, device=device)
+        abi.slqr_lstsq_mixed_ex(ctx.ctx, m, n, A0.data_ptr(), m, b0.data_ptr(), x.data_ptr(), prec,
+                                stream.cuda_stream, fp64_fallback=1)
+    stream.synchronize()
     for kappa in MIXED_KAPPAS:
         A, b_cons, x_true, b_rand = inputs[kappa]
         rec = {}
