@@ -986,9 +986,9 @@ def run_tune():
 
 
 def run_ncu_mixed(m, n, prec_name="tf32"):
-    """Two tensor-core mixed-precision LS solves (TF32 or BF16 hi + lo) of an
-    iid N(0,1) m x n matrix: a small program for ncu captures of the
-    tensor-core kernels (no torch.linalg call, which does not load under the
+    """Two mixed-precision LS solves (TF32, BF16 hi + lo or FP32 factorization)
+    of an iid N(0,1) m x n matrix: a small program for ncu captures of the
+    mixed path's kernels (no torch.linalg call, which does not load under the
     profiler)."""
     import torch
     import workloads
@@ -1000,7 +1000,7 @@ def run_ncu_mixed(m, n, prec_name="tf32"):
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     with api.Context(0) as ctx:
         for _ in range(2):
-            prec = abi.SLQR_BF16X3 if prec_name == "bf16x3" else abi.SLQR_TF32
+            prec = {"bf16x3": abi.SLQR_BF16X3, "fp32": abi.SLQR_FP32}.get(prec_name, abi.SLQR_TF32)
             st, its, err = abi.slqr_lstsq_mixed(ctx.ctx, m, n, A.data_ptr(), m, b.data_ptr(),
                                                 x.data_ptr(), prec, 0, 0.0,
                                                 torch.cuda.current_stream().cuda_stream)
@@ -1098,8 +1098,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream workload")
     ap.add_argument("--ncu-mixed", type=int, nargs=2, metavar=("M", "N"),
                     help="run one TF32 mixed-precision solve for profiling and exit")
-    ap.add_argument("--ncu-prec", default="tf32", choices=["tf32", "bf16x3"],
-                    help="tensor-core precision of --ncu-mixed")
+    ap.add_argument("--ncu-prec", default="tf32", choices=["tf32", "bf16x3", "fp32"],
+                    help="factorization precision of --ncu-mixed")
     ap.add_argument("--ncu-batch", type=int, metavar="COUNT",
                     help="run one FP64 and one FP32 batch for profiling and exit")
     ap.add_argument("--tune", action="store_true",
