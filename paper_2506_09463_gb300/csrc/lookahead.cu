@@ -9,10 +9,11 @@
 // Here one kernel on up to one CTA per SM does all of it:
 //   1. CTA q stages its 32-row-aligned slice of V and X in shared memory and
 //      forms the partial W_q = V_q^T X_q;
-//   2. (grid barrier) CTA c sums column c of the partials in a fixed order
-//      (so the result does not depend on timing) and forms column c of
-//      W' = T^T W by the substitution with T^{-1} = striu(G) + diag(1 / tau)
-//      (G = striu(V^T V) and tau as stored in the compact-WY panel);
+//   2. (grid barrier) CTA q sums columns q, q + P, .. of the partials in a
+//      fixed order (so the result does not depend on timing) and forms those
+//      columns of W' = T^T W by the substitution with
+//      T^{-1} = striu(G) + diag(1 / tau) (G = striu(V^T V) and tau as stored
+//      in the compact-WY panel);
 //   3. (grid barrier) every CTA reads W' and updates its slice, X_q -= V_q W',
 //      from the V and X still in its shared memory, and stores X_q.
 // HBM traffic is the algorithmic minimum: V and X read once, X written once.
